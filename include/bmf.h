@@ -1,0 +1,211 @@
+/*
+ * bmf.h -- C ABI of libbmf.so: the BPMF Gibbs sweep and posterior propagation (PP) of
+ * Qin et al., "Distributed Bayesian Matrix Factorization with Limited Communication"
+ * (arXiv 1703.00734), on one GB300 GPU.
+ *
+ * Model (Section 2.1): Y (N x D) partially observed, y_nd ~ N(x_n^T w_d, 1/tau) on observed
+ * entries (Eqs. 2-3), x_n ~ N(mu_X, Lambda_X^{-1}), w_d ~ N(mu_W, Lambda_W^{-1}) (Eqs. 4a/4b),
+ * Normal-Wishart hyperpriors on (mu_X, Lambda_X) and (mu_W, Lambda_W) with tau fixed
+ * (Section 5.1).  The Gibbs sweep draws the hyperparameters, then every x_n given W, then every
+ * w_d given X.  PP (Section 3.2, Algorithm 1) splits the rows into I and the columns into J
+ * blocks; stage 1 samples subset (0,0), stage 2 the subsets sharing its rows or columns with
+ * the stage-1 posterior as prior, stage 3 the rest with the stage-2 posteriors as priors; each
+ * subset posterior is summarised per row by moment matching (Section 4.1) and the summaries
+ * are combined by Eq. 14 with the eigenvalue correction of Algorithm 2.
+ *
+ * Conventions (the paper does not fix them; the library and any checker follow these):
+ *  - Gaussian draws: precision P = L L^T (lower Cholesky, positive diagonal), x = mu + L^{-T} z.
+ *  - Wishart(W, nu) draws: Bartlett decomposition on the lower Cholesky L of W:
+ *    Lambda = (L A)(L A)^T, A lower triangular, A_kk = sqrt(c_k), c_k ~ chi^2(nu - k)
+ *    (k = 0..K-1), A_kl ~ N(0,1) for k > l.
+ *  - Hyperparameter posterior: centred scatter matrix (Section 5.1 footnote):
+ *    [W*]^{-1} = W0^{-1} + N Sbar + (beta0 N / (beta0 + N)) (mu0 - xbar)(mu0 - xbar)^T,
+ *    beta* = beta0 + N, nu* = nu0 + N, mu* = (beta0 mu0 + N xbar) / beta*;
+ *    mu ~ N(mu*, (beta* Lambda)^{-1}).
+ *  - Sweep order: (mu_X, Lambda_X) | X, (mu_W, Lambda_W) | W, then X | W, then W | X.
+ *  - Ordering (Section 5.2): BMF_ORDER_DECREASING sorts rows (columns) by decreasing number
+ *    of training observations, ties by original index; row_bounds/col_bounds are given in
+ *    that order.  Subset (i, j) (0-based) has id s = i*J + j and stage 1 if i = j = 0,
+ *    stage 2 if exactly one of i, j is 0, stage 3 otherwise.
+ *  - Propagated priors (Algorithm 1, Section 5.1): in stage 2, subset (i,0) uses the stage-1
+ *    posterior of W^(0) and draws hyperparameters for X^(i); subset (0,j) uses the stage-1
+ *    posterior of X^(0) and draws hyperparameters for W^(j).  In stage 3, subset (i,j) uses
+ *    the posterior of X^(i) from (i,0) and of W^(j) from (0,j) and draws no hyperparameters.
+ *    A propagated factor starts its chain at the propagated mean.
+ *  - Moment matching: over the retained samples (sweep t, counted from 1 within a subset's
+ *    chain, is retained when t > burnin and (t - burnin - 1) % thin == 0):
+ *    mu = mean, Sigma = E[x x^T] - mu mu^T (1/S normaliser), Lambda = Sigma^{-1}.
+ *  - Aggregation (Eq. 14, Algorithm 2): for X^(i) submodel "(1)" is subset (i,0) and the
+ *    others are (i,j), j >= 1; for W^(j) it is (0,j) and (i,j), i >= 1.  A difference
+ *    Lambda^(j) - Lambda^(1) that is not positive definite (FP64 Cholesky pivot <= 0) gets
+ *    |lambda_min| + eps added to its diagonal, eps = eps_rel * max(1, mean diag Lambda^(1)).
+ *  - Prediction (Section 5.2): y_hat = offset + mu*_x^T mu*_w with the aggregated posterior
+ *    means (for a 1 x 1 grid: the means of the retained samples); offset is the training mean
+ *    when cfg.center = 1, else 0.
+ *
+ * Draw buffers (bmf_draws): for each sweep of a batch (the subsets of one stage, or one
+ * subset), in this order:
+ *    for each subset of the batch in id order: an X block then a W block of K(K+3)/2 numbers
+ *      each: c[K] (chi-square variates, dof nu0 + n - k for k = 0..K-1, where n is the number
+ *      of rows of that factor block in the subset), the K(K-1)/2 below-diagonal normals row by
+ *      row (k = 1..K-1, l = 0..k-1), z_mu[K].  The block of a propagated factor is present and
+ *      ignored.
+ *    then z for every X row of the batch (subsets in id order, rows in local order), K each;
+ *    then z for every W row of the batch, K each.
+ *  Consecutive sweeps follow each other.  With draws == NULL the library draws from its
+ *  own device generator (counter-based Philox4x32-10, Salmon et al. SC'11) seeded by cfg.seed.
+ *
+ * Memory and errors.  The context owns all device memory it allocates.  Host pointers passed
+ * in are read during the call only; the caller keeps ownership.  Every call is synchronous
+ * with respect to the host unless stated.  Calls return a bmf_status; nothing aborts or traps
+ * on the device.  bmf_last_error() gives a message for the last failed call.  A context must
+ * be used from one host thread at a time.
+ */
+#ifndef BMF_H
+#define BMF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bmf_ctx bmf_ctx;
+
+typedef enum {
+    BMF_OK = 0,
+    BMF_E_ARG = 1,       /* null pointer, index or size out of range, duplicate entry */
+    BMF_E_SHAPE = 2,     /* inconsistent sizes (bounds, draw buffer length, K) */
+    BMF_E_NOT_PD = 3,    /* a conditional precision or moment-matched covariance is not PD */
+    BMF_E_NONFINITE = 4, /* NaN or Inf in an input value */
+    BMF_E_TIMEOUT = 5,   /* a bounded device wait expired */
+    BMF_E_OOM = 6,       /* device allocation failed */
+    BMF_E_CUDA = 7,      /* CUDA runtime error */
+    BMF_E_STATE = 8      /* call not valid now (e.g. stage 2 before stage 1) */
+} bmf_status;
+
+/* Precision of the gathered factor copies and of the Gram accumulation.  The conditional
+ * assembly, Cholesky, solves, draws, hyperparameter step and moments are FP64 in all modes. */
+enum { BMF_FP64 = 0, BMF_FP32 = 1, BMF_BF16 = 2 };
+enum { BMF_ORDER_NONE = 0, BMF_ORDER_DECREASING = 1 };
+enum { BMF_FACTOR_X = 0, BMF_FACTOR_W = 1 };
+
+#define BMF_MAX_K 64
+
+typedef struct {
+    int32_t K;         /* latent dimension, 1..BMF_MAX_K */
+    int32_t precision; /* BMF_FP64 / BMF_FP32 / BMF_BF16 */
+    double tau;        /* noise precision (Eq. 3), > 0 */
+    double beta0;      /* Normal-Wishart beta0 > 0 */
+    double nu0;        /* Normal-Wishart nu0 > K - 1 */
+    const double *mu0; /* host [K], or NULL for zeros */
+    const double *W0;  /* host [K*K] symmetric positive definite, or NULL for the identity */
+    int32_t order;     /* BMF_ORDER_NONE / BMF_ORDER_DECREASING */
+    int32_t center;    /* 1: subtract the training mean from the values (added back in y_hat) */
+    int32_t burnin;    /* sweeps discarded per chain before moments are accumulated */
+    int32_t thin;      /* keep every thin-th sweep after burn-in (>= 1) */
+    uint64_t seed;     /* device generator seed (used when draws == NULL) */
+    double eps_rel;    /* Algorithm 2 epsilon scale (<= 0: 1e-6) */
+} bmf_config;
+
+typedef struct {
+    const double *ptr; /* draw buffer (layout above), FP64 */
+    int64_t len;       /* number of doubles; must equal n_sweeps * bmf_draws_per_sweep() */
+    int32_t on_device; /* 1: ptr is device memory of the context's GPU; 0: host memory */
+} bmf_draws;
+
+typedef struct {
+    double rmse_sample; /* test RMSE of the last sweep's sample (NaN without a test set) */
+    double rmse_mean;   /* test RMSE of the mean prediction over retained samples (NaN if none) */
+    int64_t sweeps;     /* sweeps done by the batch's chains (of the first subset) */
+    int64_t kept;       /* retained samples so far (of the first subset) */
+} bmf_sweep_stats;
+
+typedef struct {
+    int32_t i, j, stage;
+    int64_t row0, row1; /* row block [row0, row1) in the reordered row order */
+    int64_t col0, col1;
+    int64_t nnz;
+} bmf_subset_info;
+
+/* Create a context: validates the COO training data (indices in range, no duplicate (row,col),
+ * finite values), reorders (cfg->order), splits it into the I x J grid (Section 3), builds the
+ * per-subset CSR (rows) and CSC (columns) lists and uploads them, and initialises every
+ * subset's chain from X0/W0init.
+ *   row, col, val: host COO of the training entries, nnz each, 0-based original indices.
+ *   row_bounds: host [I+1] increasing from 0 to N in the reordered order, or NULL for
+ *     floor(i*N/I); col_bounds likewise with J and D.
+ *   X0 [N*K], W0init [D*K]: host initial states in the ORIGINAL index order (row-major).
+ *   test_row/test_col/test_val: host COO of held-out entries for the per-sweep RMSE
+ *     (n_test may be 0 and the pointers NULL).
+ *   stream: a cudaStream_t the context enqueues on (NULL: the legacy default stream).
+ * On success *out owns the context; free it with bmf_destroy. */
+bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, int64_t nnz,
+                    const int32_t *row, const int32_t *col, const double *val, int32_t I,
+                    const int64_t *row_bounds, int32_t J, const int64_t *col_bounds,
+                    const double *X0, const double *W0init, int64_t n_test,
+                    const int32_t *test_row, const int32_t *test_col, const double *test_val,
+                    void *stream);
+
+/* Number of doubles of one sweep's draw buffer for a batch: the subsets of `stage` (1..3)
+ * when subset < 0, else the single subset `subset`. */
+int64_t bmf_draws_per_sweep(const bmf_ctx *ctx, int32_t stage, int32_t subset);
+
+/* n_sweeps Gibbs sweeps of one subset's chain (the whole data for a 1 x 1 grid).  The subset's
+ * stage must be open (see bmf_stage).  draws: NULL for the device generator, else the buffer
+ * for n_sweeps sweeps of this single-subset batch.  stats may be NULL. */
+bmf_status bmf_sweep(bmf_ctx *ctx, int32_t subset, int32_t n_sweeps, const bmf_draws *draws,
+                     bmf_sweep_stats *stats);
+
+/* n_sweeps Gibbs sweeps of every subset of `stage` (Algorithm 1), all subsets of the stage
+ * batched into the same kernel launches.  The first call for stage 2 (3) finalises the moments
+ * of stage 1 (2) and installs the propagated priors; stages are opened in order and a stage
+ * may be called several times to continue its chains. */
+bmf_status bmf_stage(bmf_ctx *ctx, int32_t stage, int32_t n_sweeps, const bmf_draws *draws,
+                     bmf_sweep_stats *stats);
+
+/* Posterior-mean predictions (Section 5.2) for n entries given by original indices (host
+ * arrays).  Finalises the moments of the open stage and aggregates (Eq. 14, Algorithm 2).
+ * yhat: host [n] or NULL; y: host [n] or NULL; rmse: RMSE against y (needs y) or NULL. */
+bmf_status bmf_predict(bmf_ctx *ctx, int64_t n, const int32_t *row, const int32_t *col,
+                       const double *y, double *yhat, double *rmse);
+
+/* Aggregated posterior means (Eq. 14 / Algorithm 2) in the ORIGINAL order: Xm [N*K],
+ * Wm [D*K] host; n_corrected (nullable) counts eigenvalue-corrected (row, submodel) pairs. */
+bmf_status bmf_posterior_means(bmf_ctx *ctx, double *Xm, double *Wm, int64_t *n_corrected);
+
+/* Chain state of one subset to / from host memory, in the subset's local (reordered) order:
+ * X [n_rows*K], W [n_cols*K], hyper = mu_X[K], Lambda_X[K*K], mu_W[K], Lambda_W[K*K]
+ * (the last hyperparameter draw).  Any pointer may be NULL to skip that part. */
+bmf_status bmf_get_state(bmf_ctx *ctx, int32_t subset, double *X, double *W, double *hyper);
+bmf_status bmf_set_state(bmf_ctx *ctx, int32_t subset, const double *X, const double *W);
+
+/* Moment sums of one subset: S1 [n*K], S2 [n*K*K] for factor BMF_FACTOR_X / _W, and the
+ * number of retained samples. */
+bmf_status bmf_get_moments(bmf_ctx *ctx, int32_t subset, int32_t factor, double *S1, double *S2,
+                           int64_t *kept);
+
+/* Per-row moment-matched posterior (mu [n*K], Lambda [n*K*K]) of one subset's factor, as
+ * propagated to the next stage.  Valid once the subset's stage has been finalised. */
+bmf_status bmf_get_posterior(bmf_ctx *ctx, int32_t subset, int32_t factor, double *mu,
+                             double *Lam);
+
+/* Install a per-row Gaussian prior (mu [n*K], Lambda [n*K*K], host) on one subset's factor,
+ * replacing its hyperparameter draws (as a propagated prior does). */
+bmf_status bmf_set_prior(bmf_ctx *ctx, int32_t subset, int32_t factor, const double *mu,
+                         const double *Lam);
+
+/* Grid geometry of one subset, and the reordering (new -> original index) of rows/columns. */
+bmf_status bmf_subset_info(const bmf_ctx *ctx, int32_t subset, bmf_subset_info *info);
+bmf_status bmf_get_perm(const bmf_ctx *ctx, int64_t *row_perm, int64_t *col_perm);
+
+void bmf_destroy(bmf_ctx *ctx);
+
+/* Message of the last failed call on ctx (or of the last failed bmf_init when ctx is NULL). */
+const char *bmf_last_error(const bmf_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BMF_H */

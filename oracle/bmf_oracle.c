@@ -1,0 +1,526 @@
+/*
+ * bmf_oracle.c -- the ORACLE: a plain, slow, FP64 CPU restatement of the BPMF Gibbs sweep
+ * and of the posterior-propagation (PP) approximation and aggregation steps of
+ * Qin et al., "Distributed Bayesian Matrix Factorization with Limited Communication"
+ * (arXiv 1703.00734).
+ *
+ * THIS FILE IS TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark load it.  It shares no code, header, table or constant
+ * with the CUDA library; the library never loads it.
+ *
+ * Everything is written out from the definitions, in the order the method states them,
+ * with sequential loops and no blocking or reordering:
+ *   - model: Gaussian likelihood on observed entries with noise precision tau (Eqs. 2-3),
+ *     Gaussian row priors (Eqs. 4a/4b), Normal-Wishart hyperpriors (Section 5.1);
+ *   - Gibbs conditionals: the textbook conjugate updates of BPMF (Salakhutdinov & Mnih 2008,
+ *     cited in Section 5.1), with the centred scatter matrix of the Section 5.1 footnote;
+ *   - moment matching (Section 4.1) and the eigenvalue-corrected aggregation of
+ *     Algorithm 2 / Eq. 14 (Section 4.2).
+ *
+ * Conventions fixed here (the paper is silent on them; the CUDA library follows the same
+ * conventions, stated in its public header):
+ *   - a Gaussian with precision P is drawn as mu + L^{-T} z with P = L L^T (lower, positive
+ *     diagonal Cholesky) and z standard normal;
+ *   - Wishart(W, nu) is drawn by the Bartlett decomposition on the lower Cholesky factor L of
+ *     W: Lambda = (L A)(L A)^T, A lower triangular, A_kk = sqrt(chi2_k) with
+ *     chi2_k ~ chi^2(nu - k) (k = 0..K-1), A_kl ~ N(0,1) for k > l;
+ *   - one block of hyperparameter draws is laid out as chi2[K], then the K(K-1)/2
+ *     below-diagonal normals row by row (k = 1..K-1, l = 0..k-1), then z_mu[K].
+ * Matrices are dense, row-major, K x K; vectors are row-major [rows x K].
+ *
+ * Pinned by tests/test_oracle_*.py against closed forms, identities and brute force
+ * (see the tests for which pin covers which function).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_NOT_PD 1
+#define ORC_ARG 2
+#define ORC_NOMEM 3
+
+/* ------------------------------------------------------------------------------------- */
+/* Dense FP64 linear algebra (textbook forms).                                           */
+/* ------------------------------------------------------------------------------------- */
+
+/* Cholesky factor of a symmetric positive definite A: A = L L^T, L lower with positive
+ * diagonal (Cholesky-Crout, column by column).  Returns ORC_NOT_PD if a pivot is not > 0. */
+static int chol_lower(int K, const double *A, double *L)
+{
+    memset(L, 0, sizeof(double) * (size_t)K * K);
+    for (int j = 0; j < K; ++j) {
+        double s = A[j * K + j];
+        for (int k = 0; k < j; ++k) s -= L[j * K + k] * L[j * K + k];
+        if (!(s > 0.0)) return ORC_NOT_PD;
+        double d = sqrt(s);
+        L[j * K + j] = d;
+        for (int i = j + 1; i < K; ++i) {
+            double t = A[i * K + j];
+            for (int k = 0; k < j; ++k) t -= L[i * K + k] * L[j * K + k];
+            L[i * K + j] = t / d;
+        }
+    }
+    return ORC_OK;
+}
+
+/* Solve L y = b in place (L lower triangular). */
+static void solve_lower(int K, const double *L, double *y)
+{
+    for (int i = 0; i < K; ++i) {
+        double t = y[i];
+        for (int k = 0; k < i; ++k) t -= L[i * K + k] * y[k];
+        y[i] = t / L[i * K + i];
+    }
+}
+
+/* Solve L^T x = y in place (L lower triangular, so L^T is upper triangular). */
+static void solve_lower_t(int K, const double *L, double *x)
+{
+    for (int i = K - 1; i >= 0; --i) {
+        double t = x[i];
+        for (int k = i + 1; k < K; ++k) t -= L[k * K + i] * x[k];
+        x[i] = t / L[i * K + i];
+    }
+}
+
+/* Inverse of a symmetric positive definite matrix through its Cholesky factor:
+ * column j of A^{-1} solves L L^T x = e_j. */
+static int spd_inverse(int K, const double *A, double *Ainv, double *work /* K*K + K */)
+{
+    double *L = work, *col = work + (size_t)K * K;
+    if (chol_lower(K, A, L)) return ORC_NOT_PD;
+    for (int j = 0; j < K; ++j) {
+        for (int i = 0; i < K; ++i) col[i] = (i == j) ? 1.0 : 0.0;
+        solve_lower(K, L, col);
+        solve_lower_t(K, L, col);
+        for (int i = 0; i < K; ++i) Ainv[i * K + j] = col[i];
+    }
+    /* symmetrise (the two triangles agree up to rounding) */
+    for (int i = 0; i < K; ++i)
+        for (int j = 0; j < i; ++j) {
+            double m = 0.5 * (Ainv[i * K + j] + Ainv[j * K + i]);
+            Ainv[i * K + j] = m;
+            Ainv[j * K + i] = m;
+        }
+    return ORC_OK;
+}
+
+/* Smallest eigenvalue of a symmetric matrix by the cyclic Jacobi method
+ * (Golub & Van Loan, "Matrix Computations", Section 8.5): rotate away each off-diagonal
+ * entry in turn until the off-diagonal mass is negligible; the diagonal then holds the
+ * eigenvalues. */
+static double jacobi_min_eig(int K, const double *M, double *a /* K*K work */)
+{
+    memcpy(a, M, sizeof(double) * (size_t)K * K);
+    double fro = 0.0;
+    for (int i = 0; i < K * K; ++i) fro += a[i] * a[i];
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < K; ++p)
+            for (int q = p + 1; q < K; ++q) off += a[p * K + q] * a[p * K + q];
+        if (off <= 1e-30 * fro || off == 0.0) break;
+        for (int p = 0; p < K; ++p)
+            for (int q = p + 1; q < K; ++q) {
+                double apq = a[p * K + q];
+                if (apq == 0.0) continue;
+                double theta = (a[q * K + q] - a[p * K + p]) / (2.0 * apq);
+                double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                /* A <- J^T A J with J the rotation in the (p, q) plane */
+                for (int k = 0; k < K; ++k) {
+                    double akp = a[k * K + p], akq = a[k * K + q];
+                    a[k * K + p] = c * akp - s * akq;
+                    a[k * K + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < K; ++k) {
+                    double apk = a[p * K + k], aqk = a[q * K + k];
+                    a[p * K + k] = c * apk - s * aqk;
+                    a[q * K + k] = s * apk + c * aqk;
+                }
+            }
+    }
+    double m = a[0];
+    for (int i = 1; i < K; ++i)
+        if (a[i * K + i] < m) m = a[i * K + i];
+    return m;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* Normal-Wishart hyperparameter update (Section 5.1 and its footnote).                  */
+/* ------------------------------------------------------------------------------------- */
+
+/* Posterior parameters of (mu, Lambda) given the N rows of X under the Normal-Wishart
+ * prior (mu0, beta0, nu0, W0):
+ *   xbar = (1/N) sum_i x_i,   Sbar = (1/N) sum_i (x_i - xbar)(x_i - xbar)^T   (centred,
+ *   as the Section 5.1 footnote corrects),
+ *   beta* = beta0 + N, nu* = nu0 + N, mu* = (beta0 mu0 + N xbar) / beta*,
+ *   [W*]^{-1} = W0^{-1} + N Sbar + (beta0 N / beta*) (mu0 - xbar)(mu0 - xbar)^T.
+ * With N = 0 the posterior equals the prior. */
+int orc_nw_posterior(int K, int64_t N, const double *X, const double *mu0, double beta0, double nu0,
+                     const double *W0, double *xbar, double *Sbar, double *mu_star, double *beta_star,
+                     double *nu_star, double *Wstar_inv)
+{
+    double *work = (double *)malloc(sizeof(double) * ((size_t)2 * K * K + K));
+    if (!work) return ORC_NOMEM;
+    for (int k = 0; k < K; ++k) xbar[k] = 0.0;
+    for (int a = 0; a < K * K; ++a) Sbar[a] = 0.0;
+    if (N > 0) {
+        for (int64_t i = 0; i < N; ++i)
+            for (int k = 0; k < K; ++k) xbar[k] += X[i * K + k];
+        for (int k = 0; k < K; ++k) xbar[k] /= (double)N;
+        for (int64_t i = 0; i < N; ++i)
+            for (int a = 0; a < K; ++a)
+                for (int b = 0; b < K; ++b)
+                    Sbar[a * K + b] += (X[i * K + a] - xbar[a]) * (X[i * K + b] - xbar[b]);
+        for (int a = 0; a < K * K; ++a) Sbar[a] /= (double)N;
+    }
+    double Nd = (double)N;
+    *beta_star = beta0 + Nd;
+    *nu_star = nu0 + Nd;
+    for (int k = 0; k < K; ++k) mu_star[k] = (beta0 * mu0[k] + Nd * xbar[k]) / *beta_star;
+    double *W0inv = work + (size_t)K * K + K; /* after the K*K + K scratch used by spd_inverse */
+    if (spd_inverse(K, W0, W0inv, work)) {
+        free(work);
+        return ORC_NOT_PD;
+    }
+    double c = beta0 * Nd / *beta_star;
+    for (int a = 0; a < K; ++a)
+        for (int b = 0; b < K; ++b)
+            Wstar_inv[a * K + b] = W0inv[a * K + b] + Nd * Sbar[a * K + b]
+                                   + c * (mu0[a] - xbar[a]) * (mu0[b] - xbar[b]);
+    free(work);
+    return ORC_OK;
+}
+
+/* One draw of (mu, Lambda) from the Normal-Wishart posterior:
+ *   Lambda ~ Wishart(W*, nu*) by the Bartlett decomposition on chol(W*) (draws chi2, nrm),
+ *   mu ~ N(mu*, (beta* Lambda)^{-1}) drawn as mu* + chol(beta* Lambda)^{-T} zmu. */
+int orc_nw_draw(int K, const double *mu_star, double beta_star, const double *Wstar_inv,
+                const double *chi2, const double *nrm, const double *zmu, double *mu_out,
+                double *Lam_out)
+{
+    size_t KK = (size_t)K * K;
+    double *w = (double *)malloc(sizeof(double) * (5 * KK + 2 * K));
+    if (!w) return ORC_NOMEM;
+    double *Wst = w, *L = w + KK, *A = w + 2 * KK, *B = w + 3 * KK, *work = w + 4 * KK;
+    double *v = w + 5 * KK + K;
+    int st = spd_inverse(K, Wstar_inv, Wst, work);
+    if (!st) st = chol_lower(K, Wst, L);
+    if (st) {
+        free(w);
+        return ORC_NOT_PD;
+    }
+    /* Bartlett factor A */
+    memset(A, 0, sizeof(double) * KK);
+    for (int k = 0; k < K; ++k) {
+        A[k * K + k] = sqrt(chi2[k]);
+        for (int l = 0; l < k; ++l) A[k * K + l] = nrm[(size_t)k * (k - 1) / 2 + l];
+    }
+    /* B = L A */
+    for (int i = 0; i < K; ++i)
+        for (int j = 0; j < K; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < K; ++k) s += L[i * K + k] * A[k * K + j];
+            B[i * K + j] = s;
+        }
+    /* Lambda = B B^T */
+    for (int i = 0; i < K; ++i)
+        for (int j = 0; j < K; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < K; ++k) s += B[i * K + k] * B[j * K + k];
+            Lam_out[i * K + j] = s;
+        }
+    /* mu = mu* + chol(beta* Lambda)^{-T} zmu */
+    for (int a = 0; a < (int)KK; ++a) A[a] = beta_star * Lam_out[a];
+    if (chol_lower(K, A, L)) {
+        free(w);
+        return ORC_NOT_PD;
+    }
+    for (int k = 0; k < K; ++k) v[k] = zmu[k];
+    solve_lower_t(K, L, v);
+    for (int k = 0; k < K; ++k) mu_out[k] = mu_star[k] + v[k];
+    free(w);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* Row conditionals (the Gibbs update of every x_n given W; Eqs. 2-4).                   */
+/* ------------------------------------------------------------------------------------- */
+
+/* For each row r of a CSR block (ptr/idx/val; idx indexes rows of the partner matrix P):
+ *   Lambda_r = Lambda_p + tau sum_{d in Omega_r} p_d p_d^T,
+ *   b_r      = Lambda_p mu_p + tau sum_{d in Omega_r} y_rd p_d,
+ *   x_r      = Lambda_r^{-1} b_r + L_r^{-T} z_r,   Lambda_r = L_r L_r^T.
+ * The prior (mu_p, Lambda_p) is shared by all rows (per_row_prior = 0: mu_p[K],
+ * Lam_p[K*K]) or given per row (per_row_prior = 1: mu_p[R*K], Lam_p[R*K*K]).
+ * On a non positive definite Lambda_r, *bad_row = r and ORC_NOT_PD is returned. */
+int orc_update_rows(int K, int64_t R, const int64_t *ptr, const int32_t *idx, const double *val,
+                    const double *P, double tau, int per_row_prior, const double *mu_p,
+                    const double *Lam_p, const double *z, double *X_out, int64_t *bad_row)
+{
+    size_t KK = (size_t)K * K;
+    double *w = (double *)malloc(sizeof(double) * (2 * KK + 2 * K));
+    if (!w) return ORC_NOMEM;
+    double *A = w, *L = w + KK, *b = w + 2 * KK;
+    for (int64_t r = 0; r < R; ++r) {
+        const double *mu = per_row_prior ? mu_p + r * K : mu_p;
+        const double *Lam = per_row_prior ? Lam_p + r * (int64_t)KK : Lam_p;
+        for (size_t a = 0; a < KK; ++a) A[a] = Lam[a];
+        for (int i = 0; i < K; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < K; ++j) s += Lam[i * K + j] * mu[j];
+            b[i] = s;
+        }
+        for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) {
+            const double *p = P + (int64_t)idx[e] * K;
+            double y = val[e];
+            for (int i = 0; i < K; ++i) {
+                for (int j = 0; j < K; ++j) A[i * K + j] += tau * p[i] * p[j];
+                b[i] += tau * y * p[i];
+            }
+        }
+        if (chol_lower(K, A, L)) {
+            if (bad_row) *bad_row = r;
+            free(w);
+            return ORC_NOT_PD;
+        }
+        solve_lower(K, L, b);                       /* b <- L^{-1} b            */
+        for (int i = 0; i < K; ++i) b[i] += z[r * K + i]; /* + z                 */
+        solve_lower_t(K, L, b);                     /* x = L^{-T}(L^{-1} b + z) */
+        for (int i = 0; i < K; ++i) X_out[r * K + i] = b[i];
+    }
+    free(w);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* One Gibbs sweep of BPMF on one data subset.                                           */
+/* ------------------------------------------------------------------------------------- */
+
+/* Order within a sweep: (mu_X, Lambda_X) | X, then (mu_W, Lambda_W) | W, then every x_n | W,
+ * then every w_d | X (the new X).  A factor whose prior is propagated from an earlier PP stage
+ * (prior_x / prior_w = 1) keeps that per-row prior and draws no hyperparameters
+ * (Section 5.1); otherwise its hyperparameters are drawn and shared by its rows.
+ * hdraw_* = one hyperparameter draw block (chi2[K], nrm[K(K-1)/2], zmu[K]).
+ * hyper_out receives mu_X[K], Lambda_X[K*K], mu_W[K], Lambda_W[K*K] (unchanged entries
+ * for a propagated factor). */
+int orc_sweep(int K, int64_t N, int64_t D, const int64_t *rptr, const int32_t *ridx,
+              const double *rval, const int64_t *cptr, const int32_t *cidx, const double *cval,
+              double tau, const double *mu0, double beta0, double nu0, const double *W0,
+              int prior_x, const double *muX_row, const double *LamX_row, int prior_w,
+              const double *muW_row, const double *LamW_row, const double *hdraw_x,
+              const double *hdraw_w, const double *zX, const double *zW, double *X, double *W,
+              double *hyper_out, int64_t *bad_row)
+{
+    size_t KK = (size_t)K * K;
+    int st;
+    double *muX = hyper_out, *LamX = hyper_out + K, *muW = hyper_out + K + KK,
+           *LamW = hyper_out + 2 * K + KK;
+    double *w = (double *)malloc(sizeof(double) * (3 * KK + 3 * K));
+    if (!w) return ORC_NOMEM;
+    double *xbar = w, *Sbar = w + K, *mus = w + K + KK, *Wsi = w + 2 * K + KK;
+    double bs, ns;
+    size_t nlow = (size_t)K * (K - 1) / 2;
+    if (!prior_x) {
+        st = orc_nw_posterior(K, N, X, mu0, beta0, nu0, W0, xbar, Sbar, mus, &bs, &ns, Wsi);
+        if (!st) st = orc_nw_draw(K, mus, bs, Wsi, hdraw_x, hdraw_x + K, hdraw_x + K + nlow, muX, LamX);
+        if (st) goto done;
+    }
+    if (!prior_w) {
+        st = orc_nw_posterior(K, D, W, mu0, beta0, nu0, W0, xbar, Sbar, mus, &bs, &ns, Wsi);
+        if (!st) st = orc_nw_draw(K, mus, bs, Wsi, hdraw_w, hdraw_w + K, hdraw_w + K + nlow, muW, LamW);
+        if (st) goto done;
+    }
+    st = orc_update_rows(K, N, rptr, ridx, rval, W, tau, prior_x, prior_x ? muX_row : muX,
+                         prior_x ? LamX_row : LamX, zX, X, bad_row);
+    if (st) goto done;
+    st = orc_update_rows(K, D, cptr, cidx, cval, X, tau, prior_w, prior_w ? muW_row : muW,
+                         prior_w ? LamW_row : LamW, zW, W, bad_row);
+done:
+    free(w);
+    return st;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* Moment matching (Section 4.1, "PP MM").                                               */
+/* ------------------------------------------------------------------------------------- */
+
+/* Running sums over retained samples: S1_r += x_r, S2_r += x_r x_r^T. */
+void orc_moments_accumulate(int K, int64_t R, const double *X, double *S1, double *S2)
+{
+    for (int64_t r = 0; r < R; ++r) {
+        const double *x = X + r * K;
+        for (int i = 0; i < K; ++i) {
+            S1[r * K + i] += x[i];
+            for (int j = 0; j < K; ++j) S2[(r * K + i) * K + j] += x[i] * x[j];
+        }
+    }
+}
+
+/* One Gaussian per row fitted to S retained samples by moment matching:
+ *   m_r = S1_r / S,   Sigma_r = S2_r / S - m_r m_r^T,   Lambda_r = Sigma_r^{-1}. */
+int orc_mm_finalize(int K, int64_t R, int64_t S, const double *S1, const double *S2,
+                    double *mu, double *Lam, int64_t *bad_row)
+{
+    size_t KK = (size_t)K * K;
+    double *w = (double *)malloc(sizeof(double) * (2 * KK + K));
+    if (!w) return ORC_NOMEM;
+    double *Sig = w, *work = w + KK;
+    for (int64_t r = 0; r < R; ++r) {
+        for (int i = 0; i < K; ++i) mu[r * K + i] = S1[r * K + i] / (double)S;
+        for (int i = 0; i < K; ++i)
+            for (int j = 0; j < K; ++j)
+                Sig[i * K + j] = S2[(r * K + i) * K + j] / (double)S - mu[r * K + i] * mu[r * K + j];
+        if (spd_inverse(K, Sig, Lam + r * (int64_t)KK, work)) {
+            if (bad_row) *bad_row = r;
+            free(w);
+            return ORC_NOT_PD;
+        }
+    }
+    free(w);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* Aggregation of the per-row Gaussians (Eq. 14 with the correction of Algorithm 2).     */
+/* ------------------------------------------------------------------------------------- */
+
+/* J submodels hold a Gaussian (mu^(j), Lambda^(j)) for each of R rows; submodel 0 is the
+ * one whose posterior was propagated to the others.  For j = 1..J-1:
+ *   if Lambda^(j) - Lambda^(0) is positive definite: Lambda*^(j) = Lambda^(j);
+ *   else: add |lambda_min| + eps to its diagonal, Lambda*^(j) = corrected + Lambda^(0);
+ * then Lambda* = (2 - J) Lambda^(0) + sum_j Lambda*^(j) and
+ * mu* = Lambda*^{-1} ((2 - J) Lambda^(0) mu^(0) + sum_j Lambda*^(j) mu^(j)).
+ * eps = eps_rel * max(1, mean diagonal of Lambda^(0)).  Positive definiteness is decided by
+ * whether the FP64 Cholesky factorisation has all pivots > 0.
+ * mu: [J][R][K], Lam: [J][R][K][K]; n_corrected counts corrected (row, j) pairs. */
+int orc_aggregate(int K, int64_t R, int J, const double *mu, const double *Lam, double eps_rel,
+                  double *mu_star, double *Lam_star, int64_t *n_corrected, int64_t *bad_row)
+{
+    size_t KK = (size_t)K * K;
+    double *w = (double *)malloc(sizeof(double) * (4 * KK + 2 * K));
+    if (!w) return ORC_NOMEM;
+    double *Dm = w, *L = w + KK, *Lj = w + 2 * KK, *work = w + 3 * KK, *h = w + 4 * KK;
+    int64_t ncorr = 0;
+    for (int64_t r = 0; r < R; ++r) {
+        const double *L0 = Lam + r * (int64_t)KK, *m0 = mu + r * K;
+        double *Ls = Lam_star + r * (int64_t)KK;
+        double c0 = 2.0 - (double)J;
+        double mean_diag = 0.0;
+        for (int i = 0; i < K; ++i) mean_diag += L0[i * K + i];
+        mean_diag /= (double)K;
+        double eps = eps_rel * (mean_diag > 1.0 ? mean_diag : 1.0);
+        for (size_t a = 0; a < KK; ++a) Ls[a] = c0 * L0[a];
+        for (int i = 0; i < K; ++i) {
+            double s = 0.0;
+            for (int k = 0; k < K; ++k) s += L0[i * K + k] * m0[k];
+            h[i] = c0 * s;
+        }
+        for (int j = 1; j < J; ++j) {
+            const double *Lja = Lam + ((int64_t)j * R + r) * (int64_t)KK;
+            const double *mj = mu + ((int64_t)j * R + r) * K;
+            for (size_t a = 0; a < KK; ++a) Dm[a] = Lja[a] - L0[a];
+            if (chol_lower(K, Dm, L) == ORC_OK) {
+                for (size_t a = 0; a < KK; ++a) Lj[a] = Lja[a];
+            } else {
+                double lmin = jacobi_min_eig(K, Dm, work);
+                for (int i = 0; i < K; ++i) Dm[i * K + i] += fabs(lmin) + eps;
+                for (size_t a = 0; a < KK; ++a) Lj[a] = Dm[a] + L0[a];
+                ++ncorr;
+            }
+            for (size_t a = 0; a < KK; ++a) Ls[a] += Lj[a];
+            for (int i = 0; i < K; ++i) {
+                double s = 0.0;
+                for (int k = 0; k < K; ++k) s += Lj[i * K + k] * mj[k];
+                h[i] += s;
+            }
+        }
+        if (chol_lower(K, Ls, L)) {
+            if (bad_row) *bad_row = r;
+            free(w);
+            return ORC_NOT_PD;
+        }
+        solve_lower(K, L, h);
+        solve_lower_t(K, L, h);
+        for (int i = 0; i < K; ++i) mu_star[r * K + i] = h[i];
+    }
+    if (n_corrected) *n_corrected = ncorr;
+    free(w);
+    return ORC_OK;
+}
+
+/* Smallest eigenvalue (exposed for the tests of the correction step). */
+double orc_min_eig(int K, const double *M)
+{
+    double *a = (double *)malloc(sizeof(double) * (size_t)K * K);
+    if (!a) return NAN;
+    double m = jacobi_min_eig(K, M, a);
+    free(a);
+    return m;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* Prediction with posterior means (Section 5.2: Eq. 1 with the means of X and W).       */
+/* ------------------------------------------------------------------------------------- */
+
+void orc_predict(int K, int64_t n, const int32_t *row, const int32_t *col, const double *Xm,
+                 const double *Wm, double offset, double *yhat)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) s += Xm[(int64_t)row[i] * K + k] * Wm[(int64_t)col[i] * K + k];
+        yhat[i] = offset + s;
+    }
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* Masked log-joint and its gradient (the differentiation extension).                    */
+/* ------------------------------------------------------------------------------------- */
+
+/* l(X, W, log a) = -(a/2) sum_{(n,d) in Omega} (y_nd - x_n^T w_d)^2 + (|Omega|/2) log a
+ *                  - 1/2 sum_n (x_n - mu_X)^T Lambda_X (x_n - mu_X)
+ *                  - 1/2 sum_d (w_d - mu_W)^T Lambda_W (w_d - mu_W)        (constants dropped)
+ * grad_x_n = a sum_{d in Omega_n} r_nd w_d - Lambda_X (x_n - mu_X),   r_nd = y_nd - x_n^T w_d,
+ * grad_w_d = a sum_{n in Omega_d} r_nd x_n - Lambda_W (w_d - mu_W),
+ * dl/dlog a = |Omega|/2 - (a/2) sum r^2.
+ * Observations are given in COO form. */
+void orc_logjoint_grad(int K, int64_t N, int64_t D, int64_t nnz, const int32_t *row,
+                       const int32_t *col, const double *val, const double *X, const double *W,
+                       double log_a, const double *muX, const double *LamX, const double *muW,
+                       const double *LamW, double *gX, double *gW, double *g_log_a, double *value)
+{
+    double a = exp(log_a);
+    double sse = 0.0;
+    for (int64_t i = 0; i < N * K; ++i) gX[i] = 0.0;
+    for (int64_t i = 0; i < D * K; ++i) gW[i] = 0.0;
+    for (int64_t e = 0; e < nnz; ++e) {
+        const double *x = X + (int64_t)row[e] * K, *w = W + (int64_t)col[e] * K;
+        double p = 0.0;
+        for (int k = 0; k < K; ++k) p += x[k] * w[k];
+        double r = val[e] - p;
+        sse += r * r;
+        for (int k = 0; k < K; ++k) {
+            gX[(int64_t)row[e] * K + k] += a * r * w[k];
+            gW[(int64_t)col[e] * K + k] += a * r * x[k];
+        }
+    }
+    double quad = 0.0;
+    for (int64_t n = 0; n < N; ++n)
+        for (int i = 0; i < K; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < K; ++j) s += LamX[i * K + j] * (X[n * K + j] - muX[j]);
+            gX[n * K + i] -= s;
+            quad += (X[n * K + i] - muX[i]) * s;
+        }
+    for (int64_t d = 0; d < D; ++d)
+        for (int i = 0; i < K; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < K; ++j) s += LamW[i * K + j] * (W[d * K + j] - muW[j]);
+            gW[d * K + i] -= s;
+            quad += (W[d * K + i] - muW[i]) * s;
+        }
+    *g_log_a = 0.5 * (double)nnz - 0.5 * a * sse;
+    *value = -0.5 * a * sse + 0.5 * (double)nnz * log_a - 0.5 * quad;
+}
