@@ -196,7 +196,7 @@ bmf_status bmf_set_prior(bmf_ctx *ctx, int32_t subset, int32_t factor, const dou
                          const double *Lam);
 
 /* Grid geometry of one subset, and the reordering (new -> original index) of rows/columns. */
-bmf_status bmf_subset_info(const bmf_ctx *ctx, int32_t subset, bmf_subset_info *info);
+bmf_status bmf_get_subset_info(const bmf_ctx *ctx, int32_t subset, bmf_subset_info *info);
 bmf_status bmf_get_perm(const bmf_ctx *ctx, int64_t *row_perm, int64_t *col_perm);
 
 void bmf_destroy(bmf_ctx *ctx);

@@ -1,0 +1,1061 @@
+// api.cu -- the C ABI of libbmf (include/bmf.h) and the runtime behind it: the context, its
+// device arenas, the batched sweep of a stage (Algorithm 1), the stage transitions with
+// propagated priors and the final aggregation (Eq. 14, Algorithm 2).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/bmf.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "plan.h"
+
+using namespace bmf;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+struct DevMem {
+    std::vector<void *> ptrs;
+    bool ok = true;
+    template <typename T>
+    T *alloc(size_t n)
+    {
+        if (n == 0) n = 1;
+        void *p = nullptr;
+        if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) {
+            ok = false;
+            return nullptr;
+        }
+        ptrs.push_back(p);
+        return static_cast<T *>(p);
+    }
+    ~DevMem()
+    {
+        for (void *p : ptrs) cudaFree(p);
+    }
+};
+
+// One factor arena (all subsets' blocks of X, or of W, stacked in slot order) with the
+// observation lists of its rows (partners in the other arena).
+struct Side {
+    int64_t R = 0;
+    double *F = nullptr;         // FP64 state [R x K]
+    void *G = nullptr;           // gathered copy [R x ldg]
+    int64_t *ptr = nullptr;      // observation list offsets [R+1]
+    int32_t *idx = nullptr;      // partner arena rows
+    void *val = nullptr;         // values (double or float)
+    GramItem *items = nullptr;   // Gram work items in arena-row order
+    int64_t *item_ptr = nullptr; // [R+1]
+    std::vector<int64_t> h_item_ptr;
+    int32_t *hslot = nullptr;    // [R] hyper slot or -1
+    std::vector<int32_t> h_hslot;
+    double *pL = nullptr, *pb = nullptr;            // per-row prior (SoA)
+    double *S1 = nullptr, *S2 = nullptr;            // moment sums (SoA)
+    double *mm_mu = nullptr, *mm_L = nullptr, *mm_b = nullptr;  // moment-matched posterior
+};
+
+struct SubState {
+    int64_t t = 0, kept = 0;
+    int prior[2] = {0, 0};  // 1: factor has a per-row (propagated or installed) prior
+    bool finalized = false;
+};
+
+}  // namespace
+
+struct bmf_ctx {
+    int K = 0, prec = BMF_FP64;
+    double tau = 1.0, beta0 = 2.0, nu0 = 1.0, eps_rel = 1e-6;
+    int burnin = 0, thin = 1;
+    uint64_t seed = 0;
+    std::vector<double> mu0, W0inv;
+    HostPlan P;
+    cudaStream_t st = nullptr;
+    int device = 0, sms = 1;
+    DevMem mem;
+    Side X, W;
+    int ldg = 0, ld_part = 0, part_rhs = 0;
+    void *part = nullptr;
+    int64_t part_cap = 0;            // items
+    double *hyper = nullptr;         // [2 * S slots]
+    double *stats = nullptr;
+    int64_t stats_cap = 0;           // chunks
+    StatChunk *d_chunks = nullptr;
+    HyperJob *d_jobs = nullptr;
+    double *mu0_d = nullptr, *W0inv_d = nullptr;
+    int32_t *trow = nullptr, *tcol = nullptr;
+    double *tval = nullptr, *ysum = nullptr;
+    double *rmse_part = nullptr, *rmse_out = nullptr;
+    int rmse_blocks = 64;
+    DevError *err_d = nullptr;
+    double *draws_d = nullptr;
+    int64_t draws_cap = 0;
+    double *aggX = nullptr, *aggW = nullptr;   // aggregated means, reordered order
+    unsigned long long *ncorr_d = nullptr;
+    std::vector<SubState> ss;
+    int stage_open = 0;
+    bool failed = false;
+    std::string err;
+    int chunk_obs = 1024;
+    int stat_rows = 512;
+};
+
+namespace {
+
+constexpr int kHyperJobsMax = 1 << 16;
+
+bmf_status fail(bmf_ctx *c, bmf_status s, const std::string &m)
+{
+    c->err = m;
+    return s;
+}
+
+bmf_status cuda_fail(bmf_ctx *c, cudaError_t e, const char *where)
+{
+    c->err = std::string("CUDA error in ") + where + ": " + cudaGetErrorString(e);
+    return BMF_E_CUDA;
+}
+
+#define CUDA_TRY(c, call)                                         \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail((c), e_, #call); \
+    } while (0)
+
+int64_t hyper_block_len(int K) { return K + (int64_t)K * (K - 1) / 2 + K; }
+
+// Host FP64 inverse of a small SPD matrix (Gauss-Jordan with partial pivoting).
+bool host_inverse(int K, const std::vector<double> &A, std::vector<double> &Ainv)
+{
+    std::vector<double> a(A);
+    Ainv.assign((size_t)K * K, 0.0);
+    for (int i = 0; i < K; ++i) Ainv[i * K + i] = 1.0;
+    for (int c = 0; c < K; ++c) {
+        int p = c;
+        for (int r = c + 1; r < K; ++r)
+            if (std::fabs(a[r * K + c]) > std::fabs(a[p * K + c])) p = r;
+        if (!(std::fabs(a[p * K + c]) > 0.0)) return false;
+        if (p != c)
+            for (int k = 0; k < K; ++k) {
+                std::swap(a[p * K + k], a[c * K + k]);
+                std::swap(Ainv[p * K + k], Ainv[c * K + k]);
+            }
+        double d = a[c * K + c];
+        for (int k = 0; k < K; ++k) {
+            a[c * K + k] /= d;
+            Ainv[c * K + k] /= d;
+        }
+        for (int r = 0; r < K; ++r)
+            if (r != c) {
+                double f = a[r * K + c];
+                if (f == 0.0) continue;
+                for (int k = 0; k < K; ++k) {
+                    a[r * K + k] -= f * a[c * K + k];
+                    Ainv[r * K + k] -= f * Ainv[c * K + k];
+                }
+            }
+    }
+    for (int i = 0; i < K; ++i)
+        for (int j = 0; j < i; ++j) {
+            double m = 0.5 * (Ainv[i * K + j] + Ainv[j * K + i]);
+            Ainv[i * K + j] = Ainv[j * K + i] = m;
+        }
+    return true;
+}
+
+const SubsetGeom &geom_of_slot(const bmf_ctx *c, int sl) { return c->P.subs[c->P.slot_sid[sl]]; }
+
+// Slot range [sl0, sl1) of a stage (slots are sorted by stage).
+bool stage_slots(const bmf_ctx *c, int stage, int &sl0, int &sl1)
+{
+    int S = (int)c->P.slot_sid.size();
+    sl0 = sl1 = -1;
+    for (int sl = 0; sl < S; ++sl)
+        if (geom_of_slot(c, sl).stage == stage) {
+            if (sl0 < 0) sl0 = sl;
+            sl1 = sl + 1;
+        }
+    return sl0 >= 0;
+}
+
+int64_t per_sweep_draws(const bmf_ctx *c, int sl0, int sl1)
+{
+    int64_t n = 2 * (int64_t)(sl1 - sl0) * hyper_block_len(c->K);
+    for (int sl = sl0; sl < sl1; ++sl) n += (geom_of_slot(c, sl).n() + geom_of_slot(c, sl).d()) * c->K;
+    return n;
+}
+
+void refresh_hslots(bmf_ctx *c, int sl)
+{
+    const SubsetGeom &g = geom_of_slot(c, sl);
+    SubState &s = c->ss[g.sid];
+    for (int64_t r = 0; r < g.n(); ++r) c->X.h_hslot[g.xoff + r] = s.prior[0] ? -1 : 2 * sl + 0;
+    for (int64_t r = 0; r < g.d(); ++r) c->W.h_hslot[g.woff + r] = s.prior[1] ? -1 : 2 * sl + 1;
+}
+
+bmf_status upload_hslots(bmf_ctx *c, int sl)
+{
+    const SubsetGeom &g = geom_of_slot(c, sl);
+    if (g.n() > 0)
+        CUDA_TRY(c, cudaMemcpyAsync(c->X.hslot + g.xoff, c->X.h_hslot.data() + g.xoff,
+                                    g.n() * sizeof(int32_t), cudaMemcpyHostToDevice, c->st));
+    if (g.d() > 0)
+        CUDA_TRY(c, cudaMemcpyAsync(c->W.hslot + g.woff, c->W.h_hslot.data() + g.woff,
+                                    g.d() * sizeof(int32_t), cudaMemcpyHostToDevice, c->st));
+    return BMF_OK;
+}
+
+bmf_status check_dev_error(bmf_ctx *c)
+{
+    DevError h;
+    CUDA_TRY(c, cudaMemcpyAsync(&h, c->err_d, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    if (h.flags) {
+        DevError z = {0u, INT32_MAX};
+        cudaMemcpy(c->err_d, &z, sizeof(z), cudaMemcpyHostToDevice);
+        c->failed = true;
+        if (h.flags & ERR_NOT_PD)
+            return fail(c, BMF_E_NOT_PD,
+                        "matrix not positive definite (arena row " +
+                            std::to_string(h.first_bad_row) + "); the context must be reset "
+                            "with bmf_set_state before further sweeps");
+        return fail(c, BMF_E_CUDA, "device error flags " + std::to_string(h.flags));
+    }
+    return BMF_OK;
+}
+
+// One factor's observation lists -> device (values converted to the gather precision) and the
+// Gram work items of every arena row (rows longer than chunk_obs are split).
+bmf_status setup_side(bmf_ctx *c, Side &s, int64_t R, const std::vector<int64_t> &ptr,
+                      const std::vector<int32_t> &idx, const std::vector<double> &val)
+{
+    s.R = R;
+    const int64_t nnz = (int64_t)idx.size();
+    s.ptr = c->mem.alloc<int64_t>(R + 1);
+    s.idx = c->mem.alloc<int32_t>(nnz);
+    if (c->prec == BMF_FP64)
+        s.val = c->mem.alloc<double>(nnz);
+    else
+        s.val = c->mem.alloc<float>(nnz);
+    if (!c->mem.ok) return fail(c, BMF_E_OOM, "device allocation failed (observation lists)");
+    CUDA_TRY(c, cudaMemcpy(s.ptr, ptr.data(), (R + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    if (nnz) {
+        CUDA_TRY(c, cudaMemcpy(s.idx, idx.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
+        if (c->prec == BMF_FP64) {
+            CUDA_TRY(c, cudaMemcpy(s.val, val.data(), nnz * sizeof(double), cudaMemcpyHostToDevice));
+        } else {
+            std::vector<float> f(val.begin(), val.end());
+            CUDA_TRY(c, cudaMemcpy(s.val, f.data(), nnz * sizeof(float), cudaMemcpyHostToDevice));
+        }
+    }
+    std::vector<GramItem> items;
+    s.h_item_ptr.assign(R + 1, 0);
+    for (int64_t r = 0; r < R; ++r) {
+        s.h_item_ptr[r] = (int64_t)items.size();
+        int64_t b = ptr[r], e = ptr[r + 1];
+        for (int64_t q = b; q < e; q += c->chunk_obs) {
+            GramItem it;
+            it.begin = q;
+            it.count = (int32_t)std::min<int64_t>(c->chunk_obs, e - q);
+            it.row = (int32_t)r;
+            items.push_back(it);
+        }
+    }
+    s.h_item_ptr[R] = (int64_t)items.size();
+    s.items = c->mem.alloc<GramItem>(items.size());
+    s.item_ptr = c->mem.alloc<int64_t>(R + 1);
+    if (!c->mem.ok) return fail(c, BMF_E_OOM, "device allocation failed (work items)");
+    if (!items.empty())
+        CUDA_TRY(c, cudaMemcpy(s.items, items.data(), items.size() * sizeof(GramItem),
+                               cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(s.item_ptr, s.h_item_ptr.data(), (R + 1) * sizeof(int64_t),
+                           cudaMemcpyHostToDevice));
+    c->part_cap = std::max<int64_t>(c->part_cap, (int64_t)items.size());
+    // state, copies, priors, moments
+    const int K = c->K;
+    const int NT = ntri(K);
+    s.F = c->mem.alloc<double>(R * K);
+    size_t gbytes = c->prec == BMF_FP64 ? 8 : (c->prec == BMF_FP32 ? 4 : 2);
+    s.G = c->mem.alloc<char>(R * c->ldg * gbytes);
+    s.hslot = c->mem.alloc<int32_t>(R);
+    s.h_hslot.assign(R, -1);
+    s.pL = c->mem.alloc<double>(R * NT);
+    s.pb = c->mem.alloc<double>(R * K);
+    s.S1 = c->mem.alloc<double>(R * K);
+    s.S2 = c->mem.alloc<double>(R * NT);
+    s.mm_mu = c->mem.alloc<double>(R * K);
+    s.mm_L = c->mem.alloc<double>(R * NT);
+    s.mm_b = c->mem.alloc<double>(R * K);
+    if (!c->mem.ok) return fail(c, BMF_E_OOM, "device allocation failed (factor arena)");
+    CUDA_TRY(c, cudaMemset(s.S1, 0, R * K * sizeof(double)));
+    CUDA_TRY(c, cudaMemset(s.S2, 0, R * NT * sizeof(double)));
+    CUDA_TRY(c, cudaMemset(s.pL, 0, R * NT * sizeof(double)));
+    CUDA_TRY(c, cudaMemset(s.pb, 0, R * K * sizeof(double)));
+    return BMF_OK;
+}
+
+// Draw buffer of a call on the device.
+bmf_status stage_draws(bmf_ctx *c, const bmf_draws *d, int64_t need, const double **out)
+{
+    if (!d) return fail(c, BMF_E_ARG, "draws == NULL: the device generator is not available in this build");
+    if (!d->ptr || d->len != need)
+        return fail(c, BMF_E_SHAPE, "draw buffer has " + std::to_string(d->len) +
+                                        " doubles, expected " + std::to_string(need));
+    if (d->on_device) {
+        *out = d->ptr;
+        return BMF_OK;
+    }
+    if (need > c->draws_cap) {
+        if (c->draws_d) cudaFree(c->draws_d);
+        c->draws_d = nullptr;
+        c->draws_cap = 0;
+        if (cudaMalloc(&c->draws_d, need * sizeof(double)) != cudaSuccess)
+            return fail(c, BMF_E_OOM, "device allocation failed (draw buffer)");
+        c->draws_cap = need;
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->draws_d, d->ptr, need * sizeof(double), cudaMemcpyHostToDevice,
+                                c->st));
+    *out = c->draws_d;
+    return BMF_OK;
+}
+
+bool keep_sample(const bmf_ctx *c, int64_t t)
+{
+    return t > c->burnin && (t - c->burnin - 1) % c->thin == 0;
+}
+
+// n sweeps of the subsets in slots [sl0, sl1) (a stage, or one subset), batched.
+bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws *draws,
+                     bmf_sweep_stats *stats)
+{
+    if (c->failed) return fail(c, BMF_E_STATE, "context is in a failed state; call bmf_set_state");
+    if (n_sweeps < 0) return fail(c, BMF_E_ARG, "n_sweeps < 0");
+    const int K = c->K;
+    const SubsetGeom &g0 = geom_of_slot(c, sl0), &gl = geom_of_slot(c, sl1 - 1);
+    const int64_t t_start = c->ss[g0.sid].t;
+    for (int sl = sl0; sl < sl1; ++sl)
+        if (c->ss[geom_of_slot(c, sl).sid].t != t_start)
+            return fail(c, BMF_E_STATE, "subsets of the batch are at different sweep counts");
+    const int64_t rx0 = g0.xoff, rx1 = gl.xoff + gl.n();
+    const int64_t rw0 = g0.woff, rw1 = gl.woff + gl.d();
+    const int64_t tt0 = g0.test_off, tt1 = gl.test_off + gl.n_test;
+    const int64_t per = per_sweep_draws(c, sl0, sl1);
+    const double *dr = nullptr;
+    bmf_status s = stage_draws(c, draws, per * n_sweeps, &dr);
+    if (s) return s;
+    // hyperparameter jobs: every factor block without a per-row prior
+    std::vector<StatChunk> chunks;
+    std::vector<HyperJob> jobs;
+    const int64_t HB = hyper_block_len(K);
+    for (int sl = sl0; sl < sl1; ++sl) {
+        const SubsetGeom &g = geom_of_slot(c, sl);
+        const SubState &su = c->ss[g.sid];
+        for (int f = 0; f < 2; ++f) {
+            if (su.prior[f]) continue;
+            const int64_t base = f == 0 ? g.xoff : g.woff, n = f == 0 ? g.n() : g.d();
+            HyperJob jb;
+            jb.chunk0 = (int32_t)chunks.size();
+            for (int64_t r = 0; r < n; r += c->stat_rows) {
+                StatChunk ch;
+                ch.r0 = base + r;
+                ch.r1 = base + std::min<int64_t>(n, r + c->stat_rows);
+                ch.out = (int32_t)chunks.size();
+                ch.arena = f;
+                chunks.push_back(ch);
+            }
+            jb.chunk1 = (int32_t)chunks.size();
+            jb.slot = 2 * sl + f;
+            jb.draw = (int32_t)((2 * (sl - sl0) + f) * HB);
+            jb.n = n;
+            jobs.push_back(jb);
+        }
+    }
+    if ((int64_t)chunks.size() > c->stats_cap || (int64_t)jobs.size() > kHyperJobsMax)
+        return fail(c, BMF_E_ARG, "internal: statistics buffers too small");
+    if (!chunks.empty())
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_chunks, chunks.data(), chunks.size() * sizeof(StatChunk),
+                                    cudaMemcpyHostToDevice, c->st));
+    if (!jobs.empty())
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_jobs, jobs.data(), jobs.size() * sizeof(HyperJob),
+                                    cudaMemcpyHostToDevice, c->st));
+    const int64_t hyper_len = 2 * (int64_t)(sl1 - sl0) * HB;
+    const int64_t zx_len = (rx1 - rx0) * K;
+    int64_t kept = c->ss[g0.sid].kept;
+    for (int it = 0; it < n_sweeps; ++it) {
+        const double *d = dr + (int64_t)it * per;
+        const int64_t t = t_start + it + 1;
+        const bool keep = keep_sample(c, t);
+        if (keep) ++kept;
+        // (mu, Lambda) | X and (mu, Lambda) | W from the state at the start of the sweep
+        launch_stats(K, c->d_chunks, (int)chunks.size(), c->X.F, c->W.F, c->stats, c->st);
+        HyperParams hp{K, c->d_jobs, (int)jobs.size(), c->stats, c->mu0_d, c->beta0, c->nu0,
+                       c->W0inv_d, d, c->hyper, c->err_d};
+        launch_hyper(hp, c->st);
+        // X | W, then W | X
+        for (int f = 0; f < 2; ++f) {
+            Side &me = f == 0 ? c->X : c->W;
+            Side &other = f == 0 ? c->W : c->X;
+            const int64_t r0 = f == 0 ? rx0 : rw0, r1 = f == 0 ? rx1 : rw1;
+            const int64_t i0 = me.h_item_ptr[r0], i1 = me.h_item_ptr[r1];
+            GramParams gp{me.items + i0, i1 - i0, me.idx, me.val, other.G, c->ldg, c->part,
+                          c->ld_part};
+            launch_gram(K, c->prec, gp, c->sms * 4, c->st);
+            CondParams cp;
+            cp.K = K;
+            cp.row0 = r0;
+            cp.row1 = r1;
+            cp.item_ptr = me.item_ptr;
+            cp.item0 = i0;
+            cp.part = c->part;
+            cp.ld = c->ld_part;
+            cp.part_rhs = ntri(padded_k(K));
+            cp.tau = c->tau;
+            cp.row_hslot = me.hslot;
+            cp.hyper = c->hyper;
+            cp.prior_L = me.pL;
+            cp.prior_b = me.pb;
+            cp.R = me.R;
+            cp.z = d + hyper_len + (f == 0 ? 0 : zx_len);
+            cp.X = me.F;
+            cp.Xg = me.G;
+            cp.ldg = c->ldg;
+            cp.keep = keep ? 1 : 0;
+            cp.S1 = me.S1;
+            cp.S2 = me.S2;
+            cp.err = c->err_d;
+            launch_cond(c->prec, cp, c->st);
+        }
+        if (tt1 > tt0) {
+            RmseParams rp{K, c->prec, tt0, tt1, c->trow, c->tcol, c->tval, c->X.G, c->W.G, c->ldg,
+                          keep ? 1 : 0, c->ysum, (double)kept, c->rmse_part};
+            launch_rmse(rp, c->rmse_blocks, c->st);
+            launch_rmse_final(c->rmse_part, c->rmse_blocks, c->rmse_out, c->st);
+        }
+    }
+    CUDA_TRY(c, cudaGetLastError());
+    for (int sl = sl0; sl < sl1; ++sl) {
+        SubState &su = c->ss[geom_of_slot(c, sl).sid];
+        su.t = t_start + n_sweeps;
+        su.kept = kept;
+        su.finalized = false;
+    }
+    s = check_dev_error(c);
+    if (s) return s;
+    if (stats) {
+        stats->sweeps = t_start + n_sweeps;
+        stats->kept = kept;
+        stats->rmse_sample = stats->rmse_mean = NAN;
+        if (tt1 > tt0 && n_sweeps > 0) {
+            double h[2];
+            CUDA_TRY(c, cudaMemcpy(h, c->rmse_out, sizeof(h), cudaMemcpyDeviceToHost));
+            const double n = (double)(tt1 - tt0);
+            stats->rmse_sample = std::sqrt(h[0] / n);
+            if (kept > 0) stats->rmse_mean = std::sqrt(h[1] / n);
+        }
+    }
+    return BMF_OK;
+}
+
+// Moment matching of every subset of a stage (the propagated summaries, Section 4.1).
+bmf_status finalize_stage(bmf_ctx *c, int stage)
+{
+    int sl0, sl1;
+    if (!stage_slots(c, stage, sl0, sl1)) return BMF_OK;
+    for (int sl = sl0; sl < sl1; ++sl) {
+        const SubsetGeom &g = geom_of_slot(c, sl);
+        SubState &su = c->ss[g.sid];
+        if (su.finalized) continue;
+        if (su.kept < 1)
+            return fail(c, BMF_E_STATE, "subset " + std::to_string(g.sid) +
+                                            " has no retained samples (burn-in not passed)");
+        for (int f = 0; f < 2; ++f) {
+            Side &sd = f == 0 ? c->X : c->W;
+            MMParams mp{c->K, f == 0 ? g.xoff : g.woff,
+                        f == 0 ? g.xoff + g.n() : g.woff + g.d(), sd.R, sd.S1, sd.S2,
+                        (double)su.kept, sd.mm_mu, sd.mm_L, sd.mm_b, c->err_d};
+            launch_mm(mp, c->st);
+        }
+        su.finalized = true;
+    }
+    CUDA_TRY(c, cudaGetLastError());
+    return check_dev_error(c);
+}
+
+bmf_status install_prior_from(bmf_ctx *c, int dst_sid, int f, int src_sid)
+{
+    const SubsetGeom &gd = c->P.subs[dst_sid], &gs = c->P.subs[src_sid];
+    Side &sd = f == 0 ? c->X : c->W;
+    const int64_t n = f == 0 ? gd.n() : gd.d();
+    PropParams pp{c->K, n, f == 0 ? gs.xoff : gs.woff, f == 0 ? gd.xoff : gd.woff, sd.R,
+                  sd.mm_mu, sd.mm_L, sd.mm_b, sd.pL, sd.pb, sd.F, sd.G, c->ldg, c->prec};
+    launch_propagate(pp, c->st);
+    c->ss[dst_sid].prior[f] = 1;
+    refresh_hslots(c, gd.slot);
+    return upload_hslots(c, gd.slot);
+}
+
+// Open `stage` (Algorithm 1): finalise the previous stage and install the propagated priors.
+bmf_status open_stage(bmf_ctx *c, int stage)
+{
+    if (stage == c->stage_open) return BMF_OK;
+    if (stage != c->stage_open + 1)
+        return fail(c, BMF_E_STATE, "stages must be opened in order (open: " +
+                                        std::to_string(c->stage_open) + ", requested: " +
+                                        std::to_string(stage) + ")");
+    int sl0, sl1;
+    if (!stage_slots(c, stage, sl0, sl1))
+        return fail(c, BMF_E_STATE, "stage " + std::to_string(stage) + " has no subsets");
+    if (stage > 1) {
+        bmf_status s = finalize_stage(c, stage - 1);
+        if (s) return s;
+        const int J = c->P.J;
+        for (int sl = sl0; sl < sl1; ++sl) {
+            const SubsetGeom &g = geom_of_slot(c, sl);
+            if (stage == 2) {
+                if (g.j == 0)
+                    s = install_prior_from(c, g.sid, 1, 0);      // W^(0) from (0,0)
+                else
+                    s = install_prior_from(c, g.sid, 0, 0);      // X^(0) from (0,0)
+            } else {
+                s = install_prior_from(c, g.sid, 0, g.i * J);    // X^(i) from (i,0)
+                if (!s) s = install_prior_from(c, g.sid, 1, g.j);  // W^(j) from (0,j)
+            }
+            if (s) return s;
+        }
+        CUDA_TRY(c, cudaGetLastError());
+        CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    }
+    c->stage_open = stage;
+    return BMF_OK;
+}
+
+int last_stage(const bmf_ctx *c)
+{
+    int m = 0;
+    for (const auto &g : c->P.subs) m = std::max(m, g.stage);
+    return m;
+}
+
+// Aggregated means (reordered order) into c->aggX / c->aggW.
+bmf_status aggregate_all(bmf_ctx *c, int64_t *n_corrected)
+{
+    if (c->stage_open != last_stage(c))
+        return fail(c, BMF_E_STATE, "every stage must be run before prediction");
+    bmf_status s = BMF_OK;
+    const int I = c->P.I, J = c->P.J, K = c->K;
+    bool single = (I == 1 && J == 1);
+    if (!single) {
+        s = finalize_stage(c, c->stage_open);
+        if (s) return s;
+    }
+    CUDA_TRY(c, cudaMemsetAsync(c->ncorr_d, 0, sizeof(unsigned long long), c->st));
+    std::vector<int64_t> base;
+    int64_t *base_d = c->mem.alloc<int64_t>(std::max(I, J));
+    if (!base_d) return fail(c, BMF_E_OOM, "device allocation failed");
+    for (int f = 0; f < 2; ++f) {
+        Side &sd = f == 0 ? c->X : c->W;
+        const int nb = f == 0 ? I : J, ns = f == 0 ? J : I;
+        for (int b = 0; b < nb; ++b) {
+            base.clear();
+            for (int q = 0; q < ns; ++q) {
+                const SubsetGeom &g = f == 0 ? c->P.subs[b * J + q] : c->P.subs[q * J + b];
+                base.push_back(f == 0 ? g.xoff : g.woff);
+            }
+            const SubsetGeom &g0 = f == 0 ? c->P.subs[b * J] : c->P.subs[b];
+            const int64_t n = f == 0 ? g0.n() : g0.d();
+            const int64_t out0 = f == 0 ? g0.r0 : g0.c0;
+            double *out = (f == 0 ? c->aggX : c->aggW) + out0 * K;
+            if (ns == 1) {
+                // one submodel: the posterior mean is the mean of the retained samples
+                const SubState &su = c->ss[g0.sid];
+                if (su.kept < 1) return fail(c, BMF_E_STATE, "no retained samples");
+                std::vector<double> S1((size_t)n * K), m((size_t)n * K);
+                for (int k = 0; k < K; ++k)
+                    if (n)
+                        CUDA_TRY(c, cudaMemcpy(S1.data() + (size_t)k * n, sd.S1 + (int64_t)k * sd.R + base[0],
+                                               n * sizeof(double), cudaMemcpyDeviceToHost));
+                for (int64_t r = 0; r < n; ++r)
+                    for (int k = 0; k < K; ++k) m[r * K + k] = S1[(size_t)k * n + r] / (double)su.kept;
+                if (n) CUDA_TRY(c, cudaMemcpy(out, m.data(), n * K * sizeof(double), cudaMemcpyHostToDevice));
+                continue;
+            }
+            CUDA_TRY(c, cudaMemcpyAsync(base_d, base.data(), ns * sizeof(int64_t),
+                                        cudaMemcpyHostToDevice, c->st));
+            AggParams ap{K, n, ns, base_d, sd.mm_mu, sd.mm_L, sd.R, c->eps_rel, out, c->ncorr_d,
+                         c->err_d};
+            launch_aggregate(ap, c->st);
+            CUDA_TRY(c, cudaStreamSynchronize(c->st));
+        }
+    }
+    CUDA_TRY(c, cudaGetLastError());
+    s = check_dev_error(c);
+    if (s) return s;
+    if (n_corrected) {
+        unsigned long long h = 0;
+        CUDA_TRY(c, cudaMemcpy(&h, c->ncorr_d, sizeof(h), cudaMemcpyDeviceToHost));
+        *n_corrected = (int64_t)h;
+    }
+    return BMF_OK;
+}
+
+// Aggregated means in the ORIGINAL order on the host.
+bmf_status means_original(bmf_ctx *c, std::vector<double> &Xm, std::vector<double> &Wm,
+                          int64_t *n_corrected)
+{
+    bmf_status s = aggregate_all(c, n_corrected);
+    if (s) return s;
+    const int K = c->K;
+    std::vector<double> xr((size_t)c->P.N * K), wr((size_t)c->P.D * K);
+    CUDA_TRY(c, cudaMemcpy(xr.data(), c->aggX, xr.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    CUDA_TRY(c, cudaMemcpy(wr.data(), c->aggW, wr.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    Xm.assign(xr.size(), 0.0);
+    Wm.assign(wr.size(), 0.0);
+    for (int64_t k = 0; k < c->P.N; ++k)
+        std::memcpy(&Xm[(size_t)c->P.row_perm[k] * K], &xr[(size_t)k * K], K * sizeof(double));
+    for (int64_t k = 0; k < c->P.D; ++k)
+        std::memcpy(&Wm[(size_t)c->P.col_perm[k] * K], &wr[(size_t)k * K], K * sizeof(double));
+    return BMF_OK;
+}
+
+bool valid_subset(const bmf_ctx *c, int32_t s) { return s >= 0 && s < (int32_t)c->P.subs.size(); }
+
+}  // namespace
+
+// ==========================================================================================
+// C ABI
+// ==========================================================================================
+extern "C" {
+
+bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, int64_t nnz,
+                    const int32_t *row, const int32_t *col, const double *val, int32_t I,
+                    const int64_t *row_bounds, int32_t J, const int64_t *col_bounds,
+                    const double *X0, const double *W0init, int64_t n_test,
+                    const int32_t *test_row, const int32_t *test_col, const double *test_val,
+                    void *stream)
+{
+    g_init_error.clear();
+    if (!out || !cfg || !X0 || !W0init) {
+        g_init_error = "null argument";
+        return BMF_E_ARG;
+    }
+    *out = nullptr;
+    const int K = cfg->K;
+    if (K < 1 || K > 16) {
+        g_init_error = "K must be in 1..16 in this build";
+        return BMF_E_ARG;
+    }
+    if (cfg->precision < BMF_FP64 || cfg->precision > BMF_BF16) {
+        g_init_error = "unknown precision";
+        return BMF_E_ARG;
+    }
+    if (!(cfg->tau > 0) || !(cfg->beta0 > 0) || cfg->thin < 1 || cfg->burnin < 0) {
+        g_init_error = "need tau > 0, beta0 > 0, thin >= 1, burnin >= 0";
+        return BMF_E_ARG;
+    }
+    double nu0 = cfg->nu0 > 0 ? cfg->nu0 : (double)K;
+    if (!(nu0 > K - 1)) {
+        g_init_error = "need nu0 > K - 1";
+        return BMF_E_ARG;
+    }
+    bmf_ctx *c = new bmf_ctx();
+    c->K = K;
+    c->prec = cfg->precision;
+    c->tau = cfg->tau;
+    c->beta0 = cfg->beta0;
+    c->nu0 = nu0;
+    c->eps_rel = cfg->eps_rel > 0 ? cfg->eps_rel : 1e-6;
+    c->burnin = cfg->burnin;
+    c->thin = cfg->thin;
+    c->seed = cfg->seed;
+    c->st = static_cast<cudaStream_t>(stream);
+    c->mu0.assign(K, 0.0);
+    if (cfg->mu0) std::memcpy(c->mu0.data(), cfg->mu0, K * sizeof(double));
+    std::vector<double> W0((size_t)K * K, 0.0);
+    if (cfg->W0)
+        std::memcpy(W0.data(), cfg->W0, W0.size() * sizeof(double));
+    else
+        for (int k = 0; k < K; ++k) W0[k * K + k] = 1.0;
+    if (!host_inverse(K, W0, c->W0inv)) {
+        g_init_error = "W0 is singular";
+        delete c;
+        return BMF_E_ARG;
+    }
+    auto bail = [&](bmf_status s, const std::string &m) {
+        g_init_error = m.empty() ? c->err : m;
+        delete c;
+        return s;
+    };
+    std::string err;
+    int st = build_plan(N, D, nnz, row, col, val, cfg->order, cfg->center, I, row_bounds, J,
+                        col_bounds, n_test, test_row, test_col, test_val, c->P, err);
+    if (st) return bail((bmf_status)st, err);
+    for (int64_t e = 0; e < N * K; ++e)
+        if (!std::isfinite(X0[e])) return bail(BMF_E_NONFINITE, "non-finite X0");
+    for (int64_t e = 0; e < D * K; ++e)
+        if (!std::isfinite(W0init[e])) return bail(BMF_E_NONFINITE, "non-finite W0init");
+    if (cudaGetDevice(&c->device) != cudaSuccess) return bail(BMF_E_CUDA, "no CUDA device");
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+    c->ldg = gather_ld(K, c->prec);
+    c->ld_part = gram_part_ld(K, c->prec);
+    bmf_status s = setup_side(c, c->X, c->P.RX, c->P.rptr, c->P.ridx, c->P.rval);
+    if (!s) s = setup_side(c, c->W, c->P.RW, c->P.cptr, c->P.cidx, c->P.cval);
+    if (s) return bail(s, "");
+    // free the host copies of the lists
+    std::vector<int64_t>().swap(c->P.rptr);
+    std::vector<int32_t>().swap(c->P.ridx);
+    std::vector<double>().swap(c->P.rval);
+    std::vector<int64_t>().swap(c->P.cptr);
+    std::vector<int32_t>().swap(c->P.cidx);
+    std::vector<double>().swap(c->P.cval);
+    const int S = I * J;
+    const size_t pbytes = c->prec == BMF_FP64 ? 8 : 4;
+    c->part = c->mem.alloc<char>(std::max<int64_t>(c->part_cap, 1) * c->ld_part * pbytes);
+    c->hyper = c->mem.alloc<double>((size_t)2 * S * hyper_slot_len(K));
+    c->stats_cap = (c->P.RX + c->P.RW) / c->stat_rows + 2 * S + 2;
+    c->stats = c->mem.alloc<double>(c->stats_cap * (K + ntri(K)));
+    c->d_chunks = c->mem.alloc<StatChunk>(c->stats_cap);
+    c->d_jobs = c->mem.alloc<HyperJob>(kHyperJobsMax);
+    c->mu0_d = c->mem.alloc<double>(K);
+    c->W0inv_d = c->mem.alloc<double>((size_t)K * K);
+    const int64_t nt = (int64_t)c->P.trow.size();
+    c->trow = c->mem.alloc<int32_t>(nt);
+    c->tcol = c->mem.alloc<int32_t>(nt);
+    c->tval = c->mem.alloc<double>(nt);
+    c->ysum = c->mem.alloc<double>(nt);
+    c->rmse_part = c->mem.alloc<double>(2 * c->rmse_blocks);
+    c->rmse_out = c->mem.alloc<double>(2);
+    c->err_d = c->mem.alloc<DevError>(1);
+    c->aggX = c->mem.alloc<double>(N * K);
+    c->aggW = c->mem.alloc<double>(D * K);
+    c->ncorr_d = c->mem.alloc<unsigned long long>(1);
+    if (!c->mem.ok) return bail(BMF_E_OOM, "device allocation failed");
+    cudaMemcpy(c->mu0_d, c->mu0.data(), K * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->W0inv_d, c->W0inv.data(), (size_t)K * K * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemset(c->hyper, 0, (size_t)2 * S * hyper_slot_len(K) * sizeof(double));
+    if (nt) {
+        cudaMemcpy(c->trow, c->P.trow.data(), nt * sizeof(int32_t), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->tcol, c->P.tcol.data(), nt * sizeof(int32_t), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->tval, c->P.tval.data(), nt * sizeof(double), cudaMemcpyHostToDevice);
+        cudaMemset(c->ysum, 0, nt * sizeof(double));
+    }
+    DevError z = {0u, INT32_MAX};
+    cudaMemcpy(c->err_d, &z, sizeof(z), cudaMemcpyHostToDevice);
+    // initial states: every subset's blocks from X0 / W0init (original order)
+    std::vector<double> hx((size_t)c->P.RX * K), hw((size_t)c->P.RW * K);
+    for (const auto &g : c->P.subs) {
+        for (int64_t r = 0; r < g.n(); ++r)
+            std::memcpy(&hx[(size_t)(g.xoff + r) * K], &X0[c->P.row_perm[g.r0 + r] * K],
+                        K * sizeof(double));
+        for (int64_t r = 0; r < g.d(); ++r)
+            std::memcpy(&hw[(size_t)(g.woff + r) * K], &W0init[c->P.col_perm[g.c0 + r] * K],
+                        K * sizeof(double));
+    }
+    cudaMemcpy(c->X.F, hx.data(), hx.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->W.F, hw.data(), hw.size() * sizeof(double), cudaMemcpyHostToDevice);
+    launch_fill_gather(K, c->prec, c->P.RX, c->X.F, c->X.G, c->ldg, c->st);
+    launch_fill_gather(K, c->prec, c->P.RW, c->W.F, c->W.G, c->ldg, c->st);
+    c->ss.assign(S, SubState());
+    for (int sl = 0; sl < S; ++sl) {
+        refresh_hslots(c, sl);
+        s = upload_hslots(c, sl);
+        if (s) return bail(s, "");
+    }
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return bail(BMF_E_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+    c->stage_open = 1;
+    *out = c;
+    return BMF_OK;
+}
+
+int64_t bmf_draws_per_sweep(const bmf_ctx *c, int32_t stage, int32_t subset)
+{
+    if (!c) return -1;
+    if (subset >= 0) {
+        if (!valid_subset(c, subset)) return -1;
+        int sl = c->P.subs[subset].slot;
+        return per_sweep_draws(c, sl, sl + 1);
+    }
+    int sl0, sl1;
+    if (!stage_slots(c, stage, sl0, sl1)) return -1;
+    return per_sweep_draws(c, sl0, sl1);
+}
+
+bmf_status bmf_sweep(bmf_ctx *c, int32_t subset, int32_t n_sweeps, const bmf_draws *draws,
+                     bmf_sweep_stats *stats)
+{
+    if (!c) return BMF_E_ARG;
+    if (!valid_subset(c, subset)) return fail(c, BMF_E_ARG, "subset out of range");
+    const SubsetGeom &g = c->P.subs[subset];
+    if (g.stage != c->stage_open)
+        return fail(c, BMF_E_STATE, "the subset's stage is not the open stage");
+    return run_batch(c, g.slot, g.slot + 1, n_sweeps, draws, stats);
+}
+
+bmf_status bmf_stage(bmf_ctx *c, int32_t stage, int32_t n_sweeps, const bmf_draws *draws,
+                     bmf_sweep_stats *stats)
+{
+    if (!c) return BMF_E_ARG;
+    if (stage < 1 || stage > 3) return fail(c, BMF_E_ARG, "stage must be 1, 2 or 3");
+    bmf_status s = open_stage(c, stage);
+    if (s) return s;
+    int sl0, sl1;
+    stage_slots(c, stage, sl0, sl1);
+    return run_batch(c, sl0, sl1, n_sweeps, draws, stats);
+}
+
+bmf_status bmf_posterior_means(bmf_ctx *c, double *Xm, double *Wm, int64_t *n_corrected)
+{
+    if (!c) return BMF_E_ARG;
+    std::vector<double> x, w;
+    bmf_status s = means_original(c, x, w, n_corrected);
+    if (s) return s;
+    if (Xm) std::memcpy(Xm, x.data(), x.size() * sizeof(double));
+    if (Wm) std::memcpy(Wm, w.data(), w.size() * sizeof(double));
+    return BMF_OK;
+}
+
+bmf_status bmf_predict(bmf_ctx *c, int64_t n, const int32_t *row, const int32_t *col,
+                       const double *y, double *yhat, double *rmse)
+{
+    if (!c) return BMF_E_ARG;
+    if (n < 0 || (n > 0 && (!row || !col))) return fail(c, BMF_E_ARG, "bad prediction entries");
+    if (rmse && !y) return fail(c, BMF_E_ARG, "rmse needs y");
+    for (int64_t e = 0; e < n; ++e)
+        if (row[e] < 0 || row[e] >= c->P.N || col[e] < 0 || col[e] >= c->P.D)
+            return fail(c, BMF_E_ARG, "prediction index out of range");
+    std::vector<double> x, w;
+    bmf_status s = means_original(c, x, w, nullptr);
+    if (s) return s;
+    if (n == 0) {
+        if (rmse) *rmse = NAN;
+        return BMF_OK;
+    }
+    // means (original order) and entries to the device, dot products there
+    DevMem tmp;
+    double *xd = tmp.alloc<double>(x.size()), *wd = tmp.alloc<double>(w.size());
+    int32_t *rd = tmp.alloc<int32_t>(n), *cd = tmp.alloc<int32_t>(n);
+    double *yd = tmp.alloc<double>(n);
+    if (!tmp.ok) return fail(c, BMF_E_OOM, "device allocation failed (predict)");
+    CUDA_TRY(c, cudaMemcpy(xd, x.data(), x.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(wd, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(rd, row, n * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(cd, col, n * sizeof(int32_t), cudaMemcpyHostToDevice));
+    launch_predict(c->K, n, rd, cd, xd, wd, c->P.offset, yd, c->st);
+    CUDA_TRY(c, cudaGetLastError());
+    std::vector<double> h(n);
+    CUDA_TRY(c, cudaMemcpyAsync(h.data(), yd, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    if (yhat) std::memcpy(yhat, h.data(), n * sizeof(double));
+    if (rmse) {
+        double ss = 0.0;
+        for (int64_t e = 0; e < n; ++e) ss += (y[e] - h[e]) * (y[e] - h[e]);
+        *rmse = std::sqrt(ss / (double)n);
+    }
+    return BMF_OK;
+}
+
+bmf_status bmf_get_state(bmf_ctx *c, int32_t subset, double *X, double *W, double *hyper)
+{
+    if (!c) return BMF_E_ARG;
+    if (!valid_subset(c, subset)) return fail(c, BMF_E_ARG, "subset out of range");
+    const SubsetGeom &g = c->P.subs[subset];
+    const int K = c->K;
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    if (X && g.n())
+        CUDA_TRY(c, cudaMemcpy(X, c->X.F + g.xoff * K, g.n() * K * sizeof(double), cudaMemcpyDeviceToHost));
+    if (W && g.d())
+        CUDA_TRY(c, cudaMemcpy(W, c->W.F + g.woff * K, g.d() * K * sizeof(double), cudaMemcpyDeviceToHost));
+    if (hyper) {
+        const int HS = hyper_slot_len(K);
+        std::vector<double> h(2 * HS);
+        CUDA_TRY(c, cudaMemcpy(h.data(), c->hyper + (int64_t)2 * g.slot * HS, 2 * HS * sizeof(double),
+                               cudaMemcpyDeviceToHost));
+        for (int f = 0; f < 2; ++f) {
+            const double *sl = h.data() + f * HS;
+            double *o = hyper + f * (K + K * K);
+            for (int i = 0; i < K; ++i) o[i] = sl[i];
+            for (int i = 0; i < K; ++i)
+                for (int j = 0; j <= i; ++j) o[K + i * K + j] = o[K + j * K + i] = sl[K + tri(i, j)];
+        }
+    }
+    return BMF_OK;
+}
+
+bmf_status bmf_set_state(bmf_ctx *c, int32_t subset, const double *X, const double *W)
+{
+    if (!c) return BMF_E_ARG;
+    if (!valid_subset(c, subset)) return fail(c, BMF_E_ARG, "subset out of range");
+    const SubsetGeom &g = c->P.subs[subset];
+    const int K = c->K;
+    if (X) {
+        for (int64_t e = 0; e < g.n() * K; ++e)
+            if (!std::isfinite(X[e])) return fail(c, BMF_E_NONFINITE, "non-finite X");
+        if (g.n())
+            CUDA_TRY(c, cudaMemcpy(c->X.F + g.xoff * K, X, g.n() * K * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    if (W) {
+        for (int64_t e = 0; e < g.d() * K; ++e)
+            if (!std::isfinite(W[e])) return fail(c, BMF_E_NONFINITE, "non-finite W");
+        if (g.d())
+            CUDA_TRY(c, cudaMemcpy(c->W.F + g.woff * K, W, g.d() * K * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    // refresh the gathered copies of the whole arenas (cheap, keeps the call simple)
+    launch_fill_gather(K, c->prec, c->X.R, c->X.F, c->X.G, c->ldg, c->st);
+    launch_fill_gather(K, c->prec, c->W.R, c->W.F, c->W.G, c->ldg, c->st);
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    c->failed = false;
+    return BMF_OK;
+}
+
+bmf_status bmf_get_moments(bmf_ctx *c, int32_t subset, int32_t factor, double *S1, double *S2,
+                           int64_t *kept)
+{
+    if (!c) return BMF_E_ARG;
+    if (!valid_subset(c, subset) || (factor != 0 && factor != 1))
+        return fail(c, BMF_E_ARG, "bad subset or factor");
+    const SubsetGeom &g = c->P.subs[subset];
+    const Side &sd = factor == 0 ? c->X : c->W;
+    const int64_t n = factor == 0 ? g.n() : g.d(), base = factor == 0 ? g.xoff : g.woff;
+    const int K = c->K, NT = ntri(K);
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    std::vector<double> col(n);
+    if (S1)
+        for (int i = 0; i < K && n; ++i) {
+            CUDA_TRY(c, cudaMemcpy(col.data(), sd.S1 + (int64_t)i * sd.R + base, n * sizeof(double),
+                                   cudaMemcpyDeviceToHost));
+            for (int64_t r = 0; r < n; ++r) S1[r * K + i] = col[r];
+        }
+    if (S2)
+        for (int e = 0; e < NT && n; ++e) {
+            CUDA_TRY(c, cudaMemcpy(col.data(), sd.S2 + (int64_t)e * sd.R + base, n * sizeof(double),
+                                   cudaMemcpyDeviceToHost));
+            int i = 0;
+            while ((i + 1) * (i + 2) / 2 <= e) ++i;
+            int j = e - i * (i + 1) / 2;
+            for (int64_t r = 0; r < n; ++r) S2[(r * K + i) * K + j] = S2[(r * K + j) * K + i] = col[r];
+        }
+    if (kept) *kept = c->ss[subset].kept;
+    return BMF_OK;
+}
+
+bmf_status bmf_get_posterior(bmf_ctx *c, int32_t subset, int32_t factor, double *mu, double *Lam)
+{
+    if (!c) return BMF_E_ARG;
+    if (!valid_subset(c, subset) || (factor != 0 && factor != 1))
+        return fail(c, BMF_E_ARG, "bad subset or factor");
+    if (!c->ss[subset].finalized) {
+        // finalise on demand (does not change the chain)
+        const SubsetGeom &g = c->P.subs[subset];
+        SubState &su = c->ss[subset];
+        if (su.kept < 1) return fail(c, BMF_E_STATE, "no retained samples");
+        for (int f = 0; f < 2; ++f) {
+            Side &sd = f == 0 ? c->X : c->W;
+            MMParams mp{c->K, f == 0 ? g.xoff : g.woff, f == 0 ? g.xoff + g.n() : g.woff + g.d(),
+                        sd.R, sd.S1, sd.S2, (double)su.kept, sd.mm_mu, sd.mm_L, sd.mm_b, c->err_d};
+            launch_mm(mp, c->st);
+        }
+        CUDA_TRY(c, cudaGetLastError());
+        bmf_status s = check_dev_error(c);
+        if (s) return s;
+        su.finalized = true;
+    }
+    const SubsetGeom &g = c->P.subs[subset];
+    const Side &sd = factor == 0 ? c->X : c->W;
+    const int64_t n = factor == 0 ? g.n() : g.d(), base = factor == 0 ? g.xoff : g.woff;
+    const int K = c->K, NT = ntri(K);
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    if (mu && n)
+        CUDA_TRY(c, cudaMemcpy(mu, sd.mm_mu + base * K, n * K * sizeof(double), cudaMemcpyDeviceToHost));
+    if (Lam) {
+        std::vector<double> col(n);
+        for (int e = 0; e < NT && n; ++e) {
+            CUDA_TRY(c, cudaMemcpy(col.data(), sd.mm_L + (int64_t)e * sd.R + base, n * sizeof(double),
+                                   cudaMemcpyDeviceToHost));
+            int i = 0;
+            while ((i + 1) * (i + 2) / 2 <= e) ++i;
+            int j = e - i * (i + 1) / 2;
+            for (int64_t r = 0; r < n; ++r) Lam[(r * K + i) * K + j] = Lam[(r * K + j) * K + i] = col[r];
+        }
+    }
+    return BMF_OK;
+}
+
+bmf_status bmf_set_prior(bmf_ctx *c, int32_t subset, int32_t factor, const double *mu,
+                         const double *Lam)
+{
+    if (!c) return BMF_E_ARG;
+    if (!valid_subset(c, subset) || (factor != 0 && factor != 1) || !mu || !Lam)
+        return fail(c, BMF_E_ARG, "bad subset, factor or null prior");
+    const SubsetGeom &g = c->P.subs[subset];
+    Side &sd = factor == 0 ? c->X : c->W;
+    const int64_t n = factor == 0 ? g.n() : g.d(), base = factor == 0 ? g.xoff : g.woff;
+    const int K = c->K, NT = ntri(K);
+    std::vector<double> L((size_t)NT * n), b((size_t)K * n);
+    for (int64_t r = 0; r < n; ++r) {
+        const double *Lr = Lam + r * K * K, *mr = mu + r * K;
+        for (int i = 0; i < K; ++i) {
+            double acc = 0.0;
+            for (int k = 0; k < K; ++k) acc += Lr[i * K + k] * mr[k];
+            b[(size_t)i * n + r] = acc;
+            for (int j = 0; j <= i; ++j) L[(size_t)tri(i, j) * n + r] = Lr[i * K + j];
+        }
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    for (int e = 0; e < NT && n; ++e)
+        CUDA_TRY(c, cudaMemcpy(sd.pL + (int64_t)e * sd.R + base, &L[(size_t)e * n], n * sizeof(double),
+                               cudaMemcpyHostToDevice));
+    for (int i = 0; i < K && n; ++i)
+        CUDA_TRY(c, cudaMemcpy(sd.pb + (int64_t)i * sd.R + base, &b[(size_t)i * n], n * sizeof(double),
+                               cudaMemcpyHostToDevice));
+    c->ss[subset].prior[factor] = 1;
+    refresh_hslots(c, g.slot);
+    bmf_status s = upload_hslots(c, g.slot);
+    if (s) return s;
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    return BMF_OK;
+}
+
+bmf_status bmf_get_subset_info(const bmf_ctx *c, int32_t subset, bmf_subset_info *info)
+{
+    if (!c || !info || !valid_subset(c, subset)) return BMF_E_ARG;
+    const SubsetGeom &g = c->P.subs[subset];
+    info->i = g.i;
+    info->j = g.j;
+    info->stage = g.stage;
+    info->row0 = g.r0;
+    info->row1 = g.r1;
+    info->col0 = g.c0;
+    info->col1 = g.c1;
+    info->nnz = g.nnz;
+    return BMF_OK;
+}
+
+bmf_status bmf_get_perm(const bmf_ctx *c, int64_t *row_perm, int64_t *col_perm)
+{
+    if (!c) return BMF_E_ARG;
+    if (row_perm) std::memcpy(row_perm, c->P.row_perm.data(), c->P.N * sizeof(int64_t));
+    if (col_perm) std::memcpy(col_perm, c->P.col_perm.data(), c->P.D * sizeof(int64_t));
+    return BMF_OK;
+}
+
+void bmf_destroy(bmf_ctx *c)
+{
+    if (!c) return;
+    if (c->st) cudaStreamSynchronize(c->st);
+    if (c->draws_d) cudaFree(c->draws_d);
+    delete c;
+}
+
+const char *bmf_last_error(const bmf_ctx *c)
+{
+    if (!c) return g_init_error.c_str();
+    return c->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,49 @@
+// common.cuh -- internal definitions shared by the library's kernels and its runtime.
+// Not part of the public ABI (include/bmf.h is).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "../../include/bmf.h"
+
+namespace bmf {
+
+constexpr int kWarp = 32;
+
+// Packed lower-triangular index of (i, j), i >= j, row by row.
+__host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+__host__ __device__ constexpr int ntri(int K) { return K * (K + 1) / 2; }
+// Gram partial of one work item: the K(K+1)/2 packed-lower entries of sum p p^T followed by
+// the K entries of sum y p, padded to a multiple of 32 (the warp reduce-scatter width).
+__host__ __device__ constexpr int gram_nv(int K) { return ntri(K) + K; }
+__host__ __device__ constexpr int gram_ld(int K) { return (gram_nv(K) + 31) / 32 * 32; }
+// Hyperparameter draw block: chi2[K], K(K-1)/2 normals, z_mu[K].
+__host__ __device__ constexpr int hyper_len(int K) { return K + K * (K - 1) / 2 + K; }
+
+// A work item of the Gram-gather pass: `count` consecutive observations of arena row `row`
+// starting at position `begin` of the observation lists.
+struct GramItem {
+    int64_t begin;
+    int32_t count;
+    int32_t row;
+};
+
+// Device error word bits (set by kernels, read by the host at sync points).
+enum : uint32_t {
+    ERR_NOT_PD = 1u << 0,
+    ERR_NONFINITE = 1u << 1,
+    ERR_TIMEOUT = 1u << 2,
+    ERR_ARG = 1u << 3,
+};
+
+struct DevError {
+    uint32_t flags;
+    int32_t first_bad_row;  // arena row of the first non-PD conditional (atomicMin)
+};
+
+// Hyperparameters of one (subset, factor): mu[K], Lambda packed lower, b = Lambda mu.
+// Laid out contiguously per slot: [mu (K)][Lambda (ntri)][b (K)].
+__host__ __device__ constexpr int hyper_slot_len(int K) { return K + ntri(K) + K; }
+
+}  // namespace bmf

@@ -1,0 +1,153 @@
+// cond.cu -- the conditional draw of every row given its partners (BPMF Gibbs step for x_n | W,
+// and symmetrically w_d | X; Eqs. 2-4, the (N+D)K^3 term of the cost model of Section 4.3):
+//   Lambda_n = Lambda_p + tau G_n,   b_n = Lambda_p mu_p + tau r_n,
+//   Lambda_n = L L^T (FP64 Cholesky),  x_n = L^{-T} (L^{-1} b_n + z_n),
+// followed by the write of the FP64 state and of its gathered copy, and the moment sums of the
+// moment-matching approximation (Section 4.1).
+//
+// FP64 throughout (the Gram partials are summed in FP64).  One thread per row: the FP64 pipe is
+// the bottleneck on this GPU (about two FP64 FMA per clock per SM), and a thread-per-row
+// factorisation keeps all 32 lanes busy with independent FP64 work.  The packed matrix of each
+// thread lives in shared memory, interleaved across the block so that consecutive threads touch
+// consecutive words; loops run over the runtime K (address arithmetic and shared-memory loads
+// issue in the shadow of the FP64 pipe).
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace bmf {
+
+template <typename GT>
+__device__ __forceinline__ GT to_gather(double x);
+template <>
+__device__ __forceinline__ double to_gather<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float to_gather<float>(double x) { return (float)x; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_gather<__nv_bfloat16>(double x)
+{
+    return __double2bfloat16(x);
+}
+
+constexpr int kCondBlock = 64;
+
+// Shared-memory slots per thread: the packed matrix (ntri(K)), the right-hand side / solution
+// (K) and the reciprocal pivots (K).
+static inline int cond_slots(int K) { return ntri(K) + 2 * K; }
+
+template <typename GT, typename AT>
+__global__ void __launch_bounds__(kCondBlock) cond_kernel(CondParams a)
+{
+    extern __shared__ double sm[];
+    const int t = threadIdx.x;
+    const int64_t r = a.row0 + (int64_t)blockIdx.x * kCondBlock + t;
+    if (r >= a.row1) return;
+    const int K = a.K;
+    const int NT = ntri(K);
+    const int64_t R = a.R;
+    double *M = sm + t;                       // M[e * kCondBlock] is entry e of this thread
+#define SM(e) M[(e) * kCondBlock]
+    const int B0 = NT, RI = NT + K;           // rhs/solution at B0 + i, reciprocal pivot at RI + i
+    // 1. G_n and r_n: FP64 sum of the row's Gram partials (fixed item order).  The partial
+    //    entries use the packed index of the padded width; tri(i, j) does not depend on it.
+    const AT *part = static_cast<const AT *>(a.part);
+    const int prhs = a.part_rhs;
+    for (int e = 0; e < NT + K; ++e) SM(e) = 0.0;
+    const int64_t i0 = a.item_ptr[r], i1 = a.item_ptr[r + 1];
+    for (int64_t it = i0; it < i1; ++it) {
+        const AT *p = part + (it - a.item0) * (int64_t)a.ld;
+        for (int e = 0; e < NT; ++e) SM(e) += (double)p[e];
+        for (int i = 0; i < K; ++i) SM(B0 + i) += (double)p[prhs + i];
+    }
+    // 2. assemble with the prior: a shared hyperparameter slot or a per-row propagated prior
+    const int h = a.row_hslot[r];
+    const double tau = a.tau;
+    if (h >= 0) {
+        const double *hp = a.hyper + (int64_t)h * hyper_slot_len(K);
+        for (int e = 0; e < NT; ++e) SM(e) = fma(tau, SM(e), hp[K + e]);
+        for (int i = 0; i < K; ++i) SM(B0 + i) = fma(tau, SM(B0 + i), hp[K + NT + i]);
+    } else {
+        for (int e = 0; e < NT; ++e) SM(e) = fma(tau, SM(e), a.prior_L[(int64_t)e * R + r]);
+        for (int i = 0; i < K; ++i) SM(B0 + i) = fma(tau, SM(B0 + i), a.prior_b[(int64_t)i * R + r]);
+    }
+    // 3. Cholesky (Crout order: column j from the columns before it)
+    for (int j = 0; j < K; ++j) {
+        const int jj = tri(j, 0);
+        double d = SM(jj + j);
+        for (int k = 0; k < j; ++k) {
+            const double l = SM(jj + k);
+            d = fma(-l, l, d);
+        }
+        if (!(d > 0.0)) {
+            atomicOr(&a.err->flags, ERR_NOT_PD);
+            atomicMin(&a.err->first_bad_row, (int)r);
+            return;
+        }
+        const double rs = rsqrt(d);
+        SM(RI + j) = rs;
+        SM(jj + j) = d * rs;
+        for (int i = j + 1; i < K; ++i) {
+            const int ii = tri(i, 0);
+            double s = SM(ii + j);
+            for (int k = 0; k < j; ++k) s = fma(-SM(ii + k), SM(jj + k), s);
+            SM(ii + j) = s * rs;
+        }
+    }
+    // 4. forward solve L y = b
+    for (int i = 0; i < K; ++i) {
+        const int ii = tri(i, 0);
+        double s = SM(B0 + i);
+        for (int k = 0; k < i; ++k) s = fma(-SM(ii + k), SM(B0 + k), s);
+        SM(B0 + i) = s * SM(RI + i);
+    }
+    // 5. back solve L^T x = y + z
+    const double *z = a.z + (r - a.row0) * K;
+    for (int i = K - 1; i >= 0; --i) {
+        double s = SM(B0 + i) + z[i];
+        for (int k = i + 1; k < K; ++k) s = fma(-SM(tri(k, i)), SM(B0 + k), s);
+        SM(B0 + i) = s * SM(RI + i);
+    }
+    // 6. state, gathered copy, moment sums
+    double *xr = a.X + r * K;
+    GT *g = static_cast<GT *>(a.Xg) + r * a.ldg;
+    for (int i = 0; i < K; ++i) {
+        const double xi = SM(B0 + i);
+        xr[i] = xi;
+        g[i] = to_gather<GT>(xi);
+    }
+    for (int i = K; i < a.ldg; ++i) g[i] = to_gather<GT>(0.0);
+    if (a.keep) {
+        for (int i = 0; i < K; ++i) {
+            const double xi = SM(B0 + i);
+            a.S1[(int64_t)i * R + r] += xi;
+            for (int j = 0; j <= i; ++j) a.S2[(int64_t)tri(i, j) * R + r] += xi * SM(B0 + j);
+        }
+    }
+#undef SM
+}
+
+template <typename GT, typename AT>
+static void launch_cond_t(const CondParams &a, cudaStream_t st)
+{
+    const size_t smem = (size_t)cond_slots(a.K) * kCondBlock * sizeof(double);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(cond_kernel<GT, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    const int64_t n = a.row1 - a.row0;
+    const int grid = (int)((n + kCondBlock - 1) / kCondBlock);
+    cond_kernel<GT, AT><<<grid, kCondBlock, smem, st>>>(a);
+}
+
+void launch_cond(int prec, const CondParams &a, cudaStream_t st)
+{
+    if (a.row1 <= a.row0) return;
+    if (prec == BMF_FP64)
+        launch_cond_t<double, double>(a, st);
+    else if (prec == BMF_FP32)
+        launch_cond_t<float, float>(a, st);
+    else
+        launch_cond_t<__nv_bfloat16, float>(a, st);
+}
+
+}  // namespace bmf

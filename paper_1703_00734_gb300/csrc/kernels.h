@@ -1,0 +1,156 @@
+// kernels.h -- launchers of the library's CUDA kernels (internal).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace bmf {
+
+// Template width of the latent dimension: K rounded up to an even number (the padded
+// dimensions carry zeros in the gathered copies and an identity block in the conditional,
+// which leaves the first K components bit-identical to an unpadded computation).
+int padded_k(int K);
+// Elements per row of a gathered factor copy (K padded, row = multiple of 16 bytes).
+int gather_ld(int K, int prec);
+// Gram entries per work item in the partial buffer.
+int gram_part_ld(int K, int prec);
+
+struct GramParams {
+    const GramItem *items;
+    int64_t n_items;
+    const int32_t *idx;   // observation partner index (arena row of the partner factor)
+    const void *val;      // observation values (double for FP64, float otherwise)
+    const void *P;        // gathered partner copy [rows x ldP]
+    int ldP;
+    void *part;           // partial Gram per item [n_items x ld] (double for FP64, float else)
+    int ld;
+};
+void launch_gram(int K, int prec, const GramParams &a, int grid, cudaStream_t st);
+int gram_parts(int K, int prec);
+
+struct CondParams {
+    int K;
+    int64_t row0, row1;          // arena rows of this launch
+    const int64_t *item_ptr;     // [R+1] first work item of each arena row
+    int64_t item0;               // item index of part[0]
+    const void *part;            // Gram partials (see GramParams)
+    int ld;
+    int part_rhs;                // offset of the right-hand side within a partial
+    double tau;
+    const int32_t *row_hslot;    // [R] hyper slot of the row, or -1 for a per-row prior
+    const double *hyper;         // [slots x hyper_slot_len(K)]
+    const double *prior_L;       // per-row priors, SoA: [ntri(K)][R]
+    const double *prior_b;       // [K][R] (Lambda mu)
+    int64_t R;                   // arena rows (SoA stride)
+    const double *z;             // standard normals of this launch's rows, [row1-row0][K]
+    double *X;                   // FP64 state [R x K]
+    void *Xg;                    // gathered copy [R x ldg]
+    int ldg;
+    int keep;                    // accumulate moments
+    double *S1;                  // SoA [K][R]
+    double *S2;                  // SoA [ntri(K)][R]
+    DevError *err;
+};
+void launch_cond(int prec, const CondParams &a, cudaStream_t st);
+
+// Per-chunk sums for the hyperparameter step: for each chunk, sum x and the packed lower
+// sum x x^T over rows [r0, r1) of an FP64 arena.
+struct StatChunk {
+    int64_t r0, r1;
+    int32_t out;      // output slot (chunk index)
+    int32_t arena;    // 0 = X arena, 1 = W arena
+};
+void launch_stats(int K, const StatChunk *chunks, int n_chunks, const double *X, const double *W,
+                  double *out, cudaStream_t st);
+
+// Normal-Wishart posterior and draw for a list of (chunk range -> hyper slot) jobs.
+struct HyperJob {
+    int32_t chunk0, chunk1;  // stats chunks to sum
+    int32_t slot;            // output hyper slot
+    int32_t draw;            // offset of the draw block (doubles) in the sweep's draw buffer
+    int64_t n;               // rows of the factor block
+};
+struct HyperParams {
+    int K;
+    const HyperJob *jobs;
+    int n_jobs;
+    const double *stats;     // [chunks x (K + ntri)]
+    const double *mu0;       // [K]
+    double beta0, nu0;
+    const double *W0inv;     // [K*K]
+    const double *draws;     // the sweep's draw buffer
+    double *hyper;           // [slots x hyper_slot_len]
+    DevError *err;
+};
+void launch_hyper(const HyperParams &a, cudaStream_t st);
+
+// Test-set predictions of the current sample, running mean, squared errors.
+struct RmseParams {
+    int K, prec;
+    int64_t t0, t1;          // test arena range
+    const int32_t *trow, *tcol;
+    const double *tval;
+    const void *Xg, *Wg;
+    int ldg;
+    int keep;
+    double *ysum;            // running sum of predictions over kept samples
+    double kept_after;       // number of kept samples after this sweep (for the mean)
+    double *partial;         // [blocks x 2]
+};
+void launch_rmse(const RmseParams &a, int blocks, cudaStream_t st);
+void launch_rmse_final(const double *partial, int blocks, double *out2, cudaStream_t st);
+
+// Moment matching (Section 4.1) per arena row: mu = S1/S, Sigma = S2/S - mu mu^T,
+// Lambda = Sigma^{-1}; writes mu [R x K] (AoS), Lambda packed SoA and b = Lambda mu SoA.
+struct MMParams {
+    int K;
+    int64_t r0, r1, R;
+    const double *S1, *S2;   // SoA
+    double S;
+    double *mu;              // [R x K]
+    double *L;               // SoA [ntri][R]
+    double *b;               // SoA [K][R]
+    DevError *err;
+};
+void launch_mm(const MMParams &a, cudaStream_t st);
+
+// Copy per-row propagated priors from a source arena range to a destination range and set the
+// destination state to the propagated mean.
+struct PropParams {
+    int K;
+    int64_t n, src0, dst0, R;
+    const double *mu, *L, *b;     // source MM results (mu AoS [R x K], L/b SoA)
+    double *pL, *pb;              // destination prior SoA
+    double *X;                    // destination state [R x K]
+    void *Xg;
+    int ldg, prec;
+};
+void launch_propagate(const PropParams &a, cudaStream_t st);
+
+// Algorithm 2 for one factor: for each global row n (reordered order), J submodel arena rows
+// sub_row[j] + (n - block start); writes mu* [n_rows x K].
+struct AggParams {
+    int K;
+    int64_t n_rows;           // rows of this block
+    int J;
+    const int64_t *sub_base;  // [J] arena row of the block's first row in submodel j
+    const double *mu;         // MM means AoS [R x K]
+    const double *L;          // MM precisions SoA [ntri][R]
+    int64_t R;
+    double eps_rel;
+    double *out;              // [n_rows x K]
+    unsigned long long *n_corrected;
+    DevError *err;
+};
+void launch_aggregate(const AggParams &a, cudaStream_t st);
+
+// y_hat = offset + xm[row]^T wm[col] for host-given entries (original order means).
+void launch_predict(int K, int64_t n, const int32_t *row, const int32_t *col, const double *Xm,
+                    const double *Wm, double offset, double *yhat, cudaStream_t st);
+
+// Device helpers
+void launch_fill_gather(int K, int prec, int64_t R, const double *X, void *Xg, int ldg,
+                        cudaStream_t st);
+
+}  // namespace bmf

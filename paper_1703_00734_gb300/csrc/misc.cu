@@ -1,0 +1,661 @@
+// misc.cu -- the smaller kernels of the sweep and of posterior propagation:
+//   * per-chunk factor statistics and the Normal-Wishart hyperparameter draw (Section 5.1 and
+//     its footnote),
+//   * the predictive RMSE pass (Section 5.2),
+//   * moment matching of the retained samples (Section 4.1),
+//   * installation of propagated priors (Algorithm 1),
+//   * the eigenvalue-corrected aggregation of Algorithm 2 / Eq. 14 (Section 4.2),
+//   * posterior-mean prediction.
+// All FP64 except the test-set dot products of the reduced-precision modes.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace bmf {
+
+__device__ __forceinline__ void decode_tri(int e, int &i, int &j)
+{
+    int r = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+    while (r * (r + 1) / 2 > e) --r;
+    while ((r + 1) * (r + 2) / 2 <= e) ++r;
+    i = r;
+    j = e - r * (r + 1) / 2;
+}
+
+// ------------------------------------------------------------------------------------------
+// Factor statistics: per chunk of rows, sum_x [K] then packed lower sum_x x^T [ntri(K)].
+// ------------------------------------------------------------------------------------------
+constexpr int kStatThreads = 256, kStatTile = 32, kStatMaxPer = 9;
+
+__global__ void __launch_bounds__(kStatThreads)
+stats_kernel(int K, const StatChunk *__restrict__ chunks, const double *__restrict__ X,
+             const double *__restrict__ W, double *__restrict__ out)
+{
+    extern __shared__ double tile[];  // [kStatTile][K]
+    const StatChunk c = chunks[blockIdx.x];
+    const double *A = c.arena ? W : X;
+    const int NS = K + ntri(K);
+    const int t = threadIdx.x;
+    double acc[kStatMaxPer];
+    int ei[kStatMaxPer], ej[kStatMaxPer];
+#pragma unroll
+    for (int q = 0; q < kStatMaxPer; ++q) {
+        acc[q] = 0.0;
+        const int e = t + q * kStatThreads;
+        if (e < K) {
+            ei[q] = e;
+            ej[q] = -1;
+        } else if (e < NS) {
+            decode_tri(e - K, ei[q], ej[q]);
+        } else {
+            ei[q] = -1;
+            ej[q] = -1;
+        }
+    }
+    for (int64_t r0 = c.r0; r0 < c.r1; r0 += kStatTile) {
+        const int rows = (int)min((int64_t)kStatTile, c.r1 - r0);
+        __syncthreads();
+        for (int q = t; q < rows * K; q += kStatThreads) tile[q] = A[r0 * K + q];
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kStatMaxPer; ++q) {
+            if (ei[q] < 0) continue;
+            const int i = ei[q], j = ej[q];
+            double s = acc[q];
+            if (j < 0)
+                for (int rr = 0; rr < rows; ++rr) s += tile[rr * K + i];
+            else
+                for (int rr = 0; rr < rows; ++rr) s = fma(tile[rr * K + i], tile[rr * K + j], s);
+            acc[q] = s;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kStatMaxPer; ++q) {
+        const int e = t + q * kStatThreads;
+        if (e < NS) out[(int64_t)c.out * NS + e] = acc[q];
+    }
+}
+
+void launch_stats(int K, const StatChunk *chunks, int n_chunks, const double *X, const double *W,
+                  double *out, cudaStream_t st)
+{
+    if (n_chunks <= 0) return;
+    stats_kernel<<<n_chunks, kStatThreads, kStatTile * K * sizeof(double), st>>>(K, chunks, X, W,
+                                                                                 out);
+}
+
+// ------------------------------------------------------------------------------------------
+// Block-level dense FP64 linear algebra on K x K row-major matrices in shared memory.
+// ------------------------------------------------------------------------------------------
+
+// In-place lower Cholesky (right-looking).  Returns false (uniformly) if a pivot is not > 0.
+__device__ bool block_chol(double *A, int K, int *flag)
+{
+    const int t = threadIdx.x, T = blockDim.x;
+    for (int k = 0; k < K; ++k) {
+        if (t == 0) {
+            const double d = A[k * K + k];
+            if (!(d > 0.0))
+                *flag = 1;
+            else
+                A[k * K + k] = sqrt(d);
+        }
+        __syncthreads();
+        if (*flag) return false;
+        const double dk = A[k * K + k];
+        for (int i = k + 1 + t; i < K; i += T) A[i * K + k] /= dk;
+        __syncthreads();
+        const int m = K - k - 1;
+        for (int e = t; e < m * m; e += T) {
+            const int i = k + 1 + e / m, j = k + 1 + e % m;
+            if (j <= i) A[i * K + j] = fma(-A[i * K + k], A[j * K + k], A[i * K + j]);
+        }
+        __syncthreads();
+    }
+    // zero the strict upper triangle
+    for (int e = t; e < K * K; e += T)
+        if (e % K > e / K) A[e] = 0.0;
+    __syncthreads();
+    return true;
+}
+
+// Inverse of S = L L^T (L lower in Lm): column c solves L y = e_c, L^T x = y; then symmetrise.
+__device__ void block_spd_inverse_from_chol(const double *Lm, double *Out, double *Tmp, int K)
+{
+    const int t = threadIdx.x, T = blockDim.x;
+    for (int c = t; c < K; c += T) {
+        for (int i = 0; i < K; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) s = fma(-Lm[i * K + k], Tmp[k * K + c], s);
+            Tmp[i * K + c] = s / Lm[i * K + i];
+        }
+        for (int i = K - 1; i >= 0; --i) {
+            double s = Tmp[i * K + c];
+            for (int k = i + 1; k < K; ++k) s = fma(-Lm[k * K + i], Out[k * K + c], s);
+            Out[i * K + c] = s / Lm[i * K + i];
+        }
+    }
+    __syncthreads();
+    for (int e = t; e < K * K; e += T) {
+        const int i = e / K, j = e % K;
+        if (j < i) {
+            const double m = 0.5 * (Out[i * K + j] + Out[j * K + i]);
+            Out[i * K + j] = m;
+            Out[j * K + i] = m;
+        }
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------------------------
+// Normal-Wishart hyperparameter draw: one block per (subset, factor) job.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) hyper_kernel(HyperParams a)
+{
+    const HyperJob jb = a.jobs[blockIdx.x];
+    const int K = a.K, KK = K * K, NS = K + ntri(K);
+    const int t = threadIdx.x, T = blockDim.x;
+    extern __shared__ double s[];
+    double *M = s, *C = M + KK, *L = C + KK, *B = L + KK;
+    double *s1 = B + KK, *xbar = s1 + K, *mus = xbar + K, *v = mus + K, *mu = v + K;
+    __shared__ int flag;
+    if (t == 0) flag = 0;
+    // 1. sum the chunk statistics in chunk order
+    for (int e = t; e < NS; e += T) {
+        double acc = 0.0;
+        for (int c = jb.chunk0; c < jb.chunk1; ++c) acc += a.stats[(int64_t)c * NS + e];
+        if (e < K) {
+            s1[e] = acc;
+        } else {
+            int i, j;
+            decode_tri(e - K, i, j);
+            M[i * K + j] = acc;
+            M[j * K + i] = acc;
+        }
+    }
+    __syncthreads();
+    const double N = (double)jb.n;
+    const double bstar = a.beta0 + N;
+    for (int e = t; e < K; e += T) {
+        xbar[e] = N > 0 ? s1[e] / N : 0.0;
+        mus[e] = (a.beta0 * a.mu0[e] + N * (N > 0 ? s1[e] / N : 0.0)) / bstar;
+    }
+    __syncthreads();
+    // 2. [W*]^{-1} = W0^{-1} + N Sbar + (beta0 N / beta*) (mu0 - xbar)(mu0 - xbar)^T with the
+    //    centred Sbar = (1/N) sum x x^T - xbar xbar^T
+    const double cw = a.beta0 * N / bstar;
+    for (int e = t; e < KK; e += T) {
+        const int i = e / K, j = e % K;
+        const double Sb = N > 0 ? M[e] / N - xbar[i] * xbar[j] : 0.0;
+        C[e] = a.W0inv[e] + N * Sb + cw * (a.mu0[i] - xbar[i]) * (a.mu0[j] - xbar[j]);
+    }
+    __syncthreads();
+    // 3. W* = ([W*]^{-1})^{-1}
+    if (!block_chol(C, K, &flag)) goto fail;
+    block_spd_inverse_from_chol(C, M, B, K);     // M = W*
+    // 4. L = chol(W*)
+    for (int e = t; e < KK; e += T) L[e] = M[e];
+    __syncthreads();
+    if (!block_chol(L, K, &flag)) goto fail;
+    // 5. Bartlett factor A (lower) in B
+    {
+        const double *dr = a.draws + jb.draw;
+        const int nlow = K * (K - 1) / 2;
+        for (int e = t; e < KK; e += T) {
+            const int i = e / K, j = e % K;
+            double val = 0.0;
+            if (i == j)
+                val = sqrt(dr[i]);
+            else if (j < i)
+                val = dr[K + i * (i - 1) / 2 + j];
+            B[e] = val;
+        }
+        if (t < K) v[t] = dr[K + nlow + t];   // z_mu
+    }
+    __syncthreads();
+    // 6. C = L A (lower), Lambda = C C^T in M
+    for (int e = t; e < KK; e += T) {
+        const int i = e / K, j = e % K;
+        double acc = 0.0;
+        if (j <= i)
+            for (int k = j; k <= i; ++k) acc = fma(L[i * K + k], B[k * K + j], acc);
+        C[e] = acc;
+    }
+    __syncthreads();
+    for (int e = t; e < KK; e += T) {
+        const int i = e / K, j = e % K;
+        double acc = 0.0;
+        const int kmax = min(i, j);
+        for (int k = 0; k <= kmax; ++k) acc = fma(C[i * K + k], C[j * K + k], acc);
+        M[e] = acc;
+    }
+    __syncthreads();
+    // 7. mu = mu* + chol(beta* Lambda)^{-T} z_mu
+    for (int e = t; e < KK; e += T) L[e] = bstar * M[e];
+    __syncthreads();
+    if (!block_chol(L, K, &flag)) goto fail;
+    if (t == 0) {
+        for (int i = K - 1; i >= 0; --i) {
+            double acc = v[i];
+            for (int k = i + 1; k < K; ++k) acc = fma(-L[k * K + i], v[k], acc);
+            v[i] = acc / L[i * K + i];
+        }
+        for (int i = 0; i < K; ++i) mu[i] = mus[i] + v[i];
+    }
+    __syncthreads();
+    // 8. write the slot: mu, Lambda (packed lower), b = Lambda mu
+    {
+        double *slot = a.hyper + (int64_t)jb.slot * hyper_slot_len(K);
+        for (int e = t; e < K; e += T) slot[e] = mu[e];
+        for (int e = t; e < ntri(K); e += T) {
+            int i, j;
+            decode_tri(e, i, j);
+            slot[K + e] = M[i * K + j];
+        }
+        for (int i = t; i < K; i += T) {
+            double acc = 0.0;
+            for (int k = 0; k < K; ++k) acc = fma(M[i * K + k], mu[k], acc);
+            slot[K + ntri(K) + i] = acc;
+        }
+    }
+    return;
+fail:
+    if (t == 0) atomicOr(&a.err->flags, ERR_NOT_PD);
+}
+
+void launch_hyper(const HyperParams &a, cudaStream_t st)
+{
+    if (a.n_jobs <= 0) return;
+    const size_t smem = (size_t)(4 * a.K * a.K + 5 * a.K) * sizeof(double);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(hyper_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    hyper_kernel<<<a.n_jobs, 256, smem, st>>>(a);
+}
+
+// ------------------------------------------------------------------------------------------
+// Predictive RMSE of the current sample and of the running mean (Section 5.2).
+// ------------------------------------------------------------------------------------------
+template <typename GT, typename AT>
+__global__ void __launch_bounds__(256) rmse_kernel(RmseParams a)
+{
+    const GT *Xg = static_cast<const GT *>(a.Xg), *Wg = static_cast<const GT *>(a.Wg);
+    double s0 = 0.0, s1 = 0.0;
+    for (int64_t e = a.t0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.t1;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const GT *x = Xg + (int64_t)a.trow[e] * a.ldg, *w = Wg + (int64_t)a.tcol[e] * a.ldg;
+        AT p = 0;
+        for (int k = 0; k < a.K; ++k) p += (AT)x[k] * (AT)w[k];
+        const double yh = (double)p;
+        const double d0 = a.tval[e] - yh;
+        s0 += d0 * d0;
+        double ys = a.ysum[e];
+        if (a.keep) {
+            ys += yh;
+            a.ysum[e] = ys;
+        }
+        if (a.kept_after > 0) {
+            const double d1 = a.tval[e] - ys / a.kept_after;
+            s1 += d1 * d1;
+        }
+    }
+    __shared__ double red[2][256];
+    red[0][threadIdx.x] = s0;
+    red[1][threadIdx.x] = s1;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + o];
+            red[1][threadIdx.x] += red[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        a.partial[2 * blockIdx.x] = red[0][0];
+        a.partial[2 * blockIdx.x + 1] = red[1][0];
+    }
+}
+
+__global__ void rmse_final_kernel(const double *partial, int blocks, double *out2)
+{
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < blocks; ++k) {
+            a += partial[2 * k];
+            b += partial[2 * k + 1];
+        }
+        out2[0] = a;
+        out2[1] = b;
+    }
+}
+
+void launch_rmse(const RmseParams &a, int blocks, cudaStream_t st)
+{
+    if (a.prec == BMF_FP64)
+        rmse_kernel<double, double><<<blocks, 256, 0, st>>>(a);
+    else if (a.prec == BMF_FP32)
+        rmse_kernel<float, float><<<blocks, 256, 0, st>>>(a);
+    else
+        rmse_kernel<__nv_bfloat16, float><<<blocks, 256, 0, st>>>(a);
+}
+
+void launch_rmse_final(const double *partial, int blocks, double *out2, cudaStream_t st)
+{
+    rmse_final_kernel<<<1, 32, 0, st>>>(partial, blocks, out2);
+}
+
+// ------------------------------------------------------------------------------------------
+// Thread-per-row FP64 helpers on packed lower matrices in interleaved shared memory.
+// ------------------------------------------------------------------------------------------
+constexpr int kRowBlock = 32;
+#define RS(base, e) (base)[(e) * kRowBlock]
+
+// In-place packed lower Cholesky; returns false if a pivot is not > 0.
+__device__ bool row_chol(double *P, int K)
+{
+    for (int j = 0; j < K; ++j) {
+        const int jj = tri(j, 0);
+        double d = RS(P, jj + j);
+        for (int k = 0; k < j; ++k) d = fma(-RS(P, jj + k), RS(P, jj + k), d);
+        if (!(d > 0.0)) return false;
+        const double sd = sqrt(d);
+        RS(P, jj + j) = sd;
+        for (int i = j + 1; i < K; ++i) {
+            const int ii = tri(i, 0);
+            double s = RS(P, ii + j);
+            for (int k = 0; k < j; ++k) s = fma(-RS(P, ii + k), RS(P, jj + k), s);
+            RS(P, ii + j) = s / sd;
+        }
+    }
+    return true;
+}
+
+// Solve (L L^T) x = b in place in vector v (interleaved), L packed in P.
+__device__ void row_solve(const double *P, double *v, int K)
+{
+    for (int i = 0; i < K; ++i) {
+        const int ii = tri(i, 0);
+        double s = RS(v, i);
+        for (int k = 0; k < i; ++k) s = fma(-RS(P, ii + k), RS(v, k), s);
+        RS(v, i) = s / RS(P, ii + i);
+    }
+    for (int i = K - 1; i >= 0; --i) {
+        double s = RS(v, i);
+        for (int k = i + 1; k < K; ++k) s = fma(-RS(P, tri(k, i)), RS(v, k), s);
+        RS(v, i) = s / RS(P, tri(i, i));
+    }
+}
+
+// Inverse of L L^T (L packed in P) into packed Out: column c from (L L^T) x = e_c, using tmp[K].
+__device__ void row_inverse(const double *P, double *Out, double *tmp, int K)
+{
+    for (int c = 0; c < K; ++c) {
+        for (int i = 0; i < K; ++i) RS(tmp, i) = (i == c) ? 1.0 : 0.0;
+        row_solve(P, tmp, K);
+        for (int i = c; i < K; ++i) RS(Out, tri(i, c)) = RS(tmp, i);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Moment matching: mu = S1/S, Sigma = S2/S - mu mu^T, Lambda = Sigma^{-1}, b = Lambda mu.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kRowBlock) mm_kernel(MMParams a)
+{
+    extern __shared__ double sm[];
+    const int t = threadIdx.x;
+    const int64_t r = a.r0 + (int64_t)blockIdx.x * kRowBlock + t;
+    if (r >= a.r1) return;
+    const int K = a.K, NT = ntri(K);
+    double *Sg = sm + t, *Lm = Sg + NT * kRowBlock, *mu = Lm + NT * kRowBlock,
+           *tmp = mu + K * kRowBlock;
+    for (int i = 0; i < K; ++i) RS(mu, i) = a.S1[(int64_t)i * a.R + r] / a.S;
+    for (int i = 0; i < K; ++i)
+        for (int j = 0; j <= i; ++j)
+            RS(Sg, tri(i, j)) = a.S2[(int64_t)tri(i, j) * a.R + r] / a.S - RS(mu, i) * RS(mu, j);
+    if (!row_chol(Sg, K)) {
+        atomicOr(&a.err->flags, ERR_NOT_PD);
+        atomicMin(&a.err->first_bad_row, (int)r);
+        return;
+    }
+    row_inverse(Sg, Lm, tmp, K);
+    for (int i = 0; i < K; ++i) a.mu[r * K + i] = RS(mu, i);
+    for (int e = 0; e < NT; ++e) a.L[(int64_t)e * a.R + r] = RS(Lm, e);
+    for (int i = 0; i < K; ++i) {
+        double acc = 0.0;
+        for (int k = 0; k < K; ++k)
+            acc = fma(RS(Lm, i >= k ? tri(i, k) : tri(k, i)), RS(mu, k), acc);
+        a.b[(int64_t)i * a.R + r] = acc;
+    }
+}
+
+void launch_mm(const MMParams &a, cudaStream_t st)
+{
+    const int64_t n = a.r1 - a.r0;
+    if (n <= 0) return;
+    const size_t smem = (size_t)(2 * ntri(a.K) + 2 * a.K) * kRowBlock * sizeof(double);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(mm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    mm_kernel<<<(int)((n + kRowBlock - 1) / kRowBlock), kRowBlock, smem, st>>>(a);
+}
+
+// ------------------------------------------------------------------------------------------
+// Propagated priors: destination rows get the source rows' moment-matched Gaussian as prior
+// and start their chain at its mean.
+// ------------------------------------------------------------------------------------------
+template <typename GT>
+__global__ void propagate_kernel(PropParams a)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= a.n) return;
+    const int64_t s = a.src0 + q, d = a.dst0 + q;
+    const int K = a.K;
+    for (int e = 0; e < ntri(K); ++e) a.pL[(int64_t)e * a.R + d] = a.L[(int64_t)e * a.R + s];
+    for (int i = 0; i < K; ++i) a.pb[(int64_t)i * a.R + d] = a.b[(int64_t)i * a.R + s];
+    GT *g = static_cast<GT *>(a.Xg) + d * a.ldg;
+    for (int i = 0; i < a.ldg; ++i) {
+        const double x = i < K ? a.mu[s * K + i] : 0.0;
+        if (i < K) a.X[d * K + i] = x;
+        if constexpr (sizeof(GT) == 2)
+            g[i] = __double2bfloat16(x);
+        else
+            g[i] = (GT)x;
+    }
+}
+
+void launch_propagate(const PropParams &a, cudaStream_t st)
+{
+    if (a.n <= 0) return;
+    const int grid = (int)((a.n + 127) / 128);
+    if (a.prec == BMF_FP64)
+        propagate_kernel<double><<<grid, 128, 0, st>>>(a);
+    else if (a.prec == BMF_FP32)
+        propagate_kernel<float><<<grid, 128, 0, st>>>(a);
+    else
+        propagate_kernel<__nv_bfloat16><<<grid, 128, 0, st>>>(a);
+}
+
+// ------------------------------------------------------------------------------------------
+// Algorithm 2 (Eq. 14 with the eigenvalue correction), thread per row.
+// ------------------------------------------------------------------------------------------
+
+// Smallest eigenvalue of the symmetric K x K matrix in `a` (row-major, thread-private global
+// scratch) by cyclic Jacobi rotations (Golub & Van Loan, Section 8.5).
+__device__ double jacobi_min_eig(double *a, int K)
+{
+    double fro = 0.0;
+    for (int e = 0; e < K * K; ++e) fro += a[e] * a[e];
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < K; ++p)
+            for (int q = p + 1; q < K; ++q) off += a[p * K + q] * a[p * K + q];
+        if (off <= 1e-30 * fro || off == 0.0) break;
+        for (int p = 0; p < K; ++p)
+            for (int q = p + 1; q < K; ++q) {
+                const double apq = a[p * K + q];
+                if (apq == 0.0) continue;
+                const double theta = (a[q * K + q] - a[p * K + p]) / (2.0 * apq);
+                const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(tt * tt + 1.0), s = tt * c;
+                for (int k = 0; k < K; ++k) {
+                    const double akp = a[k * K + p], akq = a[k * K + q];
+                    a[k * K + p] = c * akp - s * akq;
+                    a[k * K + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < K; ++k) {
+                    const double apk = a[p * K + k], aqk = a[q * K + k];
+                    a[p * K + k] = c * apk - s * aqk;
+                    a[q * K + k] = s * apk + c * aqk;
+                }
+            }
+    }
+    double m = a[0];
+    for (int i = 1; i < K; ++i) m = fmin(m, a[i * K + i]);
+    return m;
+}
+
+__global__ void __launch_bounds__(kRowBlock) aggregate_kernel(AggParams a, double *jac_scratch)
+{
+    extern __shared__ double sm[];
+    const int t = threadIdx.x;
+    const int64_t n = (int64_t)blockIdx.x * kRowBlock + t;
+    if (n >= a.n_rows) return;
+    const int K = a.K, NT = ntri(K), J = a.J;
+    double *Ls = sm + t, *Dm = Ls + NT * kRowBlock, *h = Dm + NT * kRowBlock;
+    const int64_t r1 = a.sub_base[0] + n;
+    const double c0 = 2.0 - (double)J;
+    double mean_diag = 0.0;
+    for (int i = 0; i < K; ++i) mean_diag += a.L[(int64_t)tri(i, i) * a.R + r1];
+    mean_diag /= (double)K;
+    const double eps = a.eps_rel * (mean_diag > 1.0 ? mean_diag : 1.0);
+    for (int e = 0; e < NT; ++e) RS(Ls, e) = c0 * a.L[(int64_t)e * a.R + r1];
+    for (int i = 0; i < K; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < K; ++k)
+            s = fma(a.L[(int64_t)(i >= k ? tri(i, k) : tri(k, i)) * a.R + r1], a.mu[r1 * K + k], s);
+        RS(h, i) = c0 * s;
+    }
+    unsigned long long ncorr = 0;
+    for (int j = 1; j < J; ++j) {
+        const int64_t rj = a.sub_base[j] + n;
+        for (int e = 0; e < NT; ++e)
+            RS(Dm, e) = a.L[(int64_t)e * a.R + rj] - a.L[(int64_t)e * a.R + r1];
+        // Lambda*^(j) = Lambda^(j) if the difference is PD, else corrected difference + Lambda^(1)
+        bool pd;
+        {
+            // factor a copy (kept in the accumulated slots' scratch: reuse h-adjacent area)
+            double *F = jac_scratch + n * (int64_t)K * K;   // K*K per row, also used by Jacobi
+            for (int e = 0; e < NT; ++e) F[e] = RS(Dm, e);
+            pd = true;
+            for (int jj = 0; jj < K && pd; ++jj) {
+                const int b = tri(jj, 0);
+                double d = F[b + jj];
+                for (int k = 0; k < jj; ++k) d = fma(-F[b + k], F[b + k], d);
+                if (!(d > 0.0)) {
+                    pd = false;
+                    break;
+                }
+                const double sd = sqrt(d);
+                F[b + jj] = sd;
+                for (int i = jj + 1; i < K; ++i) {
+                    const int ib = tri(i, 0);
+                    double s = F[ib + jj];
+                    for (int k = 0; k < jj; ++k) s = fma(-F[ib + k], F[b + k], s);
+                    F[ib + jj] = s / sd;
+                }
+            }
+            if (!pd) {
+                for (int i = 0; i < K; ++i)
+                    for (int k = 0; k < K; ++k)
+                        F[i * K + k] = RS(Dm, i >= k ? tri(i, k) : tri(k, i));
+                const double lmin = jacobi_min_eig(F, K);
+                for (int i = 0; i < K; ++i) RS(Dm, tri(i, i)) += fabs(lmin) + eps;
+                for (int e = 0; e < NT; ++e) RS(Dm, e) += a.L[(int64_t)e * a.R + r1];
+                ++ncorr;
+            } else {
+                for (int e = 0; e < NT; ++e) RS(Dm, e) = a.L[(int64_t)e * a.R + rj];
+            }
+        }
+        for (int e = 0; e < NT; ++e) RS(Ls, e) += RS(Dm, e);
+        for (int i = 0; i < K; ++i) {
+            double s = 0.0;
+            for (int k = 0; k < K; ++k)
+                s = fma(RS(Dm, i >= k ? tri(i, k) : tri(k, i)), a.mu[rj * K + k], s);
+            RS(h, i) += s;
+        }
+    }
+    if (!row_chol(Ls, K)) {
+        atomicOr(&a.err->flags, ERR_NOT_PD);
+        atomicMin(&a.err->first_bad_row, (int)n);
+        return;
+    }
+    row_solve(Ls, h, K);
+    for (int i = 0; i < K; ++i) a.out[n * K + i] = RS(h, i);
+    if (ncorr) atomicAdd(a.n_corrected, ncorr);
+}
+
+void launch_aggregate(const AggParams &a, cudaStream_t st)
+{
+    if (a.n_rows <= 0) return;
+    // per-row K x K scratch for the factorisation test and the Jacobi fallback
+    double *scr = nullptr;
+    if (cudaMallocAsync(&scr, (size_t)a.n_rows * a.K * a.K * sizeof(double), st) != cudaSuccess)
+        return;
+    const size_t smem = (size_t)(2 * ntri(a.K) + a.K) * kRowBlock * sizeof(double);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(aggregate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    aggregate_kernel<<<(int)((a.n_rows + kRowBlock - 1) / kRowBlock), kRowBlock, smem, st>>>(a,
+                                                                                           scr);
+    cudaFreeAsync(scr, st);
+}
+
+// ------------------------------------------------------------------------------------------
+// Posterior-mean prediction and gathered-copy refresh.
+// ------------------------------------------------------------------------------------------
+__global__ void predict_kernel(int K, int64_t n, const int32_t *row, const int32_t *col,
+                               const double *Xm, const double *Wm, double offset, double *yhat)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const double *x = Xm + (int64_t)row[e] * K, *w = Wm + (int64_t)col[e] * K;
+    double s = 0.0;
+    for (int k = 0; k < K; ++k) s = fma(x[k], w[k], s);
+    yhat[e] = offset + s;
+}
+
+void launch_predict(int K, int64_t n, const int32_t *row, const int32_t *col, const double *Xm,
+                    const double *Wm, double offset, double *yhat, cudaStream_t st)
+{
+    if (n <= 0) return;
+    predict_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(K, n, row, col, Xm, Wm, offset, yhat);
+}
+
+template <typename GT>
+__global__ void fill_gather_kernel(int K, int64_t R, const double *X, GT *Xg, int ldg)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= R * ldg) return;
+    const int64_t r = q / ldg;
+    const int i = (int)(q % ldg);
+    const double x = i < K ? X[r * K + i] : 0.0;
+    if constexpr (sizeof(GT) == 2)
+        Xg[q] = __double2bfloat16(x);
+    else
+        Xg[q] = (GT)x;
+}
+
+void launch_fill_gather(int K, int prec, int64_t R, const double *X, void *Xg, int ldg,
+                        cudaStream_t st)
+{
+    const int64_t n = R * ldg;
+    if (n <= 0) return;
+    const int grid = (int)((n + 255) / 256);
+    if (prec == BMF_FP64)
+        fill_gather_kernel<double><<<grid, 256, 0, st>>>(K, R, X, (double *)Xg, ldg);
+    else if (prec == BMF_FP32)
+        fill_gather_kernel<float><<<grid, 256, 0, st>>>(K, R, X, (float *)Xg, ldg);
+    else
+        fill_gather_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(K, R, X, (__nv_bfloat16 *)Xg, ldg);
+}
+
+}  // namespace bmf

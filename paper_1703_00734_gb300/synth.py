@@ -146,9 +146,9 @@ def make_workload(name: str = None, test_frac: float = 0.1, scale: float = 1.0, 
     cfg = dict(WORKLOADS[name]) if name else {}
     sizes = {k: over.pop(k) for k in ("N", "D", "M") if k in over}
     cfg.update(over)
-    N = sizes.get("N", max(2, int(round(cfg["N"] * scale))))
-    D = sizes.get("D", max(2, int(round(cfg["D"] * scale))))
-    M = sizes.get("M", max(4, int(round(cfg["M"] * scale * scale))))
+    N = sizes["N"] if "N" in sizes else max(2, int(round(cfg["N"] * scale)))
+    D = sizes["D"] if "D" in sizes else max(2, int(round(cfg["D"] * scale)))
+    M = sizes["M"] if "M" in sizes else max(4, int(round(cfg["M"] * scale * scale)))
     K = cfg["K"]
     seed = cfg.get("seed", 0)
     rng = rng_for(seed, 1)
