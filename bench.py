@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark of the BPMF Gibbs sweep (Qin et al., arXiv 1703.00734, Section 5.1) on one GB300.
+
+A step is one full Gibbs sweep of the plain sampler on the 69,878 x 10,677 Zipf(1.2) rating
+matrix with 10M observations (9M train), K = 10: Normal-Wishart draws for both factors, the
+Gram-gather and FP64 conditional draw of every row and every column, and the test-RMSE pass.
+The headline `value` is sweeps/s of the reduced-precision path (FP32 gathers and Gram, FP64
+Cholesky/Wishart), inputs resident in HBM; the plain FP64 GPU sweep and the test RMSE of both
+are reported beside it.  `--impl reference` times the FP64 CPU oracle instead.
+
+Prints ONE JSON line (rank 0).  For --gpus N > 1 (torchrun) every rank runs an independent
+replica of the workload (the plain sweep does not shard) and value sums them.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "zipf-69878x10677-10M-k10"
+METRIC = "Gibbs sweeps/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 ALU peak: 152 SMs x 2 FP64 FMA/clock x 2 FLOP x 2.07 GHz (unit count and maximum clock
+# of this GPU; a dependent-free DFMA loop measured 1.19 TFLOP/s, 1.89 FMA/clock/SM).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------------------
+def load_workload(name):
+    from paper_1703_00734_gb300 import synth
+    t = time.time()
+    d = synth.make_workload(name)
+    log(f"workload {name}: N={d['N']} D={d['D']} train={len(d['row'])} "
+        f"test={len(d['test_row'])} ({time.time() - t:.1f}s)")
+    return d
+
+
+def make_draws(d, K, nu0, n_sweeps, seed, out=None):
+    """n_sweeps of draw buffers for the single-subset (1 x 1) sampler."""
+    from paper_1703_00734_gb300 import synth
+    sizes = [(d["N"], d["D"])]
+    return np.concatenate([synth.sweep_draws(sizes, K, nu0, synth.rng_for(seed, 1, t))
+                           for t in range(n_sweeps)])
+
+
+def algorithmic(d, K, prec):
+    """Algorithmic work per launch of each kernel class (the cost terms of Section 4.3)."""
+    M = len(d["row"])
+    b = {"fp64": 8, "fp32": 4, "bf16": 2}[prec]
+    bval = 8 if prec == "fp64" else 4
+    per_obs = 4 + bval + K * b              # index + value + gathered partner row
+    nt = K * (K + 1) // 2
+    fma_row = nt + K + (K ** 3 - K) // 6 + K * (K - 1)   # assembly, Cholesky, two solves
+    return {
+        "gram_x": ("hbm", M * per_obs, "GB/s"),
+        "gram_w": ("hbm", M * per_obs, "GB/s"),
+        "cond_x": ("alu", 2.0 * fma_row * d["N"], "TFLOP/s"),
+        "cond_w": ("alu", 2.0 * fma_row * d["D"], "TFLOP/s"),
+    }
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1703_00734_gb300 import bmf
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    d = load_workload(args.workload)
+    K, tau = d["K"], d["tau"]
+    nu0 = float(K)
+    test = (d["test_row"], d["test_col"], d["test_val"])
+    W, S = args.warmup, args.steps
+
+    def context(prec):
+        return bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], K, tau, prec, X0=d["X0"],
+                       W0=d["W0"], test=test, burnin=args.burnin, seed=rank,
+                       stream=stream.cuda_stream)
+
+    per = None
+    # ---- headline: reduced-precision path, inputs resident ---------------------------
+    m = context(args.precision)
+    per = m.draws_per_sweep(1)
+    host = make_draws(d, K, nu0, W + S, seed=100 + rank)
+    assert host.size == per * (W + S)
+    dr = torch.from_numpy(host).to(dev)
+    m.sweep(0, W, dr[: W * per])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    n0 = m.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        st = m.sweep(0, S, dr[W * per:(W + S) * per])
+        e1.record(stream)
+        e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = m.launch_count() - n0
+    torch.cuda.synchronize()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    rmse_red = st["rmse_mean"]
+    # ---- per-kernel timing over the same number of steps (profiling pass) ------------
+    m.profile(True)
+    m.sweep(0, S, dr[W * per:(W + S) * per])
+    prof = m.profile_read()
+    m.profile(False)
+    # ---- e2e: host (pinned) draws copied in every step, stats read back ---------------
+    pinned = torch.from_numpy(host[W * per:(W + S) * per].copy()).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(S):
+        m.sweep(0, 1, pinned[k * per:(k + 1) * per])
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    m.close()
+    del dr
+    # ---- plain FP64 GPU sweep, same data and draws ------------------------------------
+    fp64 = None
+    if not args.no_fp64:
+        S64 = min(S, args.fp64_steps)
+        m64 = context("fp64")
+        dr64 = torch.from_numpy(host[: (W + S64) * per]).to(dev)
+        m64.sweep(0, W, dr64[: W * per])
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st64 = m64.sweep(0, S64, dr64[W * per:(W + S64) * per])
+        b.record(stream)
+        b.synchronize()
+        fp64 = {"sweeps_per_s": S64 / (a.elapsed_time(b) / 1e3), "steps": S64,
+                "rmse_mean": st64["rmse_mean"]}
+        m64.close()
+        del dr64
+    # RMSE of the reduced-precision chain at the same sweep count as the FP64 chain
+    rmse_same = None
+    if fp64 is not None:
+        mr = context(args.precision)
+        drr = torch.from_numpy(host[: (W + fp64["steps"]) * per]).to(dev)
+        str_ = mr.sweep(0, W + fp64["steps"], drr)
+        rmse_same = str_["rmse_mean"]
+        mr.close()
+        del drr
+    if rank != 0:
+        return None
+    sweeps_s = world * S / (ms / 1e3)
+    M = len(d["row"])
+    gflops = 2 * M * 2 * K * K * sweeps_s / 1e9
+    # roofline of the dominant kernel class
+    algo = algorithmic(d, K, args.precision)
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    kernels = {}
+    for name, (n, tot) in prof.items():
+        if n == 0:
+            continue
+        avg_ms = tot / n
+        ent = {"launches": n, "avg_us": avg_ms * 1e3, "share": None}
+        if name in algo:
+            bound, work, unit = algo[name]
+            ach = work / (avg_ms / 1e3) / (1e9 if unit == "GB/s" else 1e12)
+            peak = hbm if unit == "GB/s" else FP64_PEAK_TFLOPS
+            ent.update(bound=bound, achieved=ach, peak=peak, unit=unit, frac=ach / peak)
+        kernels[name] = ent
+    total = sum(v["avg_us"] * v["launches"] for v in kernels.values())
+    for v in kernels.values():
+        v["share"] = v["avg_us"] * v["launches"] / total if total else None
+    dom = max((k for k in kernels if "bound" in kernels[k]),
+              key=lambda k: kernels[k]["avg_us"] * kernels[k]["launches"])
+    kd = kernels[dom]
+    roof = {"kernel": dom, "bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
+            "unit": kd["unit"], "frac": kd["frac"], "traffic": traffic_for(dom, args.precision),
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if kd["unit"] == "GB/s"
+            else "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"}
+    out = {
+        "metric": METRIC, "value": sweeps_s, "unit": "sweeps/s", "n_gpus": world, "steps": S,
+        "warmup": W, "ms_per_step": ms / S, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.precision != "fp64" else "f64",
+        "data": "synthetic (seeded Zipf(1.2) rating matrix standing in for a MovieLens-shaped "
+                "data set; no real data available)",
+        "config": {"workload": WORKLOAD if args.workload == WORKLOAD else args.workload,
+                   "N": d["N"], "D": d["D"], "train_obs": M, "test_obs": len(d["test_row"]),
+                   "K": K, "tau": tau, "precision": args.precision, "grid": "1x1",
+                   "l2": "inputs larger than L2 (observation lists 144 MB > 129 MB L2)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "obsK2_gflops": gflops,
+        "rmse": {"reduced": rmse_red, "reduced_at_fp64_steps": rmse_same,
+                 "fp64": fp64["rmse_mean"] if fp64 else None,
+                 "abs_diff": abs(rmse_same - fp64["rmse_mean"]) if fp64 else None},
+        "fp64_plain": fp64,
+        "speedup_vs_fp64_plain": sweeps_s / world / fp64["sweeps_per_s"] if fp64 else None,
+        "roofline": roof,
+        "kernels": kernels,
+        "e2e": {"value": world * S / e2e_s, "unit": "sweeps/s",
+                "h2d_bytes_per_step": per * 8, "d2h_bytes_per_step": 8 + 16},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(d, args.cpu_seconds)
+    return out
+
+
+def traffic_for(kernel, prec):
+    """DRAM bytes per launch from the committed ncu summary, if one matches."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 4 and not line.startswith("#") and f[0] == kernel and f[1] == prec \
+                and f[2] == WORKLOAD:
+            return float(f[3])
+    return None
+
+
+# ---------------------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline / reference arm)
+# ---------------------------------------------------------------------------------------
+def oracle_sweeps(d, budget_s, max_sweeps, warmup=0):
+    import oracle
+    K = d["K"]
+    p = oracle.plan(d["N"], d["D"], d["row"], d["col"], d["val"], 1, 1)
+    s = p.subsets[0]
+    prior = oracle.NWPrior(K)
+    st = oracle.new_chain(d["X0"][p.row_perm], d["W0"][p.col_perm], K)
+    lay = oracle.stage_draw_layout([s], K)
+    H = oracle.hyper_block_len(K)
+
+    def one(t):
+        dr = make_draws(d, K, prior.nu0, 1, seed=900 + t)
+        oracle.sweep_subset(s, st, K, d["tau"], prior, dr[0:H], dr[H:2 * H],
+                            dr[lay[(0, "zx")]:lay[(0, "zx")] + s.n * K],
+                            dr[lay[(0, "zw")]:lay[(0, "zw")] + s.d * K])
+
+    for t in range(warmup):
+        one(t)
+    done, busy = 0, 0.0
+    while done < max_sweeps and (done == 0 or busy < budget_s):
+        t0 = time.perf_counter()
+        one(warmup + done)
+        busy += time.perf_counter() - t0
+        done += 1
+    return done, busy
+
+
+def cpu_baseline(d, budget):
+    n, secs = oracle_sweeps(d, budget, 1000)
+    return {"value": n / secs, "unit": "sweeps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} full FP64 oracle sweeps of the same workload, single thread "
+                      f"({secs:.1f} s, draw generation excluded)"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    d = load_workload(args.workload)
+    n, secs = oracle_sweeps(d, args.cpu_seconds * 4, max(args.steps, 1),
+                            warmup=min(args.warmup, 1))
+    v = n / secs
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "sweeps/s", "n_gpus": 1,
+            "steps": n, "warmup": min(args.warmup, 1), "ms_per_step": secs * 1e3 / n,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "K": d["K"],
+                                            "precision": "fp64", "grid": "1x1"},
+            "cpu_baseline": {"value": v, "unit": "sweeps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{n} full sweeps (time-bounded), single thread"},
+            "e2e": {"value": v, "unit": "sweeps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
+    ap.add_argument("--burnin", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=20)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+    else:
+        if world > 1:
+            import torch
+            torch.cuda.set_device(local_rank)
+            torch.distributed.init_process_group("nccl")
+        out = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

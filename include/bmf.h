@@ -106,7 +106,12 @@ typedef struct {
     int32_t thin;      /* keep every thin-th sweep after burn-in (>= 1) */
     uint64_t seed;     /* device generator seed (used when draws == NULL) */
     double eps_rel;    /* Algorithm 2 epsilon scale (<= 0: 1e-6) */
+    int32_t moments;   /* BMF_MOMENTS_AUTO: second moments (for moment matching) only when the
+                          grid has more than one subset; BMF_MOMENTS_MEAN: sums of x only (enough
+                          for posterior-mean prediction); BMF_MOMENTS_FULL: sums of x and x x^T */
 } bmf_config;
+
+enum { BMF_MOMENTS_AUTO = 0, BMF_MOMENTS_MEAN = 1, BMF_MOMENTS_FULL = 2 };
 
 typedef struct {
     const double *ptr; /* draw buffer (layout above), FP64 */
@@ -181,12 +186,12 @@ bmf_status bmf_get_state(bmf_ctx *ctx, int32_t subset, double *X, double *W, dou
 bmf_status bmf_set_state(bmf_ctx *ctx, int32_t subset, const double *X, const double *W);
 
 /* Moment sums of one subset: S1 [n*K], S2 [n*K*K] for factor BMF_FACTOR_X / _W, and the
- * number of retained samples. */
+ * number of retained samples.  S2 needs second moments (BMF_E_STATE otherwise). */
 bmf_status bmf_get_moments(bmf_ctx *ctx, int32_t subset, int32_t factor, double *S1, double *S2,
                            int64_t *kept);
 
 /* Per-row moment-matched posterior (mu [n*K], Lambda [n*K*K]) of one subset's factor, as
- * propagated to the next stage.  Valid once the subset's stage has been finalised. */
+ * propagated to the next stage (needs second moments; BMF_E_STATE otherwise). */
 bmf_status bmf_get_posterior(bmf_ctx *ctx, int32_t subset, int32_t factor, double *mu,
                              double *Lam);
 
@@ -198,6 +203,20 @@ bmf_status bmf_set_prior(bmf_ctx *ctx, int32_t subset, int32_t factor, const dou
 /* Grid geometry of one subset, and the reordering (new -> original index) of rows/columns. */
 bmf_status bmf_get_subset_info(const bmf_ctx *ctx, int32_t subset, bmf_subset_info *info);
 bmf_status bmf_get_perm(const bmf_ctx *ctx, int64_t *row_perm, int64_t *col_perm);
+
+/* Tracing.  With profiling on, bmf_sweep / bmf_stage record a pair of CUDA events on the
+ * context stream around every kernel launch and accumulate the elapsed time per kernel class
+ * ("stats", "hyper", "gram_x", "cond_x", "gram_w", "cond_w", "rmse").  bmf_profile_read copies
+ * up to `max` entries into `out`, returns how many classes there are and resets the totals.
+ * bmf_launch_count returns the number of kernels this context has launched since bmf_init. */
+typedef struct {
+    char name[16];
+    int64_t launches;
+    double total_ms;
+} bmf_kernel_time;
+bmf_status bmf_profile_enable(bmf_ctx *ctx, int32_t on);
+int32_t bmf_profile_read(bmf_ctx *ctx, bmf_kernel_time *out, int32_t max);
+int64_t bmf_launch_count(const bmf_ctx *ctx);
 
 void bmf_destroy(bmf_ctx *ctx);
 

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libbmf.so")
 BMF_FP64, BMF_FP32, BMF_BF16 = 0, 1, 2
 PRECISION = {"fp64": BMF_FP64, "fp32": BMF_FP32, "bf16": BMF_BF16}
 ORDER = {"none": 0, "decreasing": 1}
+MOMENTS = {"auto": 0, "mean": 1, "full": 2}
 FACTOR_X, FACTOR_W = 0, 1
 STATUS = {0: "BMF_OK", 1: "BMF_E_ARG", 2: "BMF_E_SHAPE", 3: "BMF_E_NOT_PD",
           4: "BMF_E_NONFINITE", 5: "BMF_E_TIMEOUT", 6: "BMF_E_OOM", 7: "BMF_E_CUDA",
@@ -31,7 +32,8 @@ class Config(ctypes.Structure):
                 ("beta0", ctypes.c_double), ("nu0", ctypes.c_double),
                 ("mu0", ctypes.POINTER(ctypes.c_double)), ("W0", ctypes.POINTER(ctypes.c_double)),
                 ("order", ctypes.c_int32), ("center", ctypes.c_int32), ("burnin", ctypes.c_int32),
-                ("thin", ctypes.c_int32), ("seed", ctypes.c_uint64), ("eps_rel", ctypes.c_double)]
+                ("thin", ctypes.c_int32), ("seed", ctypes.c_uint64), ("eps_rel", ctypes.c_double),
+                ("moments", ctypes.c_int32)]
 
 
 class Draws(ctypes.Structure):
@@ -41,6 +43,11 @@ class Draws(ctypes.Structure):
 class SweepStats(ctypes.Structure):
     _fields_ = [("rmse_sample", ctypes.c_double), ("rmse_mean", ctypes.c_double),
                 ("sweeps", ctypes.c_int64), ("kept", ctypes.c_int64)]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 16), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double)]
 
 
 class SubsetInfo(ctypes.Structure):
@@ -90,6 +97,12 @@ def load(path: str = LIB_PATH):
     L.bmf_get_subset_info.restype = st
     L.bmf_get_perm.argtypes = [P, P, P]
     L.bmf_get_perm.restype = st
+    L.bmf_profile_enable.argtypes = [P, i32]
+    L.bmf_profile_enable.restype = st
+    L.bmf_profile_read.argtypes = [P, ctypes.POINTER(KernelTime), i32]
+    L.bmf_profile_read.restype = i32
+    L.bmf_launch_count.argtypes = [P]
+    L.bmf_launch_count.restype = i64
     L.bmf_destroy.argtypes = [P]
     L.bmf_destroy.restype = None
     L.bmf_last_error.argtypes = [P]
@@ -113,7 +126,7 @@ class BMF:
     def __init__(self, N, D, row, col, val, K, tau, precision="fp64", I=1, J=1, row_bounds=None,
                  col_bounds=None, X0=None, W0=None, test=None, beta0=2.0, nu0=None, mu0=None,
                  W0_prior=None, order="decreasing", center=True, burnin=0, thin=1, seed=0,
-                 eps_rel=1e-6, stream=None):
+                 eps_rel=1e-6, moments="auto", stream=None):
         L = load()
         self.L = L
         self.N, self.D, self.K, self.I, self.J = int(N), int(D), int(K), int(I), int(J)
@@ -136,7 +149,8 @@ class BMF:
                      mu0=mu0a.ctypes.data_as(dp) if mu0a is not None else None,
                      W0=W0a.ctypes.data_as(dp) if W0a is not None else None,
                      order=ORDER[order], center=int(bool(center)), burnin=int(burnin),
-                     thin=int(thin), seed=int(seed), eps_rel=float(eps_rel))
+                     thin=int(thin), seed=int(seed), eps_rel=float(eps_rel),
+                     moments=MOMENTS[moments])
         self.precision = cfg.precision
         h = ctypes.c_void_p()
         st = L.bmf_init(ctypes.byref(h), ctypes.byref(cfg), N, D, len(row), _ptr(row), _ptr(col),
@@ -251,6 +265,17 @@ class BMF:
     def set_prior(self, s, factor, mu, Lam):
         mu, Lam = _arr(mu, np.float64), _arr(Lam, np.float64)
         self._check(self.L.bmf_set_prior(self.h, s, factor, _ptr(mu), _ptr(Lam)))
+
+    def profile(self, on=True):
+        self._check(self.L.bmf_profile_enable(self.h, int(bool(on))))
+
+    def profile_read(self):
+        buf = (KernelTime * 16)()
+        n = self.L.bmf_profile_read(self.h, buf, 16)
+        return {buf[k].name.decode(): (buf[k].launches, buf[k].total_ms) for k in range(n)}
+
+    def launch_count(self):
+        return int(self.L.bmf_launch_count(self.h))
 
     def close(self):
         if getattr(self, "h", None):

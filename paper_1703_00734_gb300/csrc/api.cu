@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/bmf.h"
+#include "bmf.h"
 #include "common.cuh"
 #include "kernels.h"
 #include "plan.h"
@@ -51,9 +51,22 @@ struct Side {
     void *val = nullptr;         // values (double or float)
     GramItem *items = nullptr;   // Gram work items in arena-row order
     int64_t *item_ptr = nullptr; // [R+1]
+    GramTask *tasks = nullptr;   // warp tasks, grouped per slot
+    std::vector<int64_t> slot_task;  // [S+1] first task of each slot
     std::vector<int64_t> h_item_ptr;
     int32_t *hslot = nullptr;    // [R] hyper slot or -1
     std::vector<int32_t> h_hslot;
+    // rows with more than one Gram work item, their FP64 sums
+    std::vector<int32_t> h_multi;     // arena rows, increasing
+    // conditional-kernel blocks: up to kCondBlock rows of one subset each, in slot order
+    std::vector<CondBlock> h_blocks;
+    std::vector<int64_t> slot_blk;    // [S+1] first block of each slot
+    CondBlock *blocks = nullptr;
+    StatChunk *chunks = nullptr;      // the same row ranges, for the standalone statistics pass
+    int64_t stat0 = 0;                // first statistics slot of this arena
+    int32_t *multi_idx = nullptr;     // [R] slot in rowsum or -1
+    int *counters = nullptr;          // [slots x parts] completion counters (zero when idle)
+    double *rowsum = nullptr;
     double *pL = nullptr, *pb = nullptr;            // per-row prior (SoA)
     double *S1 = nullptr, *S2 = nullptr;            // moment sums (SoA)
     double *mm_mu = nullptr, *mm_L = nullptr, *mm_b = nullptr;  // moment-matched posterior
@@ -68,6 +81,15 @@ struct SubState {
 }  // namespace
 
 struct bmf_ctx {
+    ~bmf_ctx()
+    {
+        if (st2) {
+            cudaStreamSynchronize(st2);
+            cudaStreamDestroy(st2);
+        }
+        for (cudaEvent_t e : {ev_fork, ev_fac[0], ev_fac[1], ev_hyp[0], ev_hyp[1]})
+            if (e) cudaEventDestroy(e);
+    }
     int K = 0, prec = BMF_FP64;
     double tau = 1.0, beta0 = 2.0, nu0 = 1.0, eps_rel = 1e-6;
     int burnin = 0, thin = 1;
@@ -75,6 +97,8 @@ struct bmf_ctx {
     std::vector<double> mu0, W0inv;
     HostPlan P;
     cudaStream_t st = nullptr;
+    cudaStream_t st2 = nullptr;      // side stream: factor statistics and hyperparameter draws
+    cudaEvent_t ev_fork = nullptr, ev_fac[2] = {nullptr, nullptr}, ev_hyp[2] = {nullptr, nullptr};
     int device = 0, sms = 1;
     DevMem mem;
     Side X, W;
@@ -84,13 +108,12 @@ struct bmf_ctx {
     double *hyper = nullptr;         // [2 * S slots]
     double *stats = nullptr;
     int64_t stats_cap = 0;           // chunks
-    StatChunk *d_chunks = nullptr;
     HyperJob *d_jobs = nullptr;
     double *mu0_d = nullptr, *W0inv_d = nullptr;
     int32_t *trow = nullptr, *tcol = nullptr;
     double *tval = nullptr, *ysum = nullptr;
     double *rmse_part = nullptr, *rmse_out = nullptr;
-    int rmse_blocks = 64;
+    int rmse_blocks = 608;
     DevError *err_d = nullptr;
     double *draws_d = nullptr;
     int64_t draws_cap = 0;
@@ -101,12 +124,65 @@ struct bmf_ctx {
     bool failed = false;
     std::string err;
     int chunk_obs = 1024;
-    int stat_rows = 512;
+    bool full_moments = false;
+    // tracing
+    int64_t launches = 0;
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+    size_t ev_used = 0;
+    double prof_ms[8] = {0};
+    int64_t prof_n[8] = {0};
 };
 
 namespace {
 
 constexpr int kHyperJobsMax = 1 << 16;
+
+enum { K_STATS = 0, K_HYPER, K_GRAM_X, K_COND_X, K_GRAM_W, K_COND_W, K_RMSE, K_NCLASS };
+const char *kClassName[K_NCLASS] = {"stats", "hyper", "gram_x", "cond_x", "gram_w", "cond_w", "rmse"};
+
+cudaEvent_t pool_event(bmf_ctx *c)
+{
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->ev_pool.push_back(e);
+    }
+    return c->ev_pool[c->ev_used++];
+}
+
+// Run `launch` (which enqueues `n` kernels) and, with profiling on, bracket it with events.
+template <typename F>
+void traced(bmf_ctx *c, cudaStream_t st, int cls, int n, F &&launch)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (c->prof) {
+        a = pool_event(c);
+        b = pool_event(c);
+        cudaEventRecord(a, st);
+    }
+    launch();
+    c->launches += n;
+    if (c->prof) {
+        cudaEventRecord(b, st);
+        c->ev_pending.push_back({cls, {a, b}});
+    }
+}
+
+// After a synchronisation: fold the pending event pairs into the per-class totals.
+void collect_profile(bmf_ctx *c)
+{
+    for (auto &p : c->ev_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess) {
+            c->prof_ms[p.first] += ms;
+            c->prof_n[p.first] += 1;
+        }
+    }
+    c->ev_pending.clear();
+    c->ev_used = 0;
+}
 
 bmf_status fail(bmf_ctx *c, bmf_status s, const std::string &m)
 {
@@ -211,6 +287,7 @@ bmf_status upload_hslots(bmf_ctx *c, int sl)
 
 bmf_status check_dev_error(bmf_ctx *c)
 {
+    if (c->st2) CUDA_TRY(c, cudaStreamSynchronize(c->st2));
     DevError h;
     CUDA_TRY(c, cudaMemcpyAsync(&h, c->err_d, sizeof(h), cudaMemcpyDeviceToHost, c->st));
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
@@ -266,6 +343,53 @@ bmf_status setup_side(bmf_ctx *c, Side &s, int64_t R, const std::vector<int64_t>
         }
     }
     s.h_item_ptr[R] = (int64_t)items.size();
+    std::vector<int32_t> midx(R, -1);
+    for (int64_t r = 0; r < R; ++r)
+        if (s.h_item_ptr[r + 1] - s.h_item_ptr[r] > 1) {
+            midx[r] = (int32_t)s.h_multi.size();
+            s.h_multi.push_back((int32_t)r);
+        }
+    const size_t nctr = s.h_multi.size() * (size_t)gram_parts(c->K, c->prec);
+    s.counters = c->mem.alloc<int>(nctr);
+    s.multi_idx = c->mem.alloc<int32_t>(R);
+    s.rowsum = c->mem.alloc<double>(s.h_multi.size() * (size_t)gram_nv(padded_k(c->K)));
+    if (!c->mem.ok) return fail(c, BMF_E_OOM, "device allocation failed (row sums)");
+    CUDA_TRY(c, cudaMemset(s.counters, 0, std::max<size_t>(nctr, 1) * sizeof(int)));
+    CUDA_TRY(c, cudaMemcpy(s.multi_idx, midx.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice));
+    // warp tasks per slot: long rows / row chunks one per warp, short rows packed 32/G per warp
+    {
+        const int S = (int)c->P.slot_sid.size();
+        const bool xs = &s == &c->X;
+        std::vector<GramTask> tasks;
+        s.slot_task.assign(S + 1, 0);
+        for (int sl = 0; sl < S; ++sl) {
+            s.slot_task[sl] = (int64_t)tasks.size();
+            const SubsetGeom &g = geom_of_slot(c, sl);
+            const int64_t r0 = xs ? g.xoff : g.woff, r1 = r0 + (xs ? g.n() : g.d());
+            GramTask cur{0, 0, 0};
+            for (int64_t r = r0; r < r1; ++r) {
+                const int64_t i0 = s.h_item_ptr[r], i1 = s.h_item_ptr[r + 1];
+                if (i1 == i0) continue;
+                const int G = (i1 - i0 > 1) ? 32 : gram_group(items[i0].count);
+                if (G == 32) {
+                    if (cur.n) tasks.push_back(cur), cur.n = 0;
+                    for (int64_t it = i0; it < i1; ++it) tasks.push_back(GramTask{it, 1, 32});
+                    continue;
+                }
+                if (cur.n && (cur.G != G || cur.n == 32 / cur.G || cur.item0 + cur.n != i0))
+                    tasks.push_back(cur), cur.n = 0;
+                if (!cur.n) cur = GramTask{i0, 0, G};
+                ++cur.n;
+            }
+            if (cur.n) tasks.push_back(cur);
+        }
+        s.slot_task[S] = (int64_t)tasks.size();
+        s.tasks = c->mem.alloc<GramTask>(tasks.size());
+        if (!c->mem.ok) return fail(c, BMF_E_OOM, "device allocation failed (tasks)");
+        if (!tasks.empty())
+            CUDA_TRY(c, cudaMemcpy(s.tasks, tasks.data(), tasks.size() * sizeof(GramTask),
+                                   cudaMemcpyHostToDevice));
+    }
     s.items = c->mem.alloc<GramItem>(items.size());
     s.item_ptr = c->mem.alloc<int64_t>(R + 1);
     if (!c->mem.ok) return fail(c, BMF_E_OOM, "device allocation failed (work items)");
@@ -347,65 +471,104 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
     const double *dr = nullptr;
     bmf_status s = stage_draws(c, draws, per * n_sweeps, &dr);
     if (s) return s;
-    // hyperparameter jobs: every factor block without a per-row prior
-    std::vector<StatChunk> chunks;
+    // hyperparameter jobs: every factor block without a per-row prior (X jobs first).  A job
+    // sums the statistics slots of its subset's conditional-kernel blocks, which the standalone
+    // statistics pass fills before the first sweep and the conditional kernel refreshes after.
     std::vector<HyperJob> jobs;
     const int64_t HB = hyper_block_len(K);
-    for (int sl = sl0; sl < sl1; ++sl) {
-        const SubsetGeom &g = geom_of_slot(c, sl);
-        const SubState &su = c->ss[g.sid];
-        for (int f = 0; f < 2; ++f) {
-            if (su.prior[f]) continue;
-            const int64_t base = f == 0 ? g.xoff : g.woff, n = f == 0 ? g.n() : g.d();
+    int nj[2] = {0, 0};
+    for (int f = 0; f < 2; ++f) {
+        const Side &sd = f == 0 ? c->X : c->W;
+        const size_t j0 = jobs.size();
+        for (int sl = sl0; sl < sl1; ++sl) {
+            const SubsetGeom &g = geom_of_slot(c, sl);
+            if (c->ss[g.sid].prior[f]) continue;
             HyperJob jb;
-            jb.chunk0 = (int32_t)chunks.size();
-            for (int64_t r = 0; r < n; r += c->stat_rows) {
-                StatChunk ch;
-                ch.r0 = base + r;
-                ch.r1 = base + std::min<int64_t>(n, r + c->stat_rows);
-                ch.out = (int32_t)chunks.size();
-                ch.arena = f;
-                chunks.push_back(ch);
-            }
-            jb.chunk1 = (int32_t)chunks.size();
+            jb.chunk0 = (int32_t)(sd.stat0 + sd.slot_blk[sl]);
+            jb.chunk1 = (int32_t)(sd.stat0 + sd.slot_blk[sl + 1]);
             jb.slot = 2 * sl + f;
             jb.draw = (int32_t)((2 * (sl - sl0) + f) * HB);
-            jb.n = n;
+            jb.n = f == 0 ? g.n() : g.d();
             jobs.push_back(jb);
         }
+        nj[f] = (int)(jobs.size() - j0);
     }
-    if ((int64_t)chunks.size() > c->stats_cap || (int64_t)jobs.size() > kHyperJobsMax)
-        return fail(c, BMF_E_ARG, "internal: statistics buffers too small");
-    if (!chunks.empty())
-        CUDA_TRY(c, cudaMemcpyAsync(c->d_chunks, chunks.data(), chunks.size() * sizeof(StatChunk),
-                                    cudaMemcpyHostToDevice, c->st));
+    if ((int64_t)jobs.size() > kHyperJobsMax)
+        return fail(c, BMF_E_ARG, "internal: too many hyperparameter jobs");
     if (!jobs.empty())
         CUDA_TRY(c, cudaMemcpyAsync(c->d_jobs, jobs.data(), jobs.size() * sizeof(HyperJob),
                                     cudaMemcpyHostToDevice, c->st));
     const int64_t hyper_len = 2 * (int64_t)(sl1 - sl0) * HB;
     const int64_t zx_len = (rx1 - rx0) * K;
     int64_t kept = c->ss[g0.sid].kept;
+    // (mu, Lambda) | factor for sweep `it`, on the side stream.  The statistics of X for sweep
+    // it+1 depend only on the X written by sweep it, so they run while the main stream does
+    // W | X of sweep it and the Gram pass of sweep it+1 (and symmetrically for W).
+    auto side_hyper = [&](int f, int it) -> bmf_status {
+        const double *d = dr + (int64_t)it * per;
+        const HyperJob *jb = c->d_jobs + (f == 0 ? 0 : nj[0]);
+        HyperParams hp{K, jb, nj[f], c->stats, c->mu0_d, c->beta0, c->nu0, c->W0inv_d, d,
+                       c->hyper, c->err_d};
+        traced(c, c->st2, K_HYPER, 1, [&] { launch_hyper(hp, c->st2); });
+        CUDA_TRY(c, cudaEventRecord(c->ev_hyp[f], c->st2));
+        return BMF_OK;
+    };
+    const bool hyp[2] = {nj[0] > 0, nj[1] > 0};
+    if (n_sweeps > 0 && (hyp[0] || hyp[1])) {
+        // statistics of the state at the start of the call (the conditional kernel keeps them
+        // current from then on)
+        CUDA_TRY(c, cudaEventRecord(c->ev_fork, c->st));
+        CUDA_TRY(c, cudaStreamWaitEvent(c->st2, c->ev_fork, 0));
+        for (int f = 0; f < 2; ++f) {
+            if (!hyp[f]) continue;
+            const Side &sd = f == 0 ? c->X : c->W;
+            const int64_t b0 = sd.slot_blk[sl0], b1 = sd.slot_blk[sl1];
+            traced(c, c->st2, K_STATS, 1, [&] {
+                launch_stats(K, sd.chunks + b0, (int)(b1 - b0), c->X.F, c->W.F, c->stats, c->st2);
+            });
+        }
+        for (int f = 0; f < 2; ++f)
+            if (hyp[f] && (s = side_hyper(f, 0))) return s;
+    }
     for (int it = 0; it < n_sweeps; ++it) {
         const double *d = dr + (int64_t)it * per;
         const int64_t t = t_start + it + 1;
         const bool keep = keep_sample(c, t);
         if (keep) ++kept;
-        // (mu, Lambda) | X and (mu, Lambda) | W from the state at the start of the sweep
-        launch_stats(K, c->d_chunks, (int)chunks.size(), c->X.F, c->W.F, c->stats, c->st);
-        HyperParams hp{K, c->d_jobs, (int)jobs.size(), c->stats, c->mu0_d, c->beta0, c->nu0,
-                       c->W0inv_d, d, c->hyper, c->err_d};
-        launch_hyper(hp, c->st);
         // X | W, then W | X
         for (int f = 0; f < 2; ++f) {
             Side &me = f == 0 ? c->X : c->W;
             Side &other = f == 0 ? c->W : c->X;
             const int64_t r0 = f == 0 ? rx0 : rw0, r1 = f == 0 ? rx1 : rw1;
             const int64_t i0 = me.h_item_ptr[r0], i1 = me.h_item_ptr[r1];
-            GramParams gp{me.items + i0, i1 - i0, me.idx, me.val, other.G, c->ldg, c->part,
-                          c->ld_part};
-            launch_gram(K, c->prec, gp, c->sms * 4, c->st);
+            GramParams gp;
+            gp.tasks = me.tasks + me.slot_task[sl0];
+            gp.n_tasks = me.slot_task[sl1] - me.slot_task[sl0];
+            gp.items = me.items + i0;
+            gp.n_items = i1 - i0;
+            gp.idx = me.idx;
+            gp.val = me.val;
+            gp.P = other.G;
+            gp.ldP = c->ldg;
+            gp.part = c->part;
+            gp.ld = c->ld_part;
+            gp.multi_idx = me.multi_idx;
+            gp.item_ptr = me.item_ptr;
+            gp.item0 = i0;
+            gp.counters = me.counters;
+            gp.nparts = gram_parts(K, c->prec);
+            gp.rowsum = me.rowsum;
+            gp.ld_sum = gram_nv(padded_k(K));
+            gp.nv = gram_nv(padded_k(K));
+            if (gp.n_tasks > 0)
+                traced(c, c->st, f == 0 ? K_GRAM_X : K_GRAM_W, 1,
+                       [&] { launch_gram(K, c->prec, gp, c->sms * 4, c->st); });
+            if (hyp[f]) CUDA_TRY(c, cudaStreamWaitEvent(c->st, c->ev_hyp[f], 0));
             CondParams cp;
             cp.K = K;
+            const int64_t b0 = me.slot_blk[sl0], b1 = me.slot_blk[sl1];
+            cp.blocks = me.blocks + b0;
+            cp.blk0 = me.stat0 + b0;
             cp.row0 = r0;
             cp.row1 = r1;
             cp.item_ptr = me.item_ptr;
@@ -413,6 +576,9 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
             cp.part = c->part;
             cp.ld = c->ld_part;
             cp.part_rhs = ntri(padded_k(K));
+            cp.multi_idx = me.multi_idx;
+            cp.rowsum = me.rowsum;
+            cp.ld_sum = gram_nv(padded_k(K));
             cp.tau = c->tau;
             cp.row_hslot = me.hslot;
             cp.hyper = c->hyper;
@@ -424,16 +590,27 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
             cp.Xg = me.G;
             cp.ldg = c->ldg;
             cp.keep = keep ? 1 : 0;
+            cp.full = c->full_moments ? 1 : 0;
             cp.S1 = me.S1;
             cp.S2 = me.S2;
+            cp.stats = c->stats;
             cp.err = c->err_d;
-            launch_cond(c->prec, cp, c->st);
+            if (b1 > b0)
+                traced(c, c->st, f == 0 ? K_COND_X : K_COND_W, 1,
+                       [&] { launch_cond(c->prec, cp, (int)(b1 - b0), c->st); });
+            if (hyp[f] && it + 1 < n_sweeps) {
+                CUDA_TRY(c, cudaEventRecord(c->ev_fac[f], c->st));
+                CUDA_TRY(c, cudaStreamWaitEvent(c->st2, c->ev_fac[f], 0));
+                if ((s = side_hyper(f, it + 1))) return s;
+            }
         }
         if (tt1 > tt0) {
             RmseParams rp{K, c->prec, tt0, tt1, c->trow, c->tcol, c->tval, c->X.G, c->W.G, c->ldg,
                           keep ? 1 : 0, c->ysum, (double)kept, c->rmse_part};
-            launch_rmse(rp, c->rmse_blocks, c->st);
-            launch_rmse_final(c->rmse_part, c->rmse_blocks, c->rmse_out, c->st);
+            traced(c, c->st, K_RMSE, 2, [&] {
+                launch_rmse(rp, c->rmse_blocks, c->st);
+                launch_rmse_final(c->rmse_part, c->rmse_blocks, c->rmse_out, c->st);
+            });
         }
     }
     CUDA_TRY(c, cudaGetLastError());
@@ -444,6 +621,7 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
         su.finalized = false;
     }
     s = check_dev_error(c);
+    if (c->prof) collect_profile(c);
     if (s) return s;
     if (stats) {
         stats->sweeps = t_start + n_sweeps;
@@ -472,6 +650,8 @@ bmf_status finalize_stage(bmf_ctx *c, int stage)
         if (su.kept < 1)
             return fail(c, BMF_E_STATE, "subset " + std::to_string(g.sid) +
                                             " has no retained samples (burn-in not passed)");
+        if (!c->full_moments)
+            return fail(c, BMF_E_STATE, "moment matching needs second moments (moments mode)");
         for (int f = 0; f < 2; ++f) {
             Side &sd = f == 0 ? c->X : c->W;
             MMParams mp{c->K, f == 0 ? g.xoff : g.woff,
@@ -672,6 +852,12 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
     c->thin = cfg->thin;
     c->seed = cfg->seed;
     c->st = static_cast<cudaStream_t>(stream);
+    if (cfg->moments < BMF_MOMENTS_AUTO || cfg->moments > BMF_MOMENTS_FULL) {
+        g_init_error = "unknown moments mode";
+        delete c;
+        return BMF_E_ARG;
+    }
+    c->full_moments = cfg->moments == BMF_MOMENTS_FULL || (cfg->moments == BMF_MOMENTS_AUTO && I * J > 1);
     c->mu0.assign(K, 0.0);
     if (cfg->mu0) std::memcpy(c->mu0.data(), cfg->mu0, K * sizeof(double));
     std::vector<double> W0((size_t)K * K, 0.0);
@@ -698,6 +884,14 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
     for (int64_t e = 0; e < D * K; ++e)
         if (!std::isfinite(W0init[e])) return bail(BMF_E_NONFINITE, "non-finite W0init");
     if (cudaGetDevice(&c->device) != cudaSuccess) return bail(BMF_E_CUDA, "no CUDA device");
+    {
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        bool ok = cudaStreamCreateWithPriority(&c->st2, cudaStreamNonBlocking, hi) == cudaSuccess;
+        for (cudaEvent_t *e : {&c->ev_fork, &c->ev_fac[0], &c->ev_fac[1], &c->ev_hyp[0], &c->ev_hyp[1]})
+            ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) return bail(BMF_E_CUDA, "stream/event creation failed");
+    }
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
     c->ldg = gather_ld(K, c->prec);
     c->ld_part = gram_part_ld(K, c->prec);
@@ -715,10 +909,45 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
     const size_t pbytes = c->prec == BMF_FP64 ? 8 : 4;
     c->part = c->mem.alloc<char>(std::max<int64_t>(c->part_cap, 1) * c->ld_part * pbytes);
     c->hyper = c->mem.alloc<double>((size_t)2 * S * hyper_slot_len(K));
-    c->stats_cap = (c->P.RX + c->P.RW) / c->stat_rows + 2 * S + 2;
+    // block tables (subset-aligned) and the statistics slots they fill
+    for (int f = 0; f < 2; ++f) {
+        Side &sd = f == 0 ? c->X : c->W;
+        sd.slot_blk.assign(S + 1, 0);
+        for (int sl = 0; sl < S; ++sl) {
+            const SubsetGeom &g = geom_of_slot(c, sl);
+            sd.slot_blk[sl] = (int64_t)sd.h_blocks.size();
+            const int64_t base = f == 0 ? g.xoff : g.woff, n = f == 0 ? g.n() : g.d();
+            for (int64_t q = 0; q < n; q += kCondBlock) {
+                CondBlock b;
+                b.row0 = base + q;
+                b.n = (int32_t)std::min<int64_t>(kCondBlock, n - q);
+                b.pad = 0;
+                sd.h_blocks.push_back(b);
+            }
+        }
+        sd.slot_blk[S] = (int64_t)sd.h_blocks.size();
+    }
+    c->W.stat0 = (int64_t)c->X.h_blocks.size();
+    c->stats_cap = (int64_t)(c->X.h_blocks.size() + c->W.h_blocks.size());
     c->stats = c->mem.alloc<double>(c->stats_cap * (K + ntri(K)));
-    c->d_chunks = c->mem.alloc<StatChunk>(c->stats_cap);
     c->d_jobs = c->mem.alloc<HyperJob>(kHyperJobsMax);
+    for (int f = 0; f < 2; ++f) {
+        Side &sd = f == 0 ? c->X : c->W;
+        std::vector<StatChunk> ch(sd.h_blocks.size());
+        for (size_t b = 0; b < ch.size(); ++b) {
+            ch[b].r0 = sd.h_blocks[b].row0;
+            ch[b].r1 = sd.h_blocks[b].row0 + sd.h_blocks[b].n;
+            ch[b].out = (int32_t)(sd.stat0 + (int64_t)b);
+            ch[b].arena = f;
+        }
+        sd.blocks = c->mem.alloc<CondBlock>(sd.h_blocks.size());
+        sd.chunks = c->mem.alloc<StatChunk>(ch.size());
+        if (!c->mem.ok) return bail(BMF_E_OOM, "device allocation failed (block tables)");
+        if (!ch.empty()) {
+            cudaMemcpy(sd.blocks, sd.h_blocks.data(), ch.size() * sizeof(CondBlock), cudaMemcpyHostToDevice);
+            cudaMemcpy(sd.chunks, ch.data(), ch.size() * sizeof(StatChunk), cudaMemcpyHostToDevice);
+        }
+    }
     c->mu0_d = c->mem.alloc<double>(K);
     c->W0inv_d = c->mem.alloc<double>((size_t)K * K);
     const int64_t nt = (int64_t)c->P.trow.size();
@@ -931,6 +1160,8 @@ bmf_status bmf_get_moments(bmf_ctx *c, int32_t subset, int32_t factor, double *S
                                    cudaMemcpyDeviceToHost));
             for (int64_t r = 0; r < n; ++r) S1[r * K + i] = col[r];
         }
+    if (S2 && !c->full_moments)
+        return fail(c, BMF_E_STATE, "second moments are not accumulated (moments mode)");
     if (S2)
         for (int e = 0; e < NT && n; ++e) {
             CUDA_TRY(c, cudaMemcpy(col.data(), sd.S2 + (int64_t)e * sd.R + base, n * sizeof(double),
@@ -954,6 +1185,8 @@ bmf_status bmf_get_posterior(bmf_ctx *c, int32_t subset, int32_t factor, double 
         const SubsetGeom &g = c->P.subs[subset];
         SubState &su = c->ss[subset];
         if (su.kept < 1) return fail(c, BMF_E_STATE, "no retained samples");
+        if (!c->full_moments)
+            return fail(c, BMF_E_STATE, "moment matching needs second moments (moments mode)");
         for (int f = 0; f < 2; ++f) {
             Side &sd = f == 0 ? c->X : c->W;
             MMParams mp{c->K, f == 0 ? g.xoff : g.woff, f == 0 ? g.xoff + g.n() : g.woff + g.d(),
@@ -1044,11 +1277,37 @@ bmf_status bmf_get_perm(const bmf_ctx *c, int64_t *row_perm, int64_t *col_perm)
     return BMF_OK;
 }
 
+bmf_status bmf_profile_enable(bmf_ctx *c, int32_t on)
+{
+    if (!c) return BMF_E_ARG;
+    c->prof = on != 0;
+    return BMF_OK;
+}
+
+int32_t bmf_profile_read(bmf_ctx *c, bmf_kernel_time *out, int32_t max)
+{
+    if (!c) return -1;
+    for (int k = 0; k < K_NCLASS && k < max && out; ++k) {
+        std::memset(out[k].name, 0, sizeof(out[k].name));
+        std::strncpy(out[k].name, kClassName[k], sizeof(out[k].name) - 1);
+        out[k].launches = c->prof_n[k];
+        out[k].total_ms = c->prof_ms[k];
+    }
+    for (int k = 0; k < K_NCLASS; ++k) {
+        c->prof_ms[k] = 0.0;
+        c->prof_n[k] = 0;
+    }
+    return K_NCLASS;
+}
+
+int64_t bmf_launch_count(const bmf_ctx *c) { return c ? c->launches : -1; }
+
 void bmf_destroy(bmf_ctx *c)
 {
     if (!c) return;
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->draws_d) cudaFree(c->draws_d);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
 }
 

@@ -5,7 +5,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
-#include "../../include/bmf.h"
+#include "bmf.h"
 
 namespace bmf {
 
@@ -27,6 +27,14 @@ struct GramItem {
     int64_t begin;
     int32_t count;
     int32_t row;
+};
+
+// A warp task of the Gram-gather pass: items item0 .. item0 + n - 1, one per group of G lanes
+// (G = 32 with n = 1 for long rows and row chunks; G = 16 or 8 with n = 32 / G short rows).
+struct GramTask {
+    int64_t item0;
+    int32_t n;
+    int32_t G;
 };
 
 // Device error word bits (set by kernels, read by the host at sync points).

@@ -30,7 +30,19 @@ __device__ __forceinline__ __nv_bfloat16 to_gather<__nv_bfloat16>(double x)
     return __double2bfloat16(x);
 }
 
-constexpr int kCondBlock = 64;
+// FP32 -> FP64 by rebuilding the IEEE-754 fields on the integer pipe (exact for every normal
+// float; zeros, subnormals, infinities and NaNs take the hardware conversion).  On this GPU the
+// conversion instruction occupies the FP64 pipe, which this kernel is bound by.
+__device__ __forceinline__ double widen(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const uint32_t hi = (u & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((u & 0x7fffffu) >> 3);
+    const uint32_t lo = u << 29;
+    return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double widen(double d) { return d; }
 
 // Shared-memory slots per thread: the packed matrix (ntri(K)), the right-hand side / solution
 // (K) and the reciprocal pivots (K).
@@ -41,113 +53,146 @@ __global__ void __launch_bounds__(kCondBlock) cond_kernel(CondParams a)
 {
     extern __shared__ double sm[];
     const int t = threadIdx.x;
-    const int64_t r = a.row0 + (int64_t)blockIdx.x * kCondBlock + t;
-    if (r >= a.row1) return;
+    const CondBlock blk = a.blocks[blockIdx.x];
+    const int64_t r = blk.row0 + t;
+    const bool active = t < blk.n;
     const int K = a.K;
     const int NT = ntri(K);
     const int64_t R = a.R;
     double *M = sm + t;                       // M[e * kCondBlock] is entry e of this thread
 #define SM(e) M[(e) * kCondBlock]
     const int B0 = NT, RI = NT + K;           // rhs/solution at B0 + i, reciprocal pivot at RI + i
-    // 1. G_n and r_n: FP64 sum of the row's Gram partials (fixed item order).  The partial
-    //    entries use the packed index of the padded width; tri(i, j) does not depend on it.
-    const AT *part = static_cast<const AT *>(a.part);
-    const int prhs = a.part_rhs;
-    for (int e = 0; e < NT + K; ++e) SM(e) = 0.0;
-    const int64_t i0 = a.item_ptr[r], i1 = a.item_ptr[r + 1];
-    for (int64_t it = i0; it < i1; ++it) {
-        const AT *p = part + (it - a.item0) * (int64_t)a.ld;
-        for (int e = 0; e < NT; ++e) SM(e) += (double)p[e];
-        for (int i = 0; i < K; ++i) SM(B0 + i) += (double)p[prhs + i];
-    }
-    // 2. assemble with the prior: a shared hyperparameter slot or a per-row propagated prior
-    const int h = a.row_hslot[r];
-    const double tau = a.tau;
-    if (h >= 0) {
-        const double *hp = a.hyper + (int64_t)h * hyper_slot_len(K);
-        for (int e = 0; e < NT; ++e) SM(e) = fma(tau, SM(e), hp[K + e]);
-        for (int i = 0; i < K; ++i) SM(B0 + i) = fma(tau, SM(B0 + i), hp[K + NT + i]);
-    } else {
-        for (int e = 0; e < NT; ++e) SM(e) = fma(tau, SM(e), a.prior_L[(int64_t)e * R + r]);
-        for (int i = 0; i < K; ++i) SM(B0 + i) = fma(tau, SM(B0 + i), a.prior_b[(int64_t)i * R + r]);
-    }
-    // 3. Cholesky (Crout order: column j from the columns before it)
-    for (int j = 0; j < K; ++j) {
-        const int jj = tri(j, 0);
-        double d = SM(jj + j);
-        for (int k = 0; k < j; ++k) {
-            const double l = SM(jj + k);
-            d = fma(-l, l, d);
+    bool ok = active;
+    if (active) {
+        // 1. G_n and r_n: the row's single Gram partial, or the FP64 sum of its partials made by
+        //    the Gram pass for rows split over several items.  The partial entries use the packed
+        //    index of the padded width; tri(i, j) does not depend on it.
+        const int prhs = a.part_rhs;
+        const int64_t i0 = a.item_ptr[r], i1 = a.item_ptr[r + 1];
+        const int mi = a.multi_idx[r];
+        if (mi >= 0) {
+            const double *p = a.rowsum + (int64_t)mi * a.ld_sum;
+            for (int e = 0; e < NT; ++e) SM(e) = p[e];
+            for (int i = 0; i < K; ++i) SM(B0 + i) = p[prhs + i];
+        } else if (i1 > i0) {
+            const AT *p = static_cast<const AT *>(a.part) + (i0 - a.item0) * (int64_t)a.ld;
+            for (int e = 0; e < NT; ++e) SM(e) = widen(p[e]);
+            for (int i = 0; i < K; ++i) SM(B0 + i) = widen(p[prhs + i]);
+        } else {
+            for (int e = 0; e < NT + K; ++e) SM(e) = 0.0;
         }
-        if (!(d > 0.0)) {
-            atomicOr(&a.err->flags, ERR_NOT_PD);
-            atomicMin(&a.err->first_bad_row, (int)r);
-            return;
+        // 2. assemble with the prior: a shared hyperparameter slot or a per-row propagated prior
+        const int h = a.row_hslot[r];
+        const double tau = a.tau;
+        if (h >= 0) {
+            const double *hp = a.hyper + (int64_t)h * hyper_slot_len(K);
+            for (int e = 0; e < NT; ++e) SM(e) = fma(tau, SM(e), hp[K + e]);
+            for (int i = 0; i < K; ++i) SM(B0 + i) = fma(tau, SM(B0 + i), hp[K + NT + i]);
+        } else {
+            for (int e = 0; e < NT; ++e) SM(e) = fma(tau, SM(e), a.prior_L[(int64_t)e * R + r]);
+            for (int i = 0; i < K; ++i)
+                SM(B0 + i) = fma(tau, SM(B0 + i), a.prior_b[(int64_t)i * R + r]);
         }
-        const double rs = rsqrt(d);
-        SM(RI + j) = rs;
-        SM(jj + j) = d * rs;
-        for (int i = j + 1; i < K; ++i) {
+        // 3. Cholesky (Crout order: column j from the columns before it)
+        for (int j = 0; j < K && ok; ++j) {
+            const int jj = tri(j, 0);
+            double d = SM(jj + j);
+            for (int k = 0; k < j; ++k) {
+                const double l = SM(jj + k);
+                d = fma(-l, l, d);
+            }
+            if (!(d > 0.0)) {
+                atomicOr(&a.err->flags, ERR_NOT_PD);
+                atomicMin(&a.err->first_bad_row, (int)r);
+                ok = false;
+                break;
+            }
+            const double rs = rsqrt(d);
+            SM(RI + j) = rs;
+            SM(jj + j) = d * rs;
+            for (int i = j + 1; i < K; ++i) {
+                const int ii = tri(i, 0);
+                double s = SM(ii + j);
+                for (int k = 0; k < j; ++k) s = fma(-SM(ii + k), SM(jj + k), s);
+                SM(ii + j) = s * rs;
+            }
+        }
+    }
+    if (ok) {
+        // 4. forward solve L y = b
+        for (int i = 0; i < K; ++i) {
             const int ii = tri(i, 0);
-            double s = SM(ii + j);
-            for (int k = 0; k < j; ++k) s = fma(-SM(ii + k), SM(jj + k), s);
-            SM(ii + j) = s * rs;
+            double s = SM(B0 + i);
+            for (int k = 0; k < i; ++k) s = fma(-SM(ii + k), SM(B0 + k), s);
+            SM(B0 + i) = s * SM(RI + i);
         }
-    }
-    // 4. forward solve L y = b
-    for (int i = 0; i < K; ++i) {
-        const int ii = tri(i, 0);
-        double s = SM(B0 + i);
-        for (int k = 0; k < i; ++k) s = fma(-SM(ii + k), SM(B0 + k), s);
-        SM(B0 + i) = s * SM(RI + i);
-    }
-    // 5. back solve L^T x = y + z
-    const double *z = a.z + (r - a.row0) * K;
-    for (int i = K - 1; i >= 0; --i) {
-        double s = SM(B0 + i) + z[i];
-        for (int k = i + 1; k < K; ++k) s = fma(-SM(tri(k, i)), SM(B0 + k), s);
-        SM(B0 + i) = s * SM(RI + i);
-    }
-    // 6. state, gathered copy, moment sums
-    double *xr = a.X + r * K;
-    GT *g = static_cast<GT *>(a.Xg) + r * a.ldg;
-    for (int i = 0; i < K; ++i) {
-        const double xi = SM(B0 + i);
-        xr[i] = xi;
-        g[i] = to_gather<GT>(xi);
-    }
-    for (int i = K; i < a.ldg; ++i) g[i] = to_gather<GT>(0.0);
-    if (a.keep) {
+        // 5. back solve L^T x = y + z
+        const double *z = a.z + (r - a.row0) * K;
+        for (int i = K - 1; i >= 0; --i) {
+            double s = SM(B0 + i) + z[i];
+            for (int k = i + 1; k < K; ++k) s = fma(-SM(tri(k, i)), SM(B0 + k), s);
+            SM(B0 + i) = s * SM(RI + i);
+        }
+        // 6. state, gathered copy, moment sums
+        double *xr = a.X + r * K;
+        GT *g = static_cast<GT *>(a.Xg) + r * a.ldg;
         for (int i = 0; i < K; ++i) {
             const double xi = SM(B0 + i);
-            a.S1[(int64_t)i * R + r] += xi;
-            for (int j = 0; j <= i; ++j) a.S2[(int64_t)tri(i, j) * R + r] += xi * SM(B0 + j);
+            xr[i] = xi;
+            g[i] = to_gather<GT>(xi);
         }
+        for (int i = K; i < a.ldg; ++i) g[i] = to_gather<GT>(0.0);
+        if (a.keep) {
+            for (int i = 0; i < K; ++i) {
+                const double xi = SM(B0 + i);
+                a.S1[(int64_t)i * R + r] += xi;
+                if (a.full)
+                    for (int j = 0; j <= i; ++j) a.S2[(int64_t)tri(i, j) * R + r] += xi * SM(B0 + j);
+            }
+        }
+    } else {
+        for (int i = 0; i < K; ++i) SM(B0 + i) = 0.0;
+    }
+    // 7. statistics of the new state for the next hyperparameter draw: per block, sum x and
+    //    the packed lower sum x x^T over the block's rows (thread e computes entry e, in row order)
+    __syncthreads();
+    const int NS = K + NT;
+    double *out = a.stats + (a.blk0 + blockIdx.x) * (int64_t)NS;
+    for (int e = t; e < NS; e += kCondBlock) {
+        double s = 0.0;
+        if (e < K) {
+            for (int q = 0; q < blk.n; ++q) s += sm[(B0 + e) * kCondBlock + q];
+        } else {
+            int i = 0;
+            while ((i + 1) * (i + 2) / 2 <= e - K) ++i;
+            const int j = e - K - i * (i + 1) / 2;
+            for (int q = 0; q < blk.n; ++q)
+                s = fma(sm[(B0 + i) * kCondBlock + q], sm[(B0 + j) * kCondBlock + q], s);
+        }
+        out[e] = s;
     }
 #undef SM
 }
 
 template <typename GT, typename AT>
-static void launch_cond_t(const CondParams &a, cudaStream_t st)
+static void launch_cond_t(const CondParams &a, int n_blocks, cudaStream_t st)
 {
     const size_t smem = (size_t)cond_slots(a.K) * kCondBlock * sizeof(double);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(cond_kernel<GT, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-    const int64_t n = a.row1 - a.row0;
-    const int grid = (int)((n + kCondBlock - 1) / kCondBlock);
-    cond_kernel<GT, AT><<<grid, kCondBlock, smem, st>>>(a);
+    cond_kernel<GT, AT><<<n_blocks, kCondBlock, smem, st>>>(a);
 }
 
-void launch_cond(int prec, const CondParams &a, cudaStream_t st)
+void launch_cond(int prec, const CondParams &a, int n_blocks, cudaStream_t st)
 {
-    if (a.row1 <= a.row0) return;
+    if (n_blocks <= 0) return;
     if (prec == BMF_FP64)
-        launch_cond_t<double, double>(a, st);
+        launch_cond_t<double, double>(a, n_blocks, st);
     else if (prec == BMF_FP32)
-        launch_cond_t<float, float>(a, st);
+        launch_cond_t<float, float>(a, n_blocks, st);
     else
-        launch_cond_t<__nv_bfloat16, float>(a, st);
+        launch_cond_t<__nv_bfloat16, float>(a, n_blocks, st);
 }
 
 }  // namespace bmf

@@ -16,8 +16,13 @@ int gather_ld(int K, int prec);
 // Gram entries per work item in the partial buffer.
 int gram_part_ld(int K, int prec);
 
+// Lanes per row of the Gram-gather pass for a row of `count` observations.
+int gram_group(int64_t count);
+
 struct GramParams {
-    const GramItem *items;
+    const GramTask *tasks;
+    int64_t n_tasks;
+    const GramItem *items;     // items of the launch: absolute item i at items[i - item0]
     int64_t n_items;
     const int32_t *idx;   // observation partner index (arena row of the partner factor)
     const void *val;      // observation values (double for FP64, float otherwise)
@@ -25,18 +30,39 @@ struct GramParams {
     int ldP;
     void *part;           // partial Gram per item [n_items x ld] (double for FP64, float else)
     int ld;
+    // rows split over several items (see gram.cu)
+    const int32_t *multi_idx;  // [R] slot of a multi-item row, else -1
+    const int64_t *item_ptr;   // [R+1] absolute item index of each row
+    int64_t item0;             // absolute index of items[0]
+    int *counters;             // [slots x nparts], zero between launches
+    int nparts;
+    double *rowsum;            // [slots x ld_sum]
+    int ld_sum;
+    int nv;                    // entries per partial
 };
 void launch_gram(int K, int prec, const GramParams &a, int grid, cudaStream_t st);
 int gram_parts(int K, int prec);
 
+// A block of the conditional kernel: up to 64 consecutive arena rows of one subset.
+struct CondBlock {
+    int64_t row0;
+    int32_t n;
+    int32_t pad;
+};
+
 struct CondParams {
     int K;
+    const CondBlock *blocks;     // this launch's blocks (one CUDA block each)
+    int64_t blk0;                // absolute index of blocks[0] (stats partial slot)
     int64_t row0, row1;          // arena rows of this launch
     const int64_t *item_ptr;     // [R+1] first work item of each arena row
     int64_t item0;               // item index of part[0]
     const void *part;            // Gram partials (see GramParams)
     int ld;
     int part_rhs;                // offset of the right-hand side within a partial
+    const int32_t *multi_idx;    // [R] slot in rowsum of a row with >= 2 items, else -1
+    const double *rowsum;        // FP64 sums of multi-item rows [slots x ld_sum]
+    int ld_sum;
     double tau;
     const int32_t *row_hslot;    // [R] hyper slot of the row, or -1 for a per-row prior
     const double *hyper;         // [slots x hyper_slot_len(K)]
@@ -48,11 +74,15 @@ struct CondParams {
     void *Xg;                    // gathered copy [R x ldg]
     int ldg;
     int keep;                    // accumulate moments
+    int full;                    // also second moments
     double *S1;                  // SoA [K][R]
     double *S2;                  // SoA [ntri(K)][R]
+    double *stats;               // per-block sums of x and x x^T of the new state
+                                 // [blocks x (K + ntri(K))], at slot blk0 + blockIdx.x
     DevError *err;
 };
-void launch_cond(int prec, const CondParams &a, cudaStream_t st);
+void launch_cond(int prec, const CondParams &a, int n_blocks, cudaStream_t st);
+constexpr int kCondBlock = 64;
 
 // Per-chunk sums for the hyperparameter step: for each chunk, sum x and the packed lower
 // sum x x^T over rows [r0, r1) of an FP64 arena.

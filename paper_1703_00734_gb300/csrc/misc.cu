@@ -276,17 +276,58 @@ void launch_hyper(const HyperParams &a, cudaStream_t st)
 // ------------------------------------------------------------------------------------------
 // Predictive RMSE of the current sample and of the running mean (Section 5.2).
 // ------------------------------------------------------------------------------------------
-template <typename GT, typename AT>
+// Dot product of two gathered rows (ldg elements, zero padded) with 16-byte vector loads.
+__device__ __forceinline__ float dot_rows(const float *x, const float *w, int ldg)
+{
+    const float4 *a = reinterpret_cast<const float4 *>(x), *b = reinterpret_cast<const float4 *>(w);
+    float s = 0.f;
+    for (int v = 0; v < ldg / 4; ++v) {
+        const float4 p = __ldg(a + v), q = __ldg(b + v);
+        s = fmaf(p.x, q.x, s);
+        s = fmaf(p.y, q.y, s);
+        s = fmaf(p.z, q.z, s);
+        s = fmaf(p.w, q.w, s);
+    }
+    return s;
+}
+__device__ __forceinline__ double dot_rows(const double *x, const double *w, int ldg)
+{
+    const double2 *a = reinterpret_cast<const double2 *>(x), *b = reinterpret_cast<const double2 *>(w);
+    double s = 0.0;
+    for (int v = 0; v < ldg / 2; ++v) {
+        const double2 p = __ldg(a + v), q = __ldg(b + v);
+        s = fma(p.x, q.x, s);
+        s = fma(p.y, q.y, s);
+    }
+    return s;
+}
+__device__ __forceinline__ float dot_rows(const __nv_bfloat16 *x, const __nv_bfloat16 *w, int ldg)
+{
+    const uint4 *a = reinterpret_cast<const uint4 *>(x), *b = reinterpret_cast<const uint4 *>(w);
+    float s = 0.f;
+    for (int v = 0; v < ldg / 8; ++v) {
+        uint4 p = __ldg(a + v), q = __ldg(b + v);
+        const __nv_bfloat162 *pp = reinterpret_cast<const __nv_bfloat162 *>(&p);
+        const __nv_bfloat162 *qq = reinterpret_cast<const __nv_bfloat162 *>(&q);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const float2 u = __bfloat1622float2(pp[h]), t = __bfloat1622float2(qq[h]);
+            s = fmaf(u.x, t.x, s);
+            s = fmaf(u.y, t.y, s);
+        }
+    }
+    return s;
+}
+
+template <typename GT>
 __global__ void __launch_bounds__(256) rmse_kernel(RmseParams a)
 {
     const GT *Xg = static_cast<const GT *>(a.Xg), *Wg = static_cast<const GT *>(a.Wg);
     double s0 = 0.0, s1 = 0.0;
     for (int64_t e = a.t0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.t1;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const GT *x = Xg + (int64_t)a.trow[e] * a.ldg, *w = Wg + (int64_t)a.tcol[e] * a.ldg;
-        AT p = 0;
-        for (int k = 0; k < a.K; ++k) p += (AT)x[k] * (AT)w[k];
-        const double yh = (double)p;
+        const double yh = (double)dot_rows(Xg + (int64_t)a.trow[e] * a.ldg,
+                                           Wg + (int64_t)a.tcol[e] * a.ldg, a.ldg);
         const double d0 = a.tval[e] - yh;
         s0 += d0 * d0;
         double ys = a.ysum[e];
@@ -316,32 +357,45 @@ __global__ void __launch_bounds__(256) rmse_kernel(RmseParams a)
     }
 }
 
-__global__ void rmse_final_kernel(const double *partial, int blocks, double *out2)
+// Deterministic final sum: each thread sums a fixed strided subset, then a fixed tree.
+__global__ void __launch_bounds__(256) rmse_final_kernel(const double *partial, int blocks,
+                                                         double *out2)
 {
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int k = 0; k < blocks; ++k) {
-            a += partial[2 * k];
-            b += partial[2 * k + 1];
+    __shared__ double red[2][256];
+    double a = 0.0, b = 0.0;
+    for (int k = threadIdx.x; k < blocks; k += 256) {
+        a += partial[2 * k];
+        b += partial[2 * k + 1];
+    }
+    red[0][threadIdx.x] = a;
+    red[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + o];
+            red[1][threadIdx.x] += red[1][threadIdx.x + o];
         }
-        out2[0] = a;
-        out2[1] = b;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out2[0] = red[0][0];
+        out2[1] = red[1][0];
     }
 }
 
 void launch_rmse(const RmseParams &a, int blocks, cudaStream_t st)
 {
     if (a.prec == BMF_FP64)
-        rmse_kernel<double, double><<<blocks, 256, 0, st>>>(a);
+        rmse_kernel<double><<<blocks, 256, 0, st>>>(a);
     else if (a.prec == BMF_FP32)
-        rmse_kernel<float, float><<<blocks, 256, 0, st>>>(a);
+        rmse_kernel<float><<<blocks, 256, 0, st>>>(a);
     else
-        rmse_kernel<__nv_bfloat16, float><<<blocks, 256, 0, st>>>(a);
+        rmse_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(a);
 }
 
 void launch_rmse_final(const double *partial, int blocks, double *out2, cudaStream_t st)
 {
-    rmse_final_kernel<<<1, 32, 0, st>>>(partial, blocks, out2);
+    rmse_final_kernel<<<1, 256, 0, st>>>(partial, blocks, out2);
 }
 
 // ------------------------------------------------------------------------------------------

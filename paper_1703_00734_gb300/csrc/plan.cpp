@@ -6,7 +6,7 @@
 #include <cmath>
 #include <numeric>
 
-#include "../../include/bmf.h"
+#include "bmf.h"
 
 namespace bmf {
 

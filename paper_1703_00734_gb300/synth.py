@@ -35,32 +35,31 @@ def uniform_pairs(N: int, D: int, M: int, rng) -> tuple[np.ndarray, np.ndarray]:
         raise ValueError("more pairs than cells")
     keys = rng.choice(N * D, size=M, replace=False) if N * D <= 50_000_000 else None
     if keys is None:
-        keys = _distinct_keys(lambda m: rng.integers(0, N, m) * D + rng.integers(0, D, m), M)
+        keys = _distinct_keys(lambda m: rng.integers(0, N, m) * D + rng.integers(0, D, m), M,
+                              N * D)
     return (keys // D).astype(np.int32), (keys % D).astype(np.int32)
 
 
-def _distinct_keys(draw, M):
+def _distinct_keys(draw, M, ncells):
     """Draw keys in rounds, keeping the first occurrence of each new key in draw order, until
-    exactly M distinct keys exist."""
-    have = np.empty(0, np.int64)
-    sorted_have = np.empty(0, np.int64)
+    exactly M distinct keys exist (membership in a bitset over all cells)."""
+    bits = np.zeros((ncells + 63) // 64, np.uint64)
+    parts = []
     need = M
     accept = 1.0
     while need > 0:
-        m = int(min(max(need / max(accept, 0.02) * 1.1 + 1024, 1024), 4 * M + 1024))
+        m = int(min(max(need / max(accept, 0.02) * 1.05 + 1024, 1024), 4 * M + 1024))
         cand = np.asarray(draw(m), np.int64)
-        pos = np.searchsorted(sorted_have, cand)
-        pos = np.minimum(pos, max(len(sorted_have) - 1, 0))
-        old = (sorted_have[pos] == cand) if len(sorted_have) else np.zeros(len(cand), bool)
-        cand = cand[~old]
+        word, bit = cand >> 6, (cand & 63).astype(np.uint64)
+        fresh = ((bits[word] >> bit) & np.uint64(1)) == 0
+        cand = cand[fresh]
         _, first = np.unique(cand, return_index=True)
-        cand = cand[np.sort(first)]
-        take = cand[:need]
+        take = cand[np.sort(first)][:need]
+        np.bitwise_or.at(bits, take >> 6, np.left_shift(np.uint64(1), (take & 63).astype(np.uint64)))
         accept = max(len(take) / m, 1e-3)
-        have = np.concatenate([have, take])
-        sorted_have = np.sort(have)
-        need = M - len(have)
-    return have
+        parts.append(take)
+        need -= len(take)
+    return np.concatenate(parts) if parts else np.empty(0, np.int64)
 
 
 def zipf_weights(n: int, s: float, rng) -> np.ndarray:
@@ -69,19 +68,34 @@ def zipf_weights(n: int, s: float, rng) -> np.ndarray:
     return w / w.sum()
 
 
+def _inverse_cdf(cdf, u, guide):
+    """Index of the first cdf entry >= u (same result as searchsorted), found from a guide table
+    (Chen & Asau 1974): start at the first index of u's bucket and step forward."""
+    L, n = len(guide), len(cdf)
+    i = np.minimum(guide[np.minimum((u * L).astype(np.int64), L - 1)], n - 1)
+    act = np.nonzero(cdf[i] < u)[0]
+    while len(act):
+        act = act[i[act] < n - 1]
+        i[act] += 1
+        act = act[cdf[i[act]] < u[act]]
+    return i
+
+
 def zipf_pairs(N: int, D: int, M: int, s_row: float, s_col: float, rng):
     """M distinct pairs from the capped product model (module docstring)."""
     p = np.cumsum(zipf_weights(N, s_row, rng))
     q = np.cumsum(zipf_weights(D, s_col, rng))
     p /= p[-1]
     q /= q[-1]
+    gp = np.searchsorted(p, np.arange(16 * N) / (16 * N))
+    gq = np.searchsorted(q, np.arange(16 * D) / (16 * D))
 
     def draw(m):
-        r = np.minimum(np.searchsorted(p, rng.random(m)), N - 1)
-        c = np.minimum(np.searchsorted(q, rng.random(m)), D - 1)
+        r = _inverse_cdf(p, rng.random(m), gp)
+        c = _inverse_cdf(q, rng.random(m), gq)
         return r.astype(np.int64) * D + c
 
-    keys = _distinct_keys(draw, M)
+    keys = _distinct_keys(draw, M, N * D)
     return (keys // D).astype(np.int32), (keys % D).astype(np.int32)
 
 

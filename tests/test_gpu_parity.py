@@ -39,7 +39,7 @@ def test_single_transition_fp64(K):
 
 def test_multi_sweep_fp64_with_moments():
     d = small(K=4, N=257, D=129, M=5000, seed=7)
-    pr = Pair(d, 4, burnin=2, thin=2)
+    pr = Pair(d, 4, burnin=2, thin=2, moments="full")
     stats = pr.run_stage(1, 8)
     pr.compare_subset(0, rel=1e-8)
     S1, S2, kept = pr.m.get_moments(0, 0)
