@@ -220,7 +220,32 @@ int64_t bmf_launch_count(const bmf_ctx *ctx);
 
 void bmf_destroy(bmf_ctx *ctx);
 
-/* Message of the last failed call on ctx (or of the last failed bmf_init when ctx is NULL). */
+/* Aggregation without allocating (no counterpart in the paper: a deployment addition).
+ * Some callers cannot let a library call cudaMalloc: code running while a CUDA graph is being
+ * captured, or a runtime that owns all device memory through its own allocator.  This call
+ * combines, for R rows, the per-row Gaussians of J submodels by Eq. 14 with the eigenvalue
+ * correction of Algorithm 2 (the same operation bmf_posterior_means applies to a context's
+ * moment-matched subset posteriors) and allocates nothing: its per-row working matrices live in
+ * a static device array of BMF_AGGREGATE_STATIC_MAX_DOUBLES doubles (32 MiB) that every GPU
+ * loading this library holds until the process exits.
+ *   mu:  device [J][R][K], Lam: device [J][R][K][K] (full symmetric precisions); submodel 0 is
+ *        the one whose posterior was propagated to the others;
+ *   mu_star: device [R][K] output; n_corrected: host, nullable (corrected (row, j) pairs);
+ *   eps_rel as in bmf_config (<= 0: 1e-6); stream: cudaStream_t or NULL.
+ * Limits: 1 <= K <= 16, J >= 1, R * K * K <= BMF_AGGREGATE_STATIC_MAX_DOUBLES (else
+ * BMF_E_SHAPE; split the rows over several calls).  Returns BMF_E_NOT_PD if an aggregated
+ * precision is not positive definite.  The call waits for its stream before returning.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All calls share the
+ * array (each call clears its counters first); calls that overlap on the GPU race on it.
+ * Errors are reported by bmf_last_error(NULL). */
+#define BMF_AGGREGATE_STATIC_MAX_DOUBLES 4194272
+bmf_status bmf_aggregate_static(int32_t K, int64_t R, int32_t J, const double *mu,
+                                const double *Lam, double eps_rel, double *mu_star,
+                                int64_t *n_corrected, void *stream);
+
+/* Message of the last failed call on ctx; with ctx NULL, of the last failed call of this thread
+ * that takes no context (bmf_init, bmf_aggregate_static). */
 const char *bmf_last_error(const bmf_ctx *ctx);
 
 #ifdef __cplusplus

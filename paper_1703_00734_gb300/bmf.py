@@ -103,6 +103,8 @@ def load(path: str = LIB_PATH):
     L.bmf_profile_read.restype = i32
     L.bmf_launch_count.argtypes = [P]
     L.bmf_launch_count.restype = i64
+    L.bmf_aggregate_static.argtypes = [i32, i64, i32, P, P, f64, P, ctypes.POINTER(i64), P]
+    L.bmf_aggregate_static.restype = st
     L.bmf_destroy.argtypes = [P]
     L.bmf_destroy.restype = None
     L.bmf_last_error.argtypes = [P]
@@ -117,6 +119,18 @@ def _arr(a, dtype):
 
 def _ptr(a):
     return None if a is None else a.ctypes.data
+
+
+def aggregate_static(K, R, J, mu_ptr, lam_ptr, out_ptr, eps_rel=1e-6, stream=None):
+    """bmf_aggregate_static on device pointers (see include/bmf.h): Eq. 14 / Algorithm 2 over J
+    submodels for R rows, allocating nothing.  Returns the number of corrected pairs."""
+    L = load()
+    nc = ctypes.c_int64()
+    st = L.bmf_aggregate_static(int(K), int(R), int(J), mu_ptr, lam_ptr, float(eps_rel), out_ptr,
+                                ctypes.byref(nc), ctypes.c_void_p(stream) if stream else None)
+    if st:
+        raise BmfError(st, L.bmf_last_error(None).decode())
+    return nc.value
 
 
 class BMF:

@@ -18,6 +18,7 @@ using namespace bmf;
 namespace {
 
 thread_local std::string g_init_error;
+thread_local const char *g_noctx_msg = nullptr;  // set by context-less calls that do not allocate
 
 struct DevMem {
     std::vector<void *> ptrs;
@@ -805,6 +806,10 @@ bool valid_subset(const bmf_ctx *c, int32_t s) { return s >= 0 && s < (int32_t)c
 
 }  // namespace
 
+namespace bmf {
+void set_noctx_error(const char *m) { g_noctx_msg = m; }
+}
+
 // ==========================================================================================
 // C ABI
 // ==========================================================================================
@@ -818,6 +823,7 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
                     void *stream)
 {
     g_init_error.clear();
+    g_noctx_msg = nullptr;
     if (!out || !cfg || !X0 || !W0init) {
         g_init_error = "null argument";
         return BMF_E_ARG;
@@ -1313,7 +1319,7 @@ void bmf_destroy(bmf_ctx *c)
 
 const char *bmf_last_error(const bmf_ctx *c)
 {
-    if (!c) return g_init_error.c_str();
+    if (!c) return g_noctx_msg ? g_noctx_msg : g_init_error.c_str();
     return c->err.c_str();
 }
 
