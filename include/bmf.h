@@ -93,7 +93,7 @@ enum { BMF_FACTOR_X = 0, BMF_FACTOR_W = 1 };
 #define BMF_MAX_K 64
 
 typedef struct {
-    int32_t K;         /* latent dimension, 1..BMF_MAX_K */
+    int32_t K;         /* latent dimension, 1..BMF_MAX_K (Gibbs sweeps: K <= 16 in this build) */
     int32_t precision; /* BMF_FP64 / BMF_FP32 / BMF_BF16 */
     double tau;        /* noise precision (Eq. 3), > 0 */
     double beta0;      /* Normal-Wishart beta0 > 0 */
@@ -203,6 +203,32 @@ bmf_status bmf_set_prior(bmf_ctx *ctx, int32_t subset, int32_t factor, const dou
 /* Grid geometry of one subset, and the reordering (new -> original index) of rows/columns. */
 bmf_status bmf_get_subset_info(const bmf_ctx *ctx, int32_t subset, bmf_subset_info *info);
 bmf_status bmf_get_perm(const bmf_ctx *ctx, int64_t *row_perm, int64_t *col_perm);
+
+/* Adjoint of the masked log-joint of one subset (a project addition; the paper samples with
+ * Gibbs only):
+ *   l = -(a/2) sum_{Omega} (y - x_n^T w_d)^2 + (|Omega|/2) log a
+ *       - 1/2 sum_n (x_n - mu_n)^T L_n (x_n - mu_n) - 1/2 sum_d (w_d - mu_d)^T L_d (w_d - mu_d),
+ * a = exp(log_alpha), (mu, L) the rows' current priors in the subset (its last hyperparameter
+ * draw, or the propagated per-row Gaussians); y are the centred training values.  The value is
+ * returned up to an additive constant (the terms mu^T L mu are dropped).
+ *   X: device [n_rows x ld], W: device [n_cols x ld], FP32, in the subset's local (reordered)
+ *      order, 16-byte aligned, ld >= K and ld % 4 == 0 (padding is ignored);
+ *   gX, gW: device, same layouts (padding written as 0); value, g_log_alpha: host, nullable.
+ * FP32 arithmetic with FP64 scalar sums; deterministic.  1 <= K <= 64. */
+bmf_status bmf_logjoint_grad(bmf_ctx *ctx, int32_t subset, const float *X, const float *W,
+                             int64_t ld, double log_alpha, float *gX, float *gW,
+                             double *g_log_alpha, double *value);
+
+/* n_steps Langevin moves on caller-owned FP32 factors (layouts as in bmf_logjoint_grad), beside
+ * the Gibbs sweep: theta' = theta + (eps/2) grad l(theta) + sqrt(eps) xi.  With uniforms == NULL
+ * every proposal is taken (unadjusted Langevin); otherwise a Metropolis-Hastings test with the
+ * host uniforms[n_steps] accepts or rejects each proposal (MALA).
+ *   noise: device FP32 [n_steps][(n_rows + n_cols) * K] standard normals (X rows then W rows);
+ *   accepted: host, nullable (number of accepted proposals); value: host, nullable (log-joint
+ *   at the final state). */
+bmf_status bmf_langevin(bmf_ctx *ctx, int32_t subset, int32_t n_steps, float *X, float *W,
+                        int64_t ld, double log_alpha, double eps, const float *noise,
+                        const double *uniforms, int32_t *accepted, double *value);
 
 /* Tracing.  With profiling on, bmf_sweep / bmf_stage record a pair of CUDA events on the
  * context stream around every kernel launch and accumulate the elapsed time per kernel class

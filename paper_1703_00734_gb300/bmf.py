@@ -103,6 +103,12 @@ def load(path: str = LIB_PATH):
     L.bmf_profile_read.restype = i32
     L.bmf_launch_count.argtypes = [P]
     L.bmf_launch_count.restype = i64
+    L.bmf_logjoint_grad.argtypes = [P, i32, P, P, i64, f64, P, P, ctypes.POINTER(f64),
+                                    ctypes.POINTER(f64)]
+    L.bmf_logjoint_grad.restype = st
+    L.bmf_langevin.argtypes = [P, i32, i32, P, P, i64, f64, f64, P, P, ctypes.POINTER(i32),
+                               ctypes.POINTER(f64)]
+    L.bmf_langevin.restype = st
     L.bmf_aggregate_static.argtypes = [i32, i64, i32, P, P, f64, P, ctypes.POINTER(i64), P]
     L.bmf_aggregate_static.restype = st
     L.bmf_destroy.argtypes = [P]
@@ -279,6 +285,24 @@ class BMF:
     def set_prior(self, s, factor, mu, Lam):
         mu, Lam = _arr(mu, np.float64), _arr(Lam, np.float64)
         self._check(self.L.bmf_set_prior(self.h, s, factor, _ptr(mu), _ptr(Lam)))
+
+    def logjoint_grad(self, s, X_ptr, W_ptr, ld, log_alpha, gX_ptr, gW_ptr):
+        """Masked log-joint of subset s at device FP32 factors (see include/bmf.h); gradients
+        into gX/gW (device); returns (value, d value / d log alpha)."""
+        v, ga = ctypes.c_double(), ctypes.c_double()
+        self._check(self.L.bmf_logjoint_grad(self.h, s, X_ptr, W_ptr, int(ld), float(log_alpha),
+                                             gX_ptr, gW_ptr, ctypes.byref(ga), ctypes.byref(v)))
+        return v.value, ga.value
+
+    def langevin(self, s, n_steps, X_ptr, W_ptr, ld, log_alpha, eps, noise_ptr, uniforms=None):
+        """n_steps Langevin moves (MALA when uniforms are given) on device FP32 factors;
+        returns (accepted, final log-joint)."""
+        u = None if uniforms is None else _arr(uniforms, np.float64)
+        acc, v = ctypes.c_int32(), ctypes.c_double()
+        self._check(self.L.bmf_langevin(self.h, s, int(n_steps), X_ptr, W_ptr, int(ld),
+                                        float(log_alpha), float(eps), noise_ptr, _ptr(u),
+                                        ctypes.byref(acc), ctypes.byref(v)))
+        return acc.value, v.value
 
     def profile(self, on=True):
         self._check(self.L.bmf_profile_enable(self.h, int(bool(on))))

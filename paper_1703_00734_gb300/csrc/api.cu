@@ -126,6 +126,14 @@ struct bmf_ctx {
     std::string err;
     int chunk_obs = 1024;
     bool full_moments = false;
+    // adjoint / Langevin scratch (allocated on first use)
+    float *adj_part = nullptr;
+    int64_t adj_part_cap = 0;
+    double *adj_sums = nullptr;
+    int64_t adj_sums_cap = 0;
+    float *fval[2] = {nullptr, nullptr};     // FP32 values for FP64 contexts
+    float *lg_buf = nullptr;                 // Langevin proposals and gradients
+    int64_t lg_cap = 0;
     // tracing
     int64_t launches = 0;
     bool prof = false;
@@ -139,9 +147,10 @@ struct bmf_ctx {
 namespace {
 
 constexpr int kHyperJobsMax = 1 << 16;
+constexpr int kSweepMaxK = 16;
 
-enum { K_STATS = 0, K_HYPER, K_GRAM_X, K_COND_X, K_GRAM_W, K_COND_W, K_RMSE, K_NCLASS };
-const char *kClassName[K_NCLASS] = {"stats", "hyper", "gram_x", "cond_x", "gram_w", "cond_w", "rmse"};
+enum { K_STATS = 0, K_HYPER, K_GRAM_X, K_COND_X, K_GRAM_W, K_COND_W, K_RMSE, K_ADJ, K_NCLASS };
+const char *kClassName[K_NCLASS] = {"stats", "hyper", "gram_x", "cond_x", "gram_w", "cond_w", "rmse", "adjoint"};
 
 cudaEvent_t pool_event(bmf_ctx *c)
 {
@@ -459,6 +468,9 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
 {
     if (c->failed) return fail(c, BMF_E_STATE, "context is in a failed state; call bmf_set_state");
     if (n_sweeps < 0) return fail(c, BMF_E_ARG, "n_sweeps < 0");
+    if (c->K > kSweepMaxK)
+        return fail(c, BMF_E_ARG, "Gibbs sweeps support K <= " + std::to_string(kSweepMaxK) +
+                                      " in this build (the adjoint supports K <= 64)");
     const int K = c->K;
     const SubsetGeom &g0 = geom_of_slot(c, sl0), &gl = geom_of_slot(c, sl1 - 1);
     const int64_t t_start = c->ss[g0.sid].t;
@@ -830,8 +842,8 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
     }
     *out = nullptr;
     const int K = cfg->K;
-    if (K < 1 || K > 16) {
-        g_init_error = "K must be in 1..16 in this build";
+    if (K < 1 || K > BMF_MAX_K) {
+        g_init_error = "K must be in 1..64";
         return BMF_E_ARG;
     }
     if (cfg->precision < BMF_FP64 || cfg->precision > BMF_BF16) {
@@ -913,7 +925,7 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
     std::vector<double>().swap(c->P.cval);
     const int S = I * J;
     const size_t pbytes = c->prec == BMF_FP64 ? 8 : 4;
-    c->part = c->mem.alloc<char>(std::max<int64_t>(c->part_cap, 1) * c->ld_part * pbytes);
+    c->part = c->mem.alloc<char>(K <= kSweepMaxK ? std::max<int64_t>(c->part_cap, 1) * c->ld_part * pbytes : 1);
     c->hyper = c->mem.alloc<double>((size_t)2 * S * hyper_slot_len(K));
     // block tables (subset-aligned) and the statistics slots they fill
     for (int f = 0; f < 2; ++f) {
@@ -1308,12 +1320,219 @@ int32_t bmf_profile_read(bmf_ctx *c, bmf_kernel_time *out, int32_t max)
 
 int64_t bmf_launch_count(const bmf_ctx *c) { return c ? c->launches : -1; }
 
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Adjoint of the masked log-joint and Langevin moves
+// ------------------------------------------------------------------------------------------
+namespace {
+
+template <typename T>
+bmf_status grow(bmf_ctx *c, T *&p, int64_t &cap, int64_t need)
+{
+    if (need <= cap) return BMF_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    if (cudaMalloc(&p, std::max<int64_t>(need, 1) * sizeof(T)) != cudaSuccess)
+        return fail(c, BMF_E_OOM, "device allocation failed (adjoint scratch)");
+    cap = need;
+    return BMF_OK;
+}
+
+struct LogJoint {
+    double r2 = 0.0, quad = 0.0, value = 0.0, g_log_alpha = 0.0;
+};
+
+// Gradient of the subset's log-joint at (X, W) into (gX, gW); scalar parts on the host.
+bmf_status logjoint(bmf_ctx *c, int32_t subset, const float *X, const float *W, int64_t ld,
+                    double log_alpha, float *gX, float *gW, LogJoint &out)
+{
+    const SubsetGeom &g = c->P.subs[subset];
+    const int K = c->K, kt = adjoint_kt(K), ldp = adjoint_ld(K);
+    const double alpha = std::exp(log_alpha);
+    int64_t need_part = 0, nb[2];
+    for (int f = 0; f < 2; ++f) {
+        const Side &me = f == 0 ? c->X : c->W;
+        const int64_t r0 = f == 0 ? g.xoff : g.woff, r1 = r0 + (f == 0 ? g.n() : g.d());
+        need_part = std::max(need_part, (me.h_item_ptr[r1] - me.h_item_ptr[r0]) * ldp);
+        nb[f] = adjoint_row_blocks(r1 - r0);
+    }
+    bmf_status s = grow(c, c->adj_part, c->adj_part_cap, need_part);
+    if (!s) s = grow(c, c->adj_sums, c->adj_sums_cap, 2 * (nb[0] + nb[1]));
+    if (s) return s;
+    for (int f = 0; f < 2 && c->prec == BMF_FP64; ++f)
+        if (!c->fval[f]) {
+            const int64_t nnz = c->P.nnz;
+            if (cudaMalloc(&c->fval[f], std::max<int64_t>(nnz, 1) * sizeof(float)) != cudaSuccess)
+                return fail(c, BMF_E_OOM, "device allocation failed (FP32 values)");
+            launch_to_float(static_cast<const double *>((f == 0 ? c->X : c->W).val), c->fval[f], nnz, c->st);
+        }
+    for (int f = 0; f < 2; ++f) {
+        const Side &me = f == 0 ? c->X : c->W;
+        const int64_t r0 = f == 0 ? g.xoff : g.woff, r1 = r0 + (f == 0 ? g.n() : g.d());
+        const int64_t i0 = me.h_item_ptr[r0], i1 = me.h_item_ptr[r1];
+        AdjointParams ap;
+        ap.K = K;
+        ap.kt = kt;
+        ap.ldp = ldp;
+        ap.items = me.items + i0;
+        ap.n_items = i1 - i0;
+        ap.item_base = i0;
+        ap.idx = me.idx;
+        ap.val = c->prec == BMF_FP64 ? c->fval[f] : static_cast<const float *>(me.val);
+        ap.self = f == 0 ? X : W;
+        ap.other = f == 0 ? W : X;
+        ap.ld = ld;
+        ap.self0 = r0;
+        ap.other0 = f == 0 ? g.woff : g.xoff;
+        ap.part = c->adj_part;
+        ap.n_rows = r1 - r0;
+        ap.item_ptr = me.item_ptr;
+        ap.row_hslot = me.hslot;
+        ap.hyper = c->hyper;
+        ap.prior_L = me.pL;
+        ap.prior_b = me.pb;
+        ap.R = me.R;
+        ap.grad = f == 0 ? gX : gW;
+        ap.alpha = alpha;
+        ap.count_r2 = f == 0 ? 1 : 0;
+        ap.block_sums = c->adj_sums + (f == 0 ? 0 : 2 * nb[0]);
+        traced(c, c->st, K_ADJ, 2, [&] { launch_adjoint(ap, c->sms * 4, c->st); });
+    }
+    CUDA_TRY(c, cudaGetLastError());
+    std::vector<double> h(2 * (nb[0] + nb[1]));
+    CUDA_TRY(c, cudaMemcpyAsync(h.data(), c->adj_sums, h.size() * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    out.r2 = out.quad = 0.0;
+    for (int64_t b = 0; b < nb[0] + nb[1]; ++b) {
+        out.r2 += h[2 * b];
+        out.quad += h[2 * b + 1];
+    }
+    const double M = (double)g.nnz;
+    out.value = -0.5 * alpha * out.r2 + 0.5 * M * log_alpha - 0.5 * out.quad;
+    out.g_log_alpha = 0.5 * M - 0.5 * alpha * out.r2;
+    return BMF_OK;
+}
+
+double sqdiff(bmf_ctx *c, const float *a, const float *b, const float *g, double coef, int64_t n,
+              int64_t ld, bmf_status &st)
+{
+    const int blocks = 256;
+    st = grow(c, c->adj_sums, c->adj_sums_cap, (int64_t)blocks);
+    if (st) return 0.0;
+    launch_sqdiff(a, b, g, coef, n, c->K, ld, c->adj_sums, blocks, c->st);
+    std::vector<double> h(blocks);
+    if (cudaMemcpyAsync(h.data(), c->adj_sums, blocks * sizeof(double), cudaMemcpyDeviceToHost,
+                        c->st) != cudaSuccess ||
+        cudaStreamSynchronize(c->st) != cudaSuccess) {
+        st = fail(c, BMF_E_CUDA, "CUDA error in the Langevin test");
+        return 0.0;
+    }
+    double s = 0.0;
+    for (double v : h) s += v;
+    return s;
+}
+
+bool check_factor_layout(const void *p, int64_t ld, int K)
+{
+    return p && ld >= K && ld % 4 == 0 && (reinterpret_cast<uintptr_t>(p) % 16) == 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+bmf_status bmf_logjoint_grad(bmf_ctx *c, int32_t subset, const float *X, const float *W,
+                             int64_t ld, double log_alpha, float *gX, float *gW,
+                             double *g_log_alpha, double *value)
+{
+    if (!c) return BMF_E_ARG;
+    if (!valid_subset(c, subset)) return fail(c, BMF_E_ARG, "subset out of range");
+    if (c->K > 64) return fail(c, BMF_E_ARG, "the adjoint needs K <= 64");
+    if (!check_factor_layout(X, ld, c->K) || !check_factor_layout(W, ld, c->K) ||
+        !check_factor_layout(gX, ld, c->K) || !check_factor_layout(gW, ld, c->K))
+        return fail(c, BMF_E_ARG, "factors must be 16-byte aligned with ld >= K and ld % 4 == 0");
+    if (!std::isfinite(log_alpha)) return fail(c, BMF_E_NONFINITE, "non-finite log_alpha");
+    LogJoint lj;
+    bmf_status s = logjoint(c, subset, X, W, ld, log_alpha, gX, gW, lj);
+    if (s) return s;
+    if (c->prof) collect_profile(c);
+    if (value) *value = lj.value;
+    if (g_log_alpha) *g_log_alpha = lj.g_log_alpha;
+    return BMF_OK;
+}
+
+bmf_status bmf_langevin(bmf_ctx *c, int32_t subset, int32_t n_steps, float *X, float *W,
+                        int64_t ld, double log_alpha, double eps, const float *noise,
+                        const double *uniforms, int32_t *accepted, double *value)
+{
+    if (!c) return BMF_E_ARG;
+    if (!valid_subset(c, subset)) return fail(c, BMF_E_ARG, "subset out of range");
+    if (n_steps < 0 || !(eps > 0) || !noise) return fail(c, BMF_E_ARG, "need n_steps >= 0, eps > 0, noise");
+    if (c->K > 64) return fail(c, BMF_E_ARG, "Langevin moves need K <= 64");
+    if (!check_factor_layout(X, ld, c->K) || !check_factor_layout(W, ld, c->K))
+        return fail(c, BMF_E_ARG, "factors must be 16-byte aligned with ld >= K and ld % 4 == 0");
+    const SubsetGeom &g = c->P.subs[subset];
+    const int64_t n = g.n(), d = g.d(), K = c->K;
+    const int64_t sx = n * ld, sw = d * ld;
+    // buffers: gradient at the current state (gX, gW), proposal (pX, pW), its gradient (qX, qW)
+    bmf_status s = grow(c, c->lg_buf, c->lg_cap, 3 * (sx + sw) + 8);
+    if (s) return s;
+    float *gX = c->lg_buf, *gW = gX + sx, *pX = gW + sw, *pW = pX + sx, *qX = pW + sw, *qW = qX + sx;
+    LogJoint cur, prop;
+    s = logjoint(c, subset, X, W, ld, log_alpha, gX, gW, cur);
+    if (s) return s;
+    int32_t acc = 0;
+    for (int32_t it = 0; it < n_steps; ++it) {
+        const float *xi = noise + (int64_t)it * (n + d) * K;
+        CUDA_TRY(c, cudaMemcpyAsync(pX, X, sx * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+        CUDA_TRY(c, cudaMemcpyAsync(pW, W, sw * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+        traced(c, c->st, K_ADJ, 2, [&] {
+            launch_langevin(pX, gX, xi, n, (int)K, (int)ld, (float)eps, c->st);
+            launch_langevin(pW, gW, xi + n * K, d, (int)K, (int)ld, (float)eps, c->st);
+        });
+        s = logjoint(c, subset, pX, pW, ld, log_alpha, qX, qW, prop);
+        if (s) return s;
+        bool take = true;
+        if (uniforms) {
+            // log A = l' - l + log q(theta | theta') - log q(theta' | theta),
+            // log q(a | b) = -|a - b - (eps/2) grad l(b)|^2 / (2 eps)
+            bmf_status e1, e2, e3, e4;
+            const double back = sqdiff(c, X, pX, qX, 0.5 * eps, n, ld, e1) +
+                                sqdiff(c, W, pW, qW, 0.5 * eps, d, ld, e2);
+            const double fwd = sqdiff(c, pX, X, gX, 0.5 * eps, n, ld, e3) +
+                               sqdiff(c, pW, W, gW, 0.5 * eps, d, ld, e4);
+            if (e1 || e2 || e3 || e4) return BMF_E_CUDA;
+            const double logA = prop.value - cur.value - back / (2 * eps) + fwd / (2 * eps);
+            take = std::log(uniforms[it]) < logA;
+        }
+        if (take) {
+            CUDA_TRY(c, cudaMemcpyAsync(X, pX, sx * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+            CUDA_TRY(c, cudaMemcpyAsync(W, pW, sw * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+            CUDA_TRY(c, cudaMemcpyAsync(gX, qX, sx * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+            CUDA_TRY(c, cudaMemcpyAsync(gW, qW, sw * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+            cur = prop;
+            ++acc;
+        }
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    if (c->prof) collect_profile(c);
+    if (accepted) *accepted = acc;
+    if (value) *value = cur.value;
+    return BMF_OK;
+}
+
 void bmf_destroy(bmf_ctx *c)
 {
     if (!c) return;
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->draws_d) cudaFree(c->draws_d);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (void *p : {(void *)c->adj_part, (void *)c->adj_sums, (void *)c->fval[0], (void *)c->fval[1],
+                    (void *)c->lg_buf})
+        if (p) cudaFree(p);
     delete c;
 }
 

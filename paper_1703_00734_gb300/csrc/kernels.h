@@ -179,6 +179,39 @@ void launch_aggregate(const AggParams &a, cudaStream_t st);
 void launch_predict(int K, int64_t n, const int32_t *row, const int32_t *col, const double *Xm,
                     const double *Wm, double offset, double *yhat, cudaStream_t st);
 
+// Adjoint of the masked log-joint (adjoint.cu).
+int adjoint_kt(int K);          // template width (K rounded up to 4, 8, 12, 16, 32 or 64)
+int adjoint_ld(int K);          // floats per item partial
+int adjoint_row_blocks(int64_t n_rows);
+struct AdjointParams {
+    int K, kt, ldp;
+    // pass 1: items items[0 .. n_items) (absolute index item_base + i)
+    const GramItem *items;
+    int64_t n_items, item_base;
+    const int32_t *idx;         // partner arena rows
+    const float *val;
+    const float *self, *other;  // caller factors [rows x ld] FP32, 16-byte aligned, ld % 4 == 0
+    int64_t ld;
+    int64_t self0, other0;      // arena rows of local row 0
+    float *part;                // [n_items x ldp]
+    // pass 2
+    int64_t n_rows;
+    const int64_t *item_ptr;
+    const int32_t *row_hslot;
+    const double *hyper, *prior_L, *prior_b;
+    int64_t R;
+    float *grad;                // [n_rows x ld]
+    double alpha;
+    int count_r2;
+    double *block_sums;         // [row blocks x 2]: sum r^2, sum prior quadratic
+};
+void launch_adjoint(const AdjointParams &a, int grid, cudaStream_t st);
+void launch_langevin(float *theta, const float *grad, const float *xi, int64_t n_rows, int K,
+                     int ld, float eps, cudaStream_t st);
+void launch_to_float(const double *in, float *out, int64_t n, cudaStream_t st);
+void launch_sqdiff(const float *a, const float *b, const float *g, double coef, int64_t n_rows,
+                   int K, int64_t ld, double *block_sums, int blocks, cudaStream_t st);
+
 // Device helpers
 void launch_fill_gather(int K, int prec, int64_t R, const double *X, void *Xg, int ldg,
                         cudaStream_t st);

@@ -159,22 +159,50 @@ __global__ void __launch_bounds__(256) hyper_kernel(HyperParams a)
     extern __shared__ double s[];
     double *M = s, *C = M + KK, *L = C + KK, *B = L + KK;
     double *s1 = B + KK, *xbar = s1 + K, *mus = xbar + K, *v = mus + K, *mu = v + K;
+    double *red = mu + K;  // [T] stripe partial sums
     __shared__ int flag;
     if (t == 0) flag = 0;
-    // 1. sum the chunk statistics in chunk order
-    for (int e = t; e < NS; e += T) {
-        double acc = 0.0;
-        for (int c = jb.chunk0; c < jb.chunk1; ++c) acc += a.stats[(int64_t)c * NS + e];
-        if (e < K) {
-            s1[e] = acc;
-        } else {
+    // 1. sum the chunk statistics: each entry is split over `ns` stripes of chunks, each
+    //    stripe summed with eight independent accumulators, then the stripes in order (a fixed
+    //    order for a given block size, so the result is deterministic)
+    const int ns = NS < T ? T / NS : 1;
+    for (int q = t; q < ns * NS; q += T) {
+        const int e = q % NS, sidx = q / NS;
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        int c = jb.chunk0 + sidx;
+        for (; c + 7 * ns < jb.chunk1; c += 8 * ns) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] += a.stats[(int64_t)(c + u * ns) * NS + e];
+        }
+        for (; c < jb.chunk1; c += ns) acc[0] += a.stats[(int64_t)c * NS + e];
+        const double part = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+        if (ns > 1)
+            red[q] = part;
+        else if (e < K)
+            s1[e] = part;
+        else {
             int i, j;
             decode_tri(e - K, i, j);
-            M[i * K + j] = acc;
-            M[j * K + i] = acc;
+            M[i * K + j] = part;
+            M[j * K + i] = part;
         }
     }
     __syncthreads();
+    if (ns > 1) {
+        for (int e = t; e < NS; e += T) {
+            double acc = 0.0;
+            for (int sidx = 0; sidx < ns; ++sidx) acc += red[sidx * NS + e];
+            if (e < K) {
+                s1[e] = acc;
+            } else {
+                int i, j;
+                decode_tri(e - K, i, j);
+                M[i * K + j] = acc;
+                M[j * K + i] = acc;
+            }
+        }
+        __syncthreads();
+    }
     const double N = (double)jb.n;
     const double bstar = a.beta0 + N;
     for (int e = t; e < K; e += T) {
@@ -267,7 +295,7 @@ fail:
 void launch_hyper(const HyperParams &a, cudaStream_t st)
 {
     if (a.n_jobs <= 0) return;
-    const size_t smem = (size_t)(4 * a.K * a.K + 5 * a.K) * sizeof(double);
+    const size_t smem = (size_t)(4 * a.K * a.K + 5 * a.K + 256) * sizeof(double);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(hyper_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     hyper_kernel<<<a.n_jobs, 256, smem, st>>>(a);
