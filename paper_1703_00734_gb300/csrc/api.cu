@@ -147,7 +147,8 @@ struct bmf_ctx {
 namespace {
 
 constexpr int kHyperJobsMax = 1 << 16;
-constexpr int kSweepMaxK = 16;
+constexpr int kSweepMaxK = 64;
+constexpr int kNarrowMaxK = 16;   // thread-per-row kernels up to here, warp-per-row beyond
 
 enum { K_STATS = 0, K_HYPER, K_GRAM_X, K_COND_X, K_GRAM_W, K_COND_W, K_RMSE, K_ADJ, K_NCLASS };
 const char *kClassName[K_NCLASS] = {"stats", "hyper", "gram_x", "cond_x", "gram_w", "cond_w", "rmse", "adjoint"};
@@ -255,6 +256,12 @@ bool host_inverse(int K, const std::vector<double> &A, std::vector<double> &Ainv
 
 const SubsetGeom &geom_of_slot(const bmf_ctx *c, int sl) { return c->P.subs[c->P.slot_sid[sl]]; }
 
+// Gram partial layout: entries per item and the offset of the right-hand side.
+int part_nv(int K) { return K > kNarrowMaxK ? ntri(K) + K : gram_nv(padded_k(K)); }
+int part_rhs_of(int K) { return K > kNarrowMaxK ? ntri(K) : ntri(padded_k(K)); }
+int part_ld_of(int K, int prec) { return K > kNarrowMaxK ? wide_part_ld(K) : gram_part_ld(K, prec); }
+int part_parts(int K, int prec) { return K > kNarrowMaxK ? 1 : gram_parts(K, prec); }
+
 // Slot range [sl0, sl1) of a stage (slots are sorted by stage).
 bool stage_slots(const bmf_ctx *c, int stage, int &sl0, int &sl1)
 {
@@ -359,10 +366,10 @@ bmf_status setup_side(bmf_ctx *c, Side &s, int64_t R, const std::vector<int64_t>
             midx[r] = (int32_t)s.h_multi.size();
             s.h_multi.push_back((int32_t)r);
         }
-    const size_t nctr = s.h_multi.size() * (size_t)gram_parts(c->K, c->prec);
+    const size_t nctr = s.h_multi.size() * (size_t)part_parts(c->K, c->prec);
     s.counters = c->mem.alloc<int>(nctr);
     s.multi_idx = c->mem.alloc<int32_t>(R);
-    s.rowsum = c->mem.alloc<double>(s.h_multi.size() * (size_t)gram_nv(padded_k(c->K)));
+    s.rowsum = c->mem.alloc<double>(s.h_multi.size() * (size_t)part_nv(c->K));
     if (!c->mem.ok) return fail(c, BMF_E_OOM, "device allocation failed (row sums)");
     CUDA_TRY(c, cudaMemset(s.counters, 0, std::max<size_t>(nctr, 1) * sizeof(int)));
     CUDA_TRY(c, cudaMemcpy(s.multi_idx, midx.data(), R * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -555,6 +562,7 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
             const int64_t r0 = f == 0 ? rx0 : rw0, r1 = f == 0 ? rx1 : rw1;
             const int64_t i0 = me.h_item_ptr[r0], i1 = me.h_item_ptr[r1];
             GramParams gp;
+            gp.K = K;
             gp.tasks = me.tasks + me.slot_task[sl0];
             gp.n_tasks = me.slot_task[sl1] - me.slot_task[sl0];
             gp.items = me.items + i0;
@@ -569,13 +577,18 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
             gp.item_ptr = me.item_ptr;
             gp.item0 = i0;
             gp.counters = me.counters;
-            gp.nparts = gram_parts(K, c->prec);
+            gp.nparts = part_parts(K, c->prec);
             gp.rowsum = me.rowsum;
-            gp.ld_sum = gram_nv(padded_k(K));
-            gp.nv = gram_nv(padded_k(K));
-            if (gp.n_tasks > 0)
+            gp.ld_sum = part_nv(K);
+            gp.nv = part_nv(K);
+            if (K > kNarrowMaxK) {
+                if (gp.n_items > 0)
+                    traced(c, c->st, f == 0 ? K_GRAM_X : K_GRAM_W, 1,
+                           [&] { launch_gram_wide(K, c->prec, gp, c->sms * 4, c->st); });
+            } else if (gp.n_tasks > 0) {
                 traced(c, c->st, f == 0 ? K_GRAM_X : K_GRAM_W, 1,
                        [&] { launch_gram(K, c->prec, gp, c->sms * 4, c->st); });
+            }
             if (hyp[f]) CUDA_TRY(c, cudaStreamWaitEvent(c->st, c->ev_hyp[f], 0));
             CondParams cp;
             cp.K = K;
@@ -588,10 +601,10 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
             cp.item0 = i0;
             cp.part = c->part;
             cp.ld = c->ld_part;
-            cp.part_rhs = ntri(padded_k(K));
+            cp.part_rhs = part_rhs_of(K);
             cp.multi_idx = me.multi_idx;
             cp.rowsum = me.rowsum;
-            cp.ld_sum = gram_nv(padded_k(K));
+            cp.ld_sum = part_nv(K);
             cp.tau = c->tau;
             cp.row_hslot = me.hslot;
             cp.hyper = c->hyper;
@@ -609,8 +622,12 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
             cp.stats = c->stats;
             cp.err = c->err_d;
             if (b1 > b0)
-                traced(c, c->st, f == 0 ? K_COND_X : K_COND_W, 1,
-                       [&] { launch_cond(c->prec, cp, (int)(b1 - b0), c->st); });
+                traced(c, c->st, f == 0 ? K_COND_X : K_COND_W, 1, [&] {
+                    if (K > kNarrowMaxK)
+                        launch_cond_wide(c->prec, cp, (int)(b1 - b0), c->st);
+                    else
+                        launch_cond(c->prec, cp, (int)(b1 - b0), c->st);
+                });
             if (hyp[f] && it + 1 < n_sweeps) {
                 CUDA_TRY(c, cudaEventRecord(c->ev_fac[f], c->st));
                 CUDA_TRY(c, cudaStreamWaitEvent(c->st2, c->ev_fac[f], 0));
@@ -665,6 +682,8 @@ bmf_status finalize_stage(bmf_ctx *c, int stage)
                                             " has no retained samples (burn-in not passed)");
         if (!c->full_moments)
             return fail(c, BMF_E_STATE, "moment matching needs second moments (moments mode)");
+        if (c->K > kNarrowMaxK)
+            return fail(c, BMF_E_ARG, "moment matching supports K <= 16 in this build");
         for (int f = 0; f < 2; ++f) {
             Side &sd = f == 0 ? c->X : c->W;
             MMParams mp{c->K, f == 0 ? g.xoff : g.woff,
@@ -912,7 +931,7 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
     }
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
     c->ldg = gather_ld(K, c->prec);
-    c->ld_part = gram_part_ld(K, c->prec);
+    c->ld_part = part_ld_of(K, c->prec);
     bmf_status s = setup_side(c, c->X, c->P.RX, c->P.rptr, c->P.ridx, c->P.rval);
     if (!s) s = setup_side(c, c->W, c->P.RW, c->P.cptr, c->P.cidx, c->P.cval);
     if (s) return bail(s, "");
@@ -925,7 +944,7 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
     std::vector<double>().swap(c->P.cval);
     const int S = I * J;
     const size_t pbytes = c->prec == BMF_FP64 ? 8 : 4;
-    c->part = c->mem.alloc<char>(K <= kSweepMaxK ? std::max<int64_t>(c->part_cap, 1) * c->ld_part * pbytes : 1);
+    c->part = c->mem.alloc<char>(std::max<int64_t>(c->part_cap, 1) * c->ld_part * pbytes);
     c->hyper = c->mem.alloc<double>((size_t)2 * S * hyper_slot_len(K));
     // block tables (subset-aligned) and the statistics slots they fill
     for (int f = 0; f < 2; ++f) {
@@ -1205,6 +1224,8 @@ bmf_status bmf_get_posterior(bmf_ctx *c, int32_t subset, int32_t factor, double 
         if (su.kept < 1) return fail(c, BMF_E_STATE, "no retained samples");
         if (!c->full_moments)
             return fail(c, BMF_E_STATE, "moment matching needs second moments (moments mode)");
+        if (c->K > kNarrowMaxK)
+            return fail(c, BMF_E_ARG, "moment matching supports K <= 16 in this build");
         for (int f = 0; f < 2; ++f) {
             Side &sd = f == 0 ? c->X : c->W;
             MMParams mp{c->K, f == 0 ? g.xoff : g.woff, f == 0 ? g.xoff + g.n() : g.woff + g.d(),

@@ -23,6 +23,7 @@ int padded_k(int K) { return K <= 1 ? 2 : (K + 1) / 2 * 2; }
 // Gathered rows start on 16-byte boundaries (128-bit loads).
 int gather_ld(int K, int prec)
 {
+    if (K > 16) return wide_kt(K);   // rows of 32, 48 or 64 elements (16-byte multiples)
     const int KT = padded_k(K);
     const int per16 = prec == BMF_FP64 ? 2 : (prec == BMF_BF16 ? 8 : 4);
     return (KT + per16 - 1) / per16 * per16;

@@ -20,6 +20,7 @@ int gram_part_ld(int K, int prec);
 int gram_group(int64_t count);
 
 struct GramParams {
+    int K;                     // latent dimension (used by the K > 16 kernels)
     const GramTask *tasks;
     int64_t n_tasks;
     const GramItem *items;     // items of the launch: absolute item i at items[i - item0]
@@ -178,6 +179,13 @@ void launch_aggregate(const AggParams &a, cudaStream_t st);
 // y_hat = offset + xm[row]^T wm[col] for host-given entries (original order means).
 void launch_predict(int K, int64_t n, const int32_t *row, const int32_t *col, const double *Xm,
                     const double *Wm, double offset, double *yhat, cudaStream_t st);
+
+// K > 16 (wide.cu): Gram on the tensor cores (BF16, split TF32) or FP64 lanes over entries;
+// conditional draw with one warp per row.  Partials: packed lower of the exact K, then K rhs.
+int wide_kt(int K);
+int wide_part_ld(int K);
+void launch_gram_wide(int K, int prec, const GramParams &a, int grid, cudaStream_t st);
+void launch_cond_wide(int prec, const CondParams &a, int n_blocks, cudaStream_t st);
 
 // Adjoint of the masked log-joint (adjoint.cu).
 int adjoint_kt(int K);          // template width (K rounded up to 4, 8, 12, 16, 32 or 64)

@@ -1,0 +1,582 @@
+// wide.cu -- the Gram-gather pass and the conditional draw for K > 16 (same mathematics as
+// gram.cu and cond.cu; Eqs. 2-4 and the cost terms of Section 4.3).
+//
+// Gram: one warp per work item; 32 gathered partner rows are staged in shared memory per step
+// and contracted on the tensor cores:
+//   * BF16 gathers: mma.sync m16n8k16 (BF16 x BF16 -> FP32), fragments by ldmatrix.trans from
+//     row-major staged rows; the right-hand side sum y p rides along as two extra columns holding
+//     y split into BF16 high and low parts (so y keeps about 16 bits);
+//   * FP32 gathers: split TF32 (p = hi + lo, three m16n8k8 products hi.hi + hi.lo + lo.hi),
+//     which keeps close to FP32 accuracy;
+//   * FP64 gathers: lanes over the Gram entries with FP64 FMAs (the FP64 pipe is the bound).
+// Only the lower-triangular 16 x 8 tiles are computed.  Partials use the packed-lower layout of
+// the exact K followed by the K right-hand-side entries; rows split over several items are
+// finished by the warp that completes the last item (fence + counter, no waiting).
+//
+// Conditional: one warp per row, the packed matrix in shared memory; right-looking FP64
+// Cholesky with the trailing update spread over the lanes element by element; column-oriented
+// forward and back solves.  Per-block statistics of the new state for the next hyperparameter
+// draw, as in cond.cu.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace bmf {
+
+constexpr int kWideObs = 32;     // staged observations per step
+constexpr int kWideWarps = 4;    // warps per block (conditional kernel)
+
+// ------------------------------------------------------------------------------------------
+// tensor-core helpers
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2,
+                                          uint32_t &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2_t(uint32_t addr, uint32_t &r0, uint32_t &r1)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];"
+                 : "=r"(r0), "=r"(r1)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, "
+                 "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, "
+                 "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ uint32_t tf32_of(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// Lower-triangular tile list of an M x N grid of 16 x 8 tiles plus one right-hand-side tile
+// per 16-row block: tile t of block row mi covers rows 16 mi.., columns 8 nj.. (nj <= 2 mi + 1),
+// and the extra tile nj = KT / 8 holds the right-hand side.
+template <int KT>
+struct WideTiles {
+    static constexpr int M = KT / 16;
+    static constexpr int NT = M * (M + 1) + M;  // sum_{mi} (2 mi + 2) lower tiles + M rhs tiles
+};
+
+__device__ __forceinline__ int tile_mi(int t, int &nj, int M)
+{
+    // tiles of block row mi: 2 mi + 2 lower tiles, then one rhs tile
+    int mi = 0, base = 0;
+    while (t >= base + 2 * mi + 3) {
+        base += 2 * mi + 3;
+        ++mi;
+    }
+    const int off = t - base;
+    nj = off < 2 * mi + 2 ? off : -1;   // -1: the rhs tile
+    return mi;
+}
+
+// Write one item's accumulators to its partial (packed lower entries, then the rhs).
+template <int KT>
+__device__ __forceinline__ void store_tiles(float *dst, const float (&acc)[WideTiles<KT>::NT][4],
+                                            int lane, int K)
+{
+    constexpr int M = WideTiles<KT>::M;
+    const int g = lane >> 2, tig = lane & 3;
+    const int NTK = ntri(K);
+#pragma unroll
+    for (int t = 0; t < WideTiles<KT>::NT; ++t) {
+        int nj;
+        const int mi = tile_mi(t, nj, M);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int i = 16 * mi + g + (h >= 2 ? 8 : 0);
+            const int cc = 2 * tig + (h & 1);
+            if (i >= K) continue;
+            if (nj >= 0) {
+                const int j = 8 * nj + cc;
+                if (j <= i && j < K) dst[tri(i, j)] = acc[t][h];
+            } else if (cc == 0) {
+                // rhs: column 0 = y high part, column 1 = y low part -> combine
+                dst[NTK + i] = acc[t][h] + acc[t][h + 1];
+            }
+        }
+    }
+}
+
+// Rows split over several items: the warp completing the last item sums the partials (FP64).
+__device__ __forceinline__ void finish_row(const GramParams &a, const GramItem &m, float *part,
+                                           int lane)
+{
+    const int mi = a.multi_idx[m.row];
+    if (mi < 0) return;
+    __threadfence();
+    int last = 0;
+    const int64_t r0 = a.item_ptr[m.row], r1 = a.item_ptr[m.row + 1];
+    if (lane == 0) last = atomicAdd(a.counters + mi, 1) == (int)(r1 - r0) - 1;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence();
+    for (int q = lane; q < a.nv; q += 32) {
+        double s = 0.0;
+        for (int64_t it = r0; it < r1; ++it) s += (double)__ldcg(part + (it - a.item0) * (int64_t)a.ld + q);
+        a.rowsum[(int64_t)mi * a.ld_sum + q] = s;
+    }
+    if (lane == 0) a.counters[mi] = 0;
+}
+
+// ------------------------------------------------------------------------------------------
+// BF16 Gram: rows [obs][KT + 8] in shared memory (columns KT, KT+1: y high/low, then zeros)
+// ------------------------------------------------------------------------------------------
+template <int KT>
+__global__ void __launch_bounds__(128) gram_wide_bf16(GramParams a)
+{
+    constexpr int LDS = KT + 8;           // bf16 per staged row (bank-conflict free for ldmatrix)
+    constexpr int M = WideTiles<KT>::M, NTL = WideTiles<KT>::NT;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    __nv_bfloat16 *S = reinterpret_cast<__nv_bfloat16 *>(smraw) + wib * kWideObs * LDS;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(S);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const __nv_bfloat16 *P = static_cast<const __nv_bfloat16 *>(a.P);
+    const float *val = static_cast<const float *>(a.val);
+    float *part = static_cast<float *>(a.part);
+    const int K = a.K;
+    for (int64_t it = warp; it < a.n_items; it += nwarps) {
+        const GramItem m = a.items[it];
+        float acc[NTL][4];
+#pragma unroll
+        for (int t = 0; t < NTL; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
+        for (int o0 = 0; o0 < m.count; o0 += kWideObs) {
+            // stage: lane o gathers observation o0 + o (zero row past the end)
+            const int o = lane;
+            __nv_bfloat16 *row = S + o * LDS;
+            if (o0 + o < m.count) {
+                const int64_t q = m.begin + o0 + o;
+                const int c = __ldg(a.idx + q);
+                const float y = __ldg(val + q);
+                const uint4 *src = reinterpret_cast<const uint4 *>(P + (int64_t)c * a.ldP);
+#pragma unroll
+                for (int v = 0; v < KT / 8; ++v) reinterpret_cast<uint4 *>(row)[v] = __ldg(src + v);
+                const __nv_bfloat16 hi = __float2bfloat16_rn(y);
+                const __nv_bfloat16 lo = __float2bfloat16_rn(y - __bfloat162float(hi));
+                uint4 tail = make_uint4(0u, 0u, 0u, 0u);
+                tail.x = (uint32_t)__bfloat16_as_ushort(hi) | ((uint32_t)__bfloat16_as_ushort(lo) << 16);
+                reinterpret_cast<uint4 *>(row)[KT / 8] = tail;
+            } else {
+#pragma unroll
+                for (int v = 0; v <= KT / 8; ++v) reinterpret_cast<uint4 *>(row)[v] = make_uint4(0u, 0u, 0u, 0u);
+            }
+            __syncwarp();
+            // two k-steps of 16 observations
+#pragma unroll
+            for (int ks = 0; ks < kWideObs / 16; ++ks) {
+                const int kb = ks * 16;
+                // ldmatrix row addresses: lanes 0-7 / 8-15 / 16-23 / 24-31 give the 8 rows of
+                // sub-matrices (k 0-7, cols c..c+7), (k 0-7, c+8..), (k 8-15, c..), (k 8-15, c+8..)
+                const int r8 = lane & 7, sub = lane >> 3;
+                uint32_t afr[M][4];
+#pragma unroll
+                for (int mi = 0; mi < M; ++mi) {
+                    const int krow = kb + r8 + ((sub & 2) ? 8 : 0);
+                    const int col = 16 * mi + ((sub & 1) ? 8 : 0);
+                    ldsm_x4_t(sbase + (uint32_t)((krow * LDS + col) * 2), afr[mi][0], afr[mi][1],
+                              afr[mi][2], afr[mi][3]);
+                }
+#pragma unroll
+                for (int t = 0; t < NTL; ++t) {
+                    int nj;
+                    const int mi = tile_mi(t, nj, M);
+                    const int col = nj >= 0 ? 8 * nj : KT;
+                    uint32_t b0, b1;
+                    // x2: lanes 0-7 rows k 0-7, lanes 8-15 rows k 8-15 of columns col..col+7
+                    const int krow = kb + r8 + ((sub & 1) ? 8 : 0);
+                    ldsm_x2_t(sbase + (uint32_t)((krow * LDS + col) * 2), b0, b1);
+                    mma_bf16(acc[t], afr[mi], b0, b1);
+                }
+            }
+            __syncwarp();
+        }
+        store_tiles<KT>(part + it * (int64_t)a.ld, acc, lane, K);
+        finish_row(a, m, part, lane);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// FP32 Gram by split TF32: rows [obs][KT + 4] floats in shared memory (column KT holds y)
+// ------------------------------------------------------------------------------------------
+template <int KT>
+__global__ void __launch_bounds__(128) gram_wide_tf32(GramParams a)
+{
+    constexpr int LDS = KT + 8;           // conflict-free fragment loads; column KT holds y
+    constexpr int M = WideTiles<KT>::M, NTL = WideTiles<KT>::NT;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float *S = reinterpret_cast<float *>(smraw) + wib * kWideObs * LDS;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const float *P = static_cast<const float *>(a.P);
+    const float *val = static_cast<const float *>(a.val);
+    float *part = static_cast<float *>(a.part);
+    const int K = a.K;
+    const int g = lane >> 2, tig = lane & 3;
+    for (int64_t it = warp; it < a.n_items; it += nwarps) {
+        const GramItem m = a.items[it];
+        float acc[NTL][4];
+#pragma unroll
+        for (int t = 0; t < NTL; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
+        for (int o0 = 0; o0 < m.count; o0 += kWideObs) {
+            const int o = lane;
+            float *row = S + o * LDS;
+            if (o0 + o < m.count) {
+                const int64_t q = m.begin + o0 + o;
+                const int c = __ldg(a.idx + q);
+                const float4 *src = reinterpret_cast<const float4 *>(P + (int64_t)c * a.ldP);
+#pragma unroll
+                for (int v = 0; v < KT / 4; ++v) reinterpret_cast<float4 *>(row)[v] = __ldg(src + v);
+                reinterpret_cast<float4 *>(row)[KT / 4] = make_float4(__ldg(val + q), 0.f, 0.f, 0.f);
+                reinterpret_cast<float4 *>(row)[KT / 4 + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+#pragma unroll
+                for (int v = 0; v < LDS / 4; ++v) reinterpret_cast<float4 *>(row)[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int ks = 0; ks < kWideObs / 8; ++ks) {
+                const int kb = ks * 8;
+                // A = P^T (latent x obs): a0 (g, tig), a1 (g+8, tig), a2 (g, tig+4), a3 (g+8, tig+4)
+                uint32_t ah[M][4], al[M][4];
+#pragma unroll
+                for (int mi = 0; mi < M; ++mi) {
+                    const float v[4] = {S[(kb + tig) * LDS + 16 * mi + g], S[(kb + tig) * LDS + 16 * mi + g + 8],
+                                        S[(kb + tig + 4) * LDS + 16 * mi + g], S[(kb + tig + 4) * LDS + 16 * mi + g + 8]};
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        ah[mi][h] = tf32_of(v[h]);
+                        al[mi][h] = tf32_of(v[h] - __uint_as_float(ah[mi][h]));
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < NTL; ++t) {
+                    int nj;
+                    const int mi = tile_mi(t, nj, M);
+                    const int col = nj >= 0 ? 8 * nj : KT;
+                    const float bv0 = S[(kb + tig) * LDS + col + g], bv1 = S[(kb + tig + 4) * LDS + col + g];
+                    const uint32_t bh0 = tf32_of(bv0), bh1 = tf32_of(bv1);
+                    const uint32_t bl0 = tf32_of(bv0 - __uint_as_float(bh0));
+                    const uint32_t bl1 = tf32_of(bv1 - __uint_as_float(bh1));
+                    mma_tf32(acc[t], al[mi], bh0, bh1);
+                    mma_tf32(acc[t], ah[mi], bl0, bl1);
+                    mma_tf32(acc[t], ah[mi], bh0, bh1);
+                }
+            }
+            __syncwarp();
+        }
+        store_tiles<KT>(part + it * (int64_t)a.ld, acc, lane, K);
+        finish_row(a, m, part, lane);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// FP64 Gram: lanes over entries (packed lower, then rhs) of 32 staged rows [obs][K + 1]
+// ------------------------------------------------------------------------------------------
+template <int MAXP>
+__global__ void __launch_bounds__(128) gram_wide_fp64(GramParams a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int K = a.K, LDS = K + 1;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    double *S = reinterpret_cast<double *>(smraw) + wib * kWideObs * LDS;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const double *P = static_cast<const double *>(a.P);
+    const double *val = static_cast<const double *>(a.val);
+    double *part = static_cast<double *>(a.part);
+    const int NTK = ntri(K), NV = NTK + K;
+    for (int64_t it = warp; it < a.n_items; it += nwarps) {
+        const GramItem m = a.items[it];
+        double acc[MAXP];
+#pragma unroll
+        for (int u = 0; u < MAXP; ++u) acc[u] = 0.0;
+        for (int o0 = 0; o0 < m.count; o0 += kWideObs) {
+            const int nobs = min(kWideObs, m.count - o0);
+            for (int q = lane; q < nobs * LDS; q += 32) {
+                const int o = q / LDS, k = q % LDS;
+                const int64_t oq = m.begin + o0 + o;
+                S[q] = k < K ? P[(int64_t)__ldg(a.idx + oq) * a.ldP + k] : __ldg(val + oq);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < MAXP; ++u) {
+                const int e = lane + 32 * u;
+                if (e >= NV) continue;
+                int i, j;
+                if (e < NTK) {
+                    i = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+                    while (i * (i + 1) / 2 > e) --i;
+                    while ((i + 1) * (i + 2) / 2 <= e) ++i;
+                    j = e - i * (i + 1) / 2;
+                } else {
+                    i = e - NTK;
+                    j = K;   // the value column
+                }
+                double s = acc[u];
+                for (int o = 0; o < nobs; ++o) s = fma(S[o * LDS + i], S[o * LDS + j], s);
+                acc[u] = s;
+            }
+            __syncwarp();
+        }
+        double *dst = part + it * (int64_t)a.ld;
+#pragma unroll
+        for (int u = 0; u < MAXP; ++u)
+            if (lane + 32 * u < NV) dst[lane + 32 * u] = acc[u];
+        // split rows
+        const int mi = a.multi_idx[m.row];
+        if (mi >= 0) {
+            __threadfence();
+            int last = 0;
+            const int64_t r0 = a.item_ptr[m.row], r1 = a.item_ptr[m.row + 1];
+            if (lane == 0) last = atomicAdd(a.counters + mi, 1) == (int)(r1 - r0) - 1;
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __threadfence();
+                for (int q = lane; q < NV; q += 32) {
+                    double sum = 0.0;
+                    for (int64_t j = r0; j < r1; ++j) sum += __ldcg(part + (j - a.item0) * (int64_t)a.ld + q);
+                    a.rowsum[(int64_t)mi * a.ld_sum + q] = sum;
+                }
+                if (lane == 0) a.counters[mi] = 0;
+            }
+        }
+    }
+}
+
+int wide_kt(int K) { return K <= 32 ? 32 : (K <= 48 ? 48 : 64); }
+
+// Partial entries per item for K > 16 (exact K layout, padded to a multiple of 4).
+int wide_part_ld(int K) { return (ntri(K) + K + 3) / 4 * 4; }
+
+template <int KT>
+static void launch_wide_t(int prec, const GramParams &a, int grid, cudaStream_t st)
+{
+    if (prec == BMF_BF16) {
+        const size_t smem = (size_t)4 * kWideObs * (KT + 8) * 2;
+        gram_wide_bf16<KT><<<grid, 128, smem, st>>>(a);
+    } else {
+        const size_t smem = (size_t)4 * kWideObs * (KT + 8) * 4;
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(gram_wide_tf32<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        gram_wide_tf32<KT><<<grid, 128, smem, st>>>(a);
+    }
+}
+
+void launch_gram_wide(int K, int prec, const GramParams &a, int grid, cudaStream_t st)
+{
+    if (a.n_items == 0) return;
+    if (prec == BMF_FP64) {
+        const size_t smem = (size_t)4 * kWideObs * (K + 1) * 8;
+        const int nv = ntri(K) + K;
+        if (nv <= 18 * 32) {
+            if (smem > 48 * 1024)
+                cudaFuncSetAttribute(gram_wide_fp64<18>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            gram_wide_fp64<18><<<grid, 128, smem, st>>>(a);
+        } else if (nv <= 38 * 32) {
+            if (smem > 48 * 1024)
+                cudaFuncSetAttribute(gram_wide_fp64<38>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            gram_wide_fp64<38><<<grid, 128, smem, st>>>(a);
+        } else {
+            if (smem > 48 * 1024)
+                cudaFuncSetAttribute(gram_wide_fp64<67>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            gram_wide_fp64<67><<<grid, 128, smem, st>>>(a);
+        }
+        return;
+    }
+    switch (wide_kt(K)) {
+    case 32: launch_wide_t<32>(prec, a, grid, st); break;
+    case 48: launch_wide_t<48>(prec, a, grid, st); break;
+    default: launch_wide_t<64>(prec, a, grid, st); break;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Conditional draw for K > 16: one warp per row
+// ------------------------------------------------------------------------------------------
+template <typename GT>
+__device__ __forceinline__ GT to_gather_w(double x);
+template <>
+__device__ __forceinline__ double to_gather_w<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float to_gather_w<float>(double x) { return (float)x; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_gather_w<__nv_bfloat16>(double x) { return __double2bfloat16(x); }
+
+// (i, j) of position p of the packed-lower pairs with j > k enumerated by column from the last:
+// column c holds rows c..K-1; positions 0 .. (K-k-1)(K-k)/2 - 1 are exactly the columns > k.
+__device__ __forceinline__ void trailing_pair(int p, int K, int &i, int &j)
+{
+    int m = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)p)) * 0.5f);
+    while (m * (m - 1) / 2 > p) --m;
+    while (m * (m + 1) / 2 <= p) ++m;
+    j = K - m;
+    i = j + (p - m * (m - 1) / 2);
+}
+
+template <typename GT, typename AT>
+__global__ void __launch_bounds__(32 * kWideWarps) cond_wide_kernel(CondParams a)
+{
+    extern __shared__ double smw[];
+    const int K = a.K, NT = ntri(K);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int per_warp = NT + 2 * K;
+    double *M = smw + w * per_warp, *B = M + NT, *RI = B + K;
+    double *XS = smw + kWideWarps * per_warp;     // [kCondBlock][K]: x of the block's rows
+    const CondBlock blk = a.blocks[blockIdx.x];
+    const int64_t R = a.R;
+    const double tau = a.tau;
+    for (int q = w; q < blk.n; q += kWideWarps) {
+        const int64_t r = blk.row0 + q;
+        // 1-2. G, r and the prior
+        const int64_t i0 = a.item_ptr[r], i1 = a.item_ptr[r + 1];
+        const int mi = a.multi_idx[r];
+        const int h = a.row_hslot[r];
+        const double *hp = h >= 0 ? a.hyper + (int64_t)h * hyper_slot_len(K) : nullptr;
+        const AT *pp = static_cast<const AT *>(a.part) + (i0 - a.item0) * (int64_t)a.ld;
+        const double *ps = mi >= 0 ? a.rowsum + (int64_t)mi * a.ld_sum : nullptr;
+        for (int e = lane; e < NT + K; e += 32) {
+            const double gsum = ps ? ps[e] : (i1 > i0 ? (double)pp[e] : 0.0);
+            double prior;
+            if (e < NT)
+                prior = hp ? hp[K + e] : a.prior_L[(int64_t)e * R + r];
+            else
+                prior = hp ? hp[K + NT + (e - NT)] : a.prior_b[(int64_t)(e - NT) * R + r];
+            M[e] = fma(tau, gsum, prior);   // M[NT + i] is B[i]
+        }
+        __syncwarp();
+        // 3. right-looking Cholesky
+        bool ok = true;
+        for (int k = 0; k < K; ++k) {
+            const int kk = tri(k, k);
+            const double d = M[kk];
+            if (!(d > 0.0)) {
+                ok = false;
+                break;
+            }
+            const double rs = rsqrt(d);
+            __syncwarp();
+            for (int i = k + 1 + lane; i < K; i += 32) M[tri(i, k)] *= rs;
+            if (lane == 0) {
+                M[kk] = d * rs;
+                RI[k] = rs;
+            }
+            __syncwarp();
+            const int T = (K - k - 1) * (K - k) / 2;
+            for (int p = lane; p < T; p += 32) {
+                int i, j;
+                trailing_pair(p, K, i, j);
+                M[tri(i, j)] = fma(-M[tri(i, k)], M[tri(j, k)], M[tri(i, j)]);
+            }
+            __syncwarp();
+        }
+        if (!ok) {
+            if (lane == 0) {
+                atomicOr(&a.err->flags, ERR_NOT_PD);
+                atomicMin(&a.err->first_bad_row, (int)r);
+            }
+            for (int i = lane; i < K; i += 32) XS[q * K + i] = 0.0;
+            __syncwarp();
+            continue;
+        }
+        // 4. forward solve L y = b (column oriented)
+        for (int k = 0; k < K; ++k) {
+            const double yk = B[k] * RI[k];
+            __syncwarp();
+            for (int i = k + 1 + lane; i < K; i += 32) B[i] = fma(-M[tri(i, k)], yk, B[i]);
+            if (lane == 0) B[k] = yk;
+            __syncwarp();
+        }
+        // 5. back solve L^T x = y + z (column oriented)
+        const double *z = a.z + (r - a.row0) * K;
+        for (int i = lane; i < K; i += 32) B[i] += z[i];
+        __syncwarp();
+        for (int i = K - 1; i >= 0; --i) {
+            const double xi = B[i] * RI[i];
+            __syncwarp();
+            for (int k = lane; k < i; k += 32) B[k] = fma(-M[tri(i, k)], xi, B[k]);
+            if (lane == 0) B[i] = xi;
+            __syncwarp();
+        }
+        // 6. state, gathered copy, moments, block copy for the statistics
+        GT *g = static_cast<GT *>(a.Xg) + r * a.ldg;
+        for (int i = lane; i < a.ldg; i += 32) {
+            const double xi = i < K ? B[i] : 0.0;
+            g[i] = to_gather_w<GT>(xi);
+            if (i < K) {
+                a.X[r * K + i] = xi;
+                XS[q * K + i] = xi;
+                if (a.keep) a.S1[(int64_t)i * R + r] += xi;
+            }
+        }
+        if (a.keep && a.full)
+            for (int e = lane; e < NT; e += 32) {
+                int i = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+                while (i * (i + 1) / 2 > e) --i;
+                while ((i + 1) * (i + 2) / 2 <= e) ++i;
+                const int j = e - i * (i + 1) / 2;
+                a.S2[(int64_t)e * R + r] += B[i] * B[j];
+            }
+        __syncwarp();
+    }
+    __syncthreads();
+    // 7. per-block statistics of the new state
+    const int NS = K + NT;
+    double *out = a.stats + (a.blk0 + blockIdx.x) * (int64_t)NS;
+    for (int e = threadIdx.x; e < NS; e += blockDim.x) {
+        double s = 0.0;
+        if (e < K) {
+            for (int q = 0; q < blk.n; ++q) s += XS[q * K + e];
+        } else {
+            const int f = e - K;
+            int i = (int)((sqrtf(8.0f * f + 1.0f) - 1.0f) * 0.5f);
+            while (i * (i + 1) / 2 > f) --i;
+            while ((i + 1) * (i + 2) / 2 <= f) ++i;
+            const int j = f - i * (i + 1) / 2;
+            for (int q = 0; q < blk.n; ++q) s = fma(XS[q * K + i], XS[q * K + j], s);
+        }
+        out[e] = s;
+    }
+}
+
+template <typename GT, typename AT>
+static void launch_cond_wide_t(const CondParams &a, int n_blocks, cudaStream_t st)
+{
+    const size_t smem = ((size_t)kWideWarps * (ntri(a.K) + 2 * a.K) + (size_t)kCondBlock * a.K) * sizeof(double);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(cond_wide_kernel<GT, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cond_wide_kernel<GT, AT><<<n_blocks, 32 * kWideWarps, smem, st>>>(a);
+}
+
+void launch_cond_wide(int prec, const CondParams &a, int n_blocks, cudaStream_t st)
+{
+    if (n_blocks <= 0) return;
+    if (prec == BMF_FP64)
+        launch_cond_wide_t<double, double>(a, n_blocks, st);
+    else if (prec == BMF_FP32)
+        launch_cond_wide_t<float, float>(a, n_blocks, st);
+    else
+        launch_cond_wide_t<__nv_bfloat16, float>(a, n_blocks, st);
+}
+
+}  // namespace bmf

@@ -29,19 +29,30 @@ def lanes_for(count):
     return 8 if count <= 16 else (16 if count <= 48 else 32)
 
 
-def row_bounds(ptr, idx, val, P, dP, tau, mu_p, Lam_p, z, u_in, rows):
+def seq_len(n, K):
+    """Longest sequential FP32 sum behind one accumulated entry: lanes x iterations for the
+    CUDA-core kernels (K <= 16); tensor-core accumulation steps of 16 (or 8) observations plus
+    the products summed inside one instruction for K > 16."""
+    c = min(n, 1024)
+    if K > 16:
+        return math.ceil(c / 8) + 16 + 2
+    lanes = lanes_for(c)
+    return math.ceil(c / lanes) + math.log2(lanes) + 2
+
+
+def row_bounds(ptr, idx, val, P, dP, tau, mu_p, Lam_p, z, u_in, rows, u_y=U_ACC):
     out = np.zeros(len(rows))
     b_p = Lam_p @ mu_p
+    K = P.shape[1]
     for k, r in enumerate(rows):
         sl = slice(ptr[r], ptr[r + 1])
         Pr, yr, dPr = P[idx[sl]], val[sl], dP[idx[sl]]
         n = len(yr)
-        lanes = lanes_for(min(n, 1024))
-        m = math.ceil(min(n, 1024) / lanes) + math.log2(lanes) + 2 + max(0, math.ceil(n / 1024) - 1)
+        m = seq_len(n, K)
         aP, ay, adP = np.abs(Pr), np.abs(yr), np.abs(dPr)
         Lam = Lam_p + tau * Pr.T @ Pr
         E = tau * ((m * U_ACC + 2 * u_in) * aP.T @ aP + aP.T @ adP + adP.T @ aP)
-        eb = tau * ((m * U_ACC + u_in + U_ACC) * aP.T @ ay + adP.T @ ay)
+        eb = tau * ((m * U_ACC + u_in + u_y) * aP.T @ ay + adP.T @ ay)
         b = b_p + tau * Pr.T @ yr
         mu = np.linalg.solve(Lam, b)
         L = np.linalg.cholesky(Lam)
@@ -58,7 +69,7 @@ def check_half(gpu_rows, cpu_rows, bound, what, factor=2.0):
     return ratio.max()
 
 
-def run_reduced(d, K, precision, u_in, rows_x=None, rows_w=None):
+def run_reduced(d, K, precision, u_in, rows_x=None, rows_w=None, u_y=U_ACC):
     pr = Pair(d, K, precision=precision)
     s = pr.p.subsets[0]
     H = oracle.hyper_block_len(K)
@@ -76,10 +87,10 @@ def run_reduced(d, K, precision, u_in, rows_x=None, rows_w=None):
     rx = np.arange(s.n) if rows_x is None else rows_x
     rw = np.arange(s.d) if rows_w is None else rows_w
     bx = row_bounds(s.rptr, s.ridx, s.rval, W0, np.zeros_like(W0), d["tau"], st.muX, st.LamX, zx,
-                    u_in, rx)
+                    u_in, rx, u_y)
     qx = check_half(X[rx], st.X[rx], bx, f"{precision} X half")
     dX = np.abs(X - st.X)
-    bw = row_bounds(s.cptr, s.cidx, s.cval, st.X, dX, d["tau"], st.muW, st.LamW, zw, u_in, rw)
+    bw = row_bounds(s.cptr, s.cidx, s.cval, st.X, dX, d["tau"], st.muW, st.LamW, zw, u_in, rw, u_y)
     qw = check_half(W[rw], st.W[rw], bw, f"{precision} W half")
     return qx, qw
 
