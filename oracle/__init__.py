@@ -80,6 +80,9 @@ def lib():
         L.orc_logjoint_grad.argtypes = [i32, i64, i64, i64, P, P, P, P, P, f64, P, P, P, P,
                                         P, P, P, P]
         L.orc_logjoint_grad.restype = None
+        L.orc_philox4x64.argtypes = [P, P, P]
+        L.orc_philox4x64.restype = None
+        L.orc_gen_subset.argtypes = [ctypes.c_uint64, i64, i32, i32, f64, i64, i64, P, P, P, P]
         _lib = L
     return _lib
 
@@ -370,6 +373,37 @@ def stage_draw_layout(subsets, K):
         off += s.d * K
     lay["total"] = off
     return lay
+
+
+# ---------------------------------------------------------------------------------------
+# Counter-based draws (Philox4x64-10, Box-Muller, Marsaglia-Tsang; see bmf_oracle.c)
+# ---------------------------------------------------------------------------------------
+
+def philox4x64(ctr, key):
+    """The four 64-bit output words of Philox4x64-10 at counter ctr[4], key key[2]."""
+    c = np.asarray(ctr, np.uint64)
+    k = np.asarray(key, np.uint64)
+    out = np.zeros(4, np.uint64)
+    lib().orc_philox4x64(_p(c), _p(k), _p(out))
+    return out
+
+
+def gen_subset(seed, t, sid, K, nu0, n, d):
+    """Generated draws of sweep t (1-based) of subset sid with n rows, d columns:
+    (hyper block X, hyper block W, zX [n, K], zW [d, K])."""
+    H = hyper_block_len(K)
+    hx, hw = np.zeros(H), np.zeros(H)
+    zx, zw = np.zeros((n, K)), np.zeros((d, K))
+    _check(lib().orc_gen_subset(int(seed), int(t), int(sid), int(K), float(nu0), int(n), int(d),
+                                _p(hx), _p(hw), _p(zx), _p(zw)), "gen_subset")
+    return hx, hw, zx, zw
+
+
+def gen_batch_draws(subsets, K, nu0, seed, t):
+    """One sweep's generated draws for subsets processed together, in the shared layout."""
+    parts = [gen_subset(seed, t, s.sid, K, nu0, s.n, s.d) for s in subsets]
+    return np.concatenate([np.concatenate([p[0], p[1]]) for p in parts]
+                          + [p[2].ravel() for p in parts] + [p[3].ravel() for p in parts])
 
 
 # ---------------------------------------------------------------------------------------

@@ -524,3 +524,140 @@ void orc_logjoint_grad(int K, int64_t N, int64_t D, int64_t nnz, const int32_t *
     *g_log_a = 0.5 * (double)nnz - 0.5 * a * sse;
     *value = -0.5 * a * sse + 0.5 * (double)nnz * log_a - 0.5 * quad;
 }
+
+/* ------------------------------------------------------------------------------------- */
+/* Counter-based generator for the draws (the library's device generator draws the same    */
+/* numbers): Philox4x64-10 of Salmon, Moraes, Dror and Shaw, "Parallel random numbers: as  */
+/* easy as 1, 2, 3" (SC'11), and the transforms to normal and chi-square variates.         */
+/* ------------------------------------------------------------------------------------- */
+
+/* 64 x 64 -> 128-bit product (hi, lo) from 32-bit halves (schoolbook). */
+static void mulhilo64(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo)
+{
+    uint64_t a0 = a & 0xffffffffu, a1 = a >> 32, b0 = b & 0xffffffffu, b1 = b >> 32;
+    uint64_t p00 = a0 * b0, p01 = a0 * b1, p10 = a1 * b0, p11 = a1 * b1;
+    uint64_t mid = (p00 >> 32) + (p01 & 0xffffffffu) + (p10 & 0xffffffffu);
+    *lo = (mid << 32) | (p00 & 0xffffffffu);
+    *hi = p11 + (p01 >> 32) + (p10 >> 32) + (mid >> 32);
+}
+
+/* Philox4x64 with 10 rounds: each round multiplies words 0 and 2 by the two round
+ * multipliers, the new words are (hi(M1 x2) ^ x1 ^ k0, lo(M1 x2), hi(M0 x0) ^ x3 ^ k1,
+ * lo(M0 x0)), and the key is bumped by the two Weyl constants between rounds. */
+void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4])
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3], k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t hi0, lo0, hi1, lo1;
+        mulhilo64(M0, x0, &hi0, &lo0);
+        mulhilo64(M1, x2, &hi1, &lo1);
+        uint64_t n0 = hi1 ^ x1 ^ k0, n2 = hi0 ^ x3 ^ k1;
+        x0 = n0;
+        x1 = lo1;
+        x2 = n2;
+        x3 = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = x0;
+    out[1] = x1;
+    out[2] = x2;
+    out[3] = x3;
+}
+
+/* Uniforms from the top 53 bits of a word: [0, 1) and (0, 1]. */
+static double u01_closed0(uint64_t w) { return (double)(w >> 11) * 0x1.0p-53; }
+static double u01_open0(uint64_t w) { return (double)((w >> 11) + 1) * 0x1.0p-53; }
+
+/* Box-Muller (1958): two normals from the word pair (a, b). */
+static void box_muller(uint64_t a, uint64_t b, double *z0, double *z1)
+{
+    double r = sqrt(-2.0 * log(u01_open0(a)));
+    double th = 6.283185307179586 * u01_closed0(b);
+    *z0 = r * cos(th);
+    *z1 = r * sin(th);
+}
+
+/* Stream tags of the counter's third word. */
+#define ORC_KIND_CHI2 1
+#define ORC_KIND_NORMAL 2
+#define ORC_KIND_Z 3
+
+static uint64_t orc_tag(int32_t sid, int f, int kind)
+{
+    return ((uint64_t)(uint32_t)sid << 8) | ((uint64_t)f << 4) | (uint64_t)kind;
+}
+
+/* Element e of a normal stream: call e / 4 of counter (e / 4, t, tag, 0); the call's words
+ * (0, 1) give elements 0 and 1 (cosine, sine), words (2, 3) elements 2 and 3. */
+static double stream_normal(const uint64_t key[2], int64_t t, uint64_t tag, int64_t e)
+{
+    uint64_t ctr[4] = {(uint64_t)(e >> 2), (uint64_t)t, tag, 0}, w[4];
+    orc_philox4x64(ctr, key, w);
+    int p = (int)((e >> 1) & 1);
+    double z0, z1;
+    box_muller(w[2 * p], w[2 * p + 1], &z0, &z1);
+    return (e & 1) ? z1 : z0;
+}
+
+/* chi-square(dof) = 2 Gamma(dof / 2) by Marsaglia & Tsang, "A simple method for generating
+ * gamma variables" (ACM TOMS 2000): for shape a >= 1, d = a - 1/3, c = 1 / sqrt(9 d); a
+ * candidate x ~ N(0, 1) with v = (1 + c x)^3 > 0 is accepted when u < 1 - 0.0331 x^4 or
+ * log u < x^2 / 2 + d (1 - v + log v), giving d v.  For a < 1 the variate for a + 1 is
+ * multiplied by U^(1/a).  Attempt j of variate k uses counter (k, t, tag, j): x from words
+ * (0, 1) (cosine), u from word 2, U from word 3.  Returns ORC_ARG after 64 rejections. */
+static int stream_chi2(const uint64_t key[2], int64_t t, uint64_t tag, int k, double dof,
+                       double *out)
+{
+    if (!(dof > 0.0)) return ORC_ARG;
+    double a = 0.5 * dof;
+    int boost = a < 1.0;
+    double aa = boost ? a + 1.0 : a;
+    double d = aa - 1.0 / 3.0, c = 1.0 / sqrt(9.0 * d);
+    for (int j = 0; j < 64; ++j) {
+        uint64_t ctr[4] = {(uint64_t)k, (uint64_t)t, tag, (uint64_t)j}, w[4];
+        orc_philox4x64(ctr, key, w);
+        double x, unused;
+        box_muller(w[0], w[1], &x, &unused);
+        double v = 1.0 + c * x;
+        if (!(v > 0.0)) continue;
+        v = v * v * v;
+        double u = u01_open0(w[2]);
+        if (u < 1.0 - 0.0331 * (x * x) * (x * x) ||
+            log(u) < 0.5 * x * x + d * (1.0 - v + log(v))) {
+            double g = d * v;
+            if (boost) g *= pow(u01_open0(w[3]), 1.0 / a);
+            *out = 2.0 * g;
+            return ORC_OK;
+        }
+    }
+    return ORC_ARG;
+}
+
+/* The draws of sweep t (1-based) of subset `sid` with n rows and d columns: the X and W
+ * hyperparameter blocks (chi2[K] with dof nu0 + n - k resp. nu0 + d - k, K(K-1)/2 + K normals
+ * of the (sid, factor) normal stream) and z of its X rows and W columns (element r K + k of
+ * the (sid, factor) z stream).  Key (seed, 0). */
+int orc_gen_subset(uint64_t seed, int64_t t, int32_t sid, int K, double nu0, int64_t n,
+                   int64_t d, double *hx, double *hw, double *zx, double *zw)
+{
+    const uint64_t key[2] = {seed, 0};
+    const int nn = K * (K - 1) / 2 + K;
+    for (int f = 0; f < 2; ++f) {
+        double *h = f == 0 ? hx : hw;
+        const int64_t m = f == 0 ? n : d;
+        for (int k = 0; k < K; ++k) {
+            int st = stream_chi2(key, t, orc_tag(sid, f, ORC_KIND_CHI2), k, nu0 + (double)m - k,
+                                 &h[k]);
+            if (st) return st;
+        }
+        for (int e = 0; e < nn; ++e)
+            h[K + e] = stream_normal(key, t, orc_tag(sid, f, ORC_KIND_NORMAL), e);
+        double *z = f == 0 ? zx : zw;
+        for (int64_t e = 0; e < m * K; ++e)
+            z[e] = stream_normal(key, t, orc_tag(sid, f, ORC_KIND_Z), e);
+    }
+    return ORC_OK;
+}

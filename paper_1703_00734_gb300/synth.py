@@ -17,6 +17,8 @@ and statistics of the rating matrices the paper uses, Section 5.3):
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 
@@ -50,16 +52,38 @@ def _distinct_keys(draw, M, ncells):
     while need > 0:
         m = int(min(max(need / max(accept, 0.02) * 1.05 + 1024, 1024), 4 * M + 1024))
         cand = np.asarray(draw(m), np.int64)
-        word, bit = cand >> 6, (cand & 63).astype(np.uint64)
-        fresh = ((bits[word] >> bit) & np.uint64(1)) == 0
-        cand = cand[fresh]
-        _, first = np.unique(cand, return_index=True)
-        take = cand[np.sort(first)][:need]
+
+        def fresh(a, b):
+            c = cand[a:b]
+            word, bit = c >> 6, (c & 63).astype(np.uint64)
+            return c[((bits[word] >> bit) & np.uint64(1)) == 0]
+
+        cand = _parallel(fresh, m)
+        take = cand[_first_occurrences(cand, ncells)][:need]
         np.bitwise_or.at(bits, take >> 6, np.left_shift(np.uint64(1), (take & 63).astype(np.uint64)))
         accept = max(len(take) / m, 1e-3)
         parts.append(take)
         need -= len(take)
     return np.concatenate(parts) if parts else np.empty(0, np.int64)
+
+
+def _first_occurrences(keys, ncells, parts=16):
+    """Ascending positions of the first occurrence of each distinct key (key ranges are
+    deduplicated independently on a thread pool; same result as one np.unique)."""
+    if len(keys) <= 1 << 22:
+        _, first = np.unique(keys, return_index=True)
+        return np.sort(first)
+    bucket = keys // -(-ncells // parts)
+
+    def one(b):
+        sel = np.flatnonzero(bucket == b)
+        _, first = np.unique(keys[sel], return_index=True)
+        return sel[first]
+
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(min(parts, os.cpu_count() or 1)) as ex:
+        pos = np.concatenate(list(ex.map(one, range(parts))))
+    return np.sort(pos, kind="stable")
 
 
 def zipf_weights(n: int, s: float, rng) -> np.ndarray:
@@ -81,6 +105,17 @@ def _inverse_cdf(cdf, u, guide):
     return i
 
 
+def _parallel(fn, n, chunk=1 << 22):
+    """fn(a, b) over [0, n) in chunks on a thread pool, results concatenated in order (the
+    numpy kernels inside release the GIL; the result does not depend on the thread count)."""
+    starts = range(0, n, chunk)
+    if n <= chunk:
+        return fn(0, n)
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(min(16, os.cpu_count() or 1)) as ex:
+        return np.concatenate(list(ex.map(lambda a: fn(a, min(a + chunk, n)), starts)))
+
+
 def zipf_pairs(N: int, D: int, M: int, s_row: float, s_col: float, rng):
     """M distinct pairs from the capped product model (module docstring)."""
     p = np.cumsum(zipf_weights(N, s_row, rng))
@@ -91,8 +126,9 @@ def zipf_pairs(N: int, D: int, M: int, s_row: float, s_col: float, rng):
     gq = np.searchsorted(q, np.arange(16 * D) / (16 * D))
 
     def draw(m):
-        r = _inverse_cdf(p, rng.random(m), gp)
-        c = _inverse_cdf(q, rng.random(m), gq)
+        u, v = rng.random(m), rng.random(m)
+        r = _parallel(lambda a, b: _inverse_cdf(p, u[a:b], gp), m)
+        c = _parallel(lambda a, b: _inverse_cdf(q, v[a:b], gq), m)
         return r.astype(np.int64) * D + c
 
     keys = _distinct_keys(draw, M, N * D)
