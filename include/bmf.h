@@ -34,7 +34,8 @@
  *    A propagated factor starts its chain at the propagated mean.
  *  - Moment matching: over the retained samples (sweep t, counted from 1 within a subset's
  *    chain, is retained when t > burnin and (t - burnin - 1) % thin == 0):
- *    mu = mean, Sigma = E[x x^T] - mu mu^T (1/S normaliser), Lambda = Sigma^{-1}.
+ *    mu = mean, Sigma = E[x x^T] - mu mu^T (1/S normaliser), Lambda = Sigma^{-1}.  It needs
+ *    S >= K + 1 retained samples (a full-rank Sigma); fewer fail with BMF_E_STATE.
  *  - Aggregation (Eq. 14, Algorithm 2): for X^(i) submodel "(1)" is subset (i,0) and the
  *    others are (i,j), j >= 1; for W^(j) it is (0,j) and (i,j), i >= 1.  A difference
  *    Lambda^(j) - Lambda^(1) that is not positive definite (FP64 Cholesky pivot <= 0) gets
@@ -52,8 +53,24 @@
  *      ignored.
  *    then z for every X row of the batch (subsets in id order, rows in local order), K each;
  *    then z for every W row of the batch, K each.
- *  Consecutive sweeps follow each other.  With draws == NULL the library draws from its
- *  own device generator (counter-based Philox4x32-10, Salmon et al. SC'11) seeded by cfg.seed.
+ *  Consecutive sweeps follow each other.
+ *
+ * Device generator (draws == NULL).  The library then computes the same buffer on the GPU from
+ * the counter-based generator Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) with key
+ * (cfg.seed, 0) and counter (index, t, tag, attempt), where t is the 1-based sweep number of
+ * the subset's chain and tag = subset id * 256 + factor (0 = X, 1 = W) * 16 + kind:
+ *    kind 3, z of a factor block: element r K + k (local row r) is element e of a normal
+ *      stream; kind 2, the K(K-1)/2 + K normals of a hyperparameter block, likewise.  Element
+ *      e of a normal stream comes from call (e / 4, t, tag, 0): words 0, 1 give elements 4q,
+ *      4q + 1 and words 2, 3 elements 4q + 2, 4q + 3 by Box-Muller, r cos(2 pi u2) and
+ *      r sin(2 pi u2) with r = sqrt(-2 ln u1), u1 = ((w >> 11) + 1) 2^-53, u2 = (w >> 11) 2^-53;
+ *    kind 1, chi-square variate k of a block: 2 Gamma(dof / 2) by Marsaglia & Tsang (ACM TOMS
+ *      2000), attempt j on counter (k, t, tag, j) with the candidate normal from words 0, 1
+ *      (cosine), the acceptance uniform u1 of word 2 and, when dof < 2, the factor
+ *      U^(2 / dof) with U = u1 of word 3 (the shape-below-one boost).  64 rejections in a row
+ *      fail the call with BMF_E_CUDA (probability below 1e-80).
+ *  The numbers depend only on (seed, subset, factor, t, position): batching a stage or
+ *  splitting sweeps across calls does not change them.  bmf_generate_draws returns them.
  *
  * Memory and errors.  The context owns all device memory it allocates.  Host pointers passed
  * in are read during the call only; the caller keeps ownership.  Every call is synchronous
@@ -155,6 +172,13 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
 /* Number of doubles of one sweep's draw buffer for a batch: the subsets of `stage` (1..3)
  * when subset < 0, else the single subset `subset`. */
 int64_t bmf_draws_per_sweep(const bmf_ctx *ctx, int32_t stage, int32_t subset);
+
+/* The device generator's draws (draws == NULL above) of sweeps t0 .. t0 + n_sweeps - 1 (t0 >= 1)
+ * of a batch: the subsets of `stage` when subset < 0, else the single subset `subset`, in the
+ * draw-buffer layout.  out: n_sweeps * bmf_draws_per_sweep() doubles, host memory
+ * (out_on_device = 0) or device memory of the context's GPU (1).  The chains are unchanged. */
+bmf_status bmf_generate_draws(bmf_ctx *ctx, int32_t stage, int32_t subset, int64_t t0,
+                              int32_t n_sweeps, double *out, int32_t out_on_device);
 
 /* n_sweeps Gibbs sweeps of one subset's chain (the whole data for a 1 x 1 grid).  The subset's
  * stage must be open (see bmf_stage).  draws: NULL for the device generator, else the buffer

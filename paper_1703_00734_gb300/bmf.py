@@ -111,6 +111,8 @@ def load(path: str = LIB_PATH):
     L.bmf_langevin.restype = st
     L.bmf_aggregate_static.argtypes = [i32, i64, i32, P, P, f64, P, ctypes.POINTER(i64), P]
     L.bmf_aggregate_static.restype = st
+    L.bmf_generate_draws.argtypes = [P, i32, i32, i64, i32, P, i32]
+    L.bmf_generate_draws.restype = st
     L.bmf_destroy.argtypes = [P]
     L.bmf_destroy.restype = None
     L.bmf_last_error.argtypes = [P]
@@ -204,6 +206,22 @@ class BMF:
     # -- API -------------------------------------------------------------------------------
     def draws_per_sweep(self, stage=1, subset=-1):
         return int(self.L.bmf_draws_per_sweep(self.h, stage, subset))
+
+    def generate_draws(self, t0, n=1, stage=1, subset=-1, out=None):
+        """The device generator's draws of sweeps t0 .. t0 + n - 1 of a batch (stage, or one
+        subset).  out: a device tensor of n * draws_per_sweep doubles, else a host array is
+        returned."""
+        per = self.draws_per_sweep(stage, subset)
+        if per < 0:    # invalid batch: the library reports it
+            self._check(self.L.bmf_generate_draws(self.h, stage, subset, int(t0), int(n), None, 0))
+        if out is not None:
+            assert out.is_cuda and out.numel() == n * per
+            self._check(self.L.bmf_generate_draws(self.h, stage, subset, int(t0), int(n),
+                                                  out.data_ptr(), 1))
+            return out
+        a = np.zeros(n * per)
+        self._check(self.L.bmf_generate_draws(self.h, stage, subset, int(t0), int(n), _ptr(a), 0))
+        return a
 
     def sweep(self, subset=0, n=1, draws=None):
         d, keep = self._draws(draws)

@@ -118,6 +118,11 @@ struct bmf_ctx {
     DevError *err_d = nullptr;
     double *draws_d = nullptr;
     int64_t draws_cap = 0;
+    // device generator: two sweeps' draw buffers (ring) and the segment table
+    double *gen_d = nullptr;
+    int64_t gen_cap = 0;
+    GenSeg *gen_segs_d = nullptr;
+    int64_t gen_segs_cap = 0;
     double *aggX = nullptr, *aggW = nullptr;   // aggregated means, reordered order
     unsigned long long *ncorr_d = nullptr;
     std::vector<SubState> ss;
@@ -140,8 +145,8 @@ struct bmf_ctx {
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
     size_t ev_used = 0;
-    double prof_ms[8] = {0};
-    int64_t prof_n[8] = {0};
+    double prof_ms[9] = {0};
+    int64_t prof_n[9] = {0};
 };
 
 namespace {
@@ -150,8 +155,8 @@ constexpr int kHyperJobsMax = 1 << 16;
 constexpr int kSweepMaxK = 64;
 constexpr int kNarrowMaxK = 16;   // thread-per-row kernels up to here, warp-per-row beyond
 
-enum { K_STATS = 0, K_HYPER, K_GRAM_X, K_COND_X, K_GRAM_W, K_COND_W, K_RMSE, K_ADJ, K_NCLASS };
-const char *kClassName[K_NCLASS] = {"stats", "hyper", "gram_x", "cond_x", "gram_w", "cond_w", "rmse", "adjoint"};
+enum { K_STATS = 0, K_HYPER, K_GRAM_X, K_COND_X, K_GRAM_W, K_COND_W, K_RMSE, K_ADJ, K_GEN, K_NCLASS };
+const char *kClassName[K_NCLASS] = {"stats", "hyper", "gram_x", "cond_x", "gram_w", "cond_w", "rmse", "adjoint", "gen"};
 
 cudaEvent_t pool_event(bmf_ctx *c)
 {
@@ -317,6 +322,8 @@ bmf_status check_dev_error(bmf_ctx *c)
                         "matrix not positive definite (arena row " +
                             std::to_string(h.first_bad_row) + "); the context must be reset "
                             "with bmf_set_state before further sweeps");
+        if (h.flags & ERR_RNG)
+            return fail(c, BMF_E_CUDA, "device generator: 64 chi-square rejections in a row");
         return fail(c, BMF_E_CUDA, "device error flags " + std::to_string(h.flags));
     }
     return BMF_OK;
@@ -442,7 +449,10 @@ bmf_status setup_side(bmf_ctx *c, Side &s, int64_t R, const std::vector<int64_t>
 // Draw buffer of a call on the device.
 bmf_status stage_draws(bmf_ctx *c, const bmf_draws *d, int64_t need, const double **out)
 {
-    if (!d) return fail(c, BMF_E_ARG, "draws == NULL: the device generator is not available in this build");
+    if (!d) {
+        *out = nullptr;   // the device generator fills the sweep buffers
+        return BMF_OK;
+    }
     if (!d->ptr || d->len != need)
         return fail(c, BMF_E_SHAPE, "draw buffer has " + std::to_string(d->len) +
                                         " doubles, expected " + std::to_string(need));
@@ -462,6 +472,49 @@ bmf_status stage_draws(bmf_ctx *c, const bmf_draws *d, int64_t need, const doubl
                                 c->st));
     *out = c->draws_d;
     return BMF_OK;
+}
+
+// Device generator for the batch of slots [sl0, sl1): segment table to the device and room for
+// `nbuf` sweep buffers of `per` doubles.  Returns the generator's thread count in *units.
+bmf_status prepare_gen(bmf_ctx *c, int sl0, int sl1, int64_t per, int nbuf, int64_t *units,
+                       int *n_segs)
+{
+    std::vector<GenSubset> subs;
+    for (int sl = sl0; sl < sl1; ++sl) {
+        const SubsetGeom &g = geom_of_slot(c, sl);
+        subs.push_back(GenSubset{g.sid, g.n(), g.d()});
+    }
+    std::vector<GenSeg> segs;
+    *units = gen_segments(subs, c->K, c->nu0, segs);
+    *n_segs = (int)segs.size();
+    if ((int64_t)segs.size() > c->gen_segs_cap) {
+        if (c->gen_segs_d) cudaFree(c->gen_segs_d);
+        c->gen_segs_d = nullptr;
+        c->gen_segs_cap = 0;
+        if (cudaMalloc(&c->gen_segs_d, segs.size() * sizeof(GenSeg)) != cudaSuccess)
+            return fail(c, BMF_E_OOM, "device allocation failed (generator segments)");
+        c->gen_segs_cap = (int64_t)segs.size();
+    }
+    if (!segs.empty())
+        CUDA_TRY(c, cudaMemcpyAsync(c->gen_segs_d, segs.data(), segs.size() * sizeof(GenSeg),
+                                    cudaMemcpyHostToDevice, c->st));
+    const int64_t need = (int64_t)nbuf * per;
+    if (need > c->gen_cap) {
+        CUDA_TRY(c, cudaStreamSynchronize(c->st));
+        if (c->gen_d) cudaFree(c->gen_d);
+        c->gen_d = nullptr;
+        c->gen_cap = 0;
+        if (cudaMalloc(&c->gen_d, need * sizeof(double)) != cudaSuccess)
+            return fail(c, BMF_E_OOM, "device allocation failed (generator buffers)");
+        c->gen_cap = need;
+    }
+    return BMF_OK;
+}
+
+void enqueue_gen(bmf_ctx *c, int64_t units, int n_segs, int64_t t, double *out)
+{
+    GenParams gp{c->gen_segs_d, n_segs, units, c->seed, t, out, c->err_d};
+    traced(c, c->st, K_GEN, 1, [&] { launch_gen(gp, c->st); });
 }
 
 bool keep_sample(const bmf_ctx *c, int64_t t)
@@ -491,6 +544,20 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
     const double *dr = nullptr;
     bmf_status s = stage_draws(c, draws, per * n_sweeps, &dr);
     if (s) return s;
+    // with the device generator, sweep it's draws live in ring buffer it % 2: the main stream
+    // fills sweep it + 2 after sweep it's conditionals, which are ordered after every reader
+    // of that buffer (the side stream's hyperparameter draw of sweep it finishes before them)
+    const bool gen = dr == nullptr;
+    int64_t gen_units = 0;
+    int gen_segs = 0;
+    if (gen && n_sweeps > 0) {
+        if ((s = prepare_gen(c, sl0, sl1, per, 2, &gen_units, &gen_segs))) return s;
+        for (int it = 0; it < std::min(n_sweeps, 2); ++it)
+            enqueue_gen(c, gen_units, gen_segs, t_start + it + 1, c->gen_d + (int64_t)it * per);
+    }
+    auto draws_of = [&](int it) -> const double * {
+        return gen ? c->gen_d + (int64_t)(it & 1) * per : dr + (int64_t)it * per;
+    };
     // hyperparameter jobs: every factor block without a per-row prior (X jobs first).  A job
     // sums the statistics slots of its subset's conditional-kernel blocks, which the standalone
     // statistics pass fills before the first sweep and the conditional kernel refreshes after.
@@ -525,7 +592,7 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
     // it+1 depend only on the X written by sweep it, so they run while the main stream does
     // W | X of sweep it and the Gram pass of sweep it+1 (and symmetrically for W).
     auto side_hyper = [&](int f, int it) -> bmf_status {
-        const double *d = dr + (int64_t)it * per;
+        const double *d = draws_of(it);
         const HyperJob *jb = c->d_jobs + (f == 0 ? 0 : nj[0]);
         HyperParams hp{K, jb, nj[f], c->stats, c->mu0_d, c->beta0, c->nu0, c->W0inv_d, d,
                        c->hyper, c->err_d};
@@ -551,7 +618,7 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
             if (hyp[f] && (s = side_hyper(f, 0))) return s;
     }
     for (int it = 0; it < n_sweeps; ++it) {
-        const double *d = dr + (int64_t)it * per;
+        const double *d = draws_of(it);
         const int64_t t = t_start + it + 1;
         const bool keep = keep_sample(c, t);
         if (keep) ++kept;
@@ -642,6 +709,8 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
                 launch_rmse_final(c->rmse_part, c->rmse_blocks, c->rmse_out, c->st);
             });
         }
+        if (gen && it + 2 < n_sweeps)
+            enqueue_gen(c, gen_units, gen_segs, t + 2, c->gen_d + (int64_t)(it & 1) * per);
     }
     CUDA_TRY(c, cudaGetLastError());
     for (int sl = sl0; sl < sl1; ++sl) {
@@ -682,6 +751,10 @@ bmf_status finalize_stage(bmf_ctx *c, int stage)
                                             " has no retained samples (burn-in not passed)");
         if (!c->full_moments)
             return fail(c, BMF_E_STATE, "moment matching needs second moments (moments mode)");
+        if (su.kept < c->K + 1)
+            return fail(c, BMF_E_STATE, "subset " + std::to_string(g.sid) + " has " +
+                                            std::to_string(su.kept) + " retained samples; moment "
+                                            "matching needs at least K + 1 (a full-rank covariance)");
         if (c->K > kNarrowMaxK)
             return fail(c, BMF_E_ARG, "moment matching supports K <= 16 in this build");
         for (int f = 0; f < 2; ++f) {
@@ -1051,6 +1124,38 @@ int64_t bmf_draws_per_sweep(const bmf_ctx *c, int32_t stage, int32_t subset)
     return per_sweep_draws(c, sl0, sl1);
 }
 
+bmf_status bmf_generate_draws(bmf_ctx *c, int32_t stage, int32_t subset, int64_t t0,
+                              int32_t n_sweeps, double *out, int32_t out_on_device)
+{
+    if (!c) return BMF_E_ARG;
+    int sl0, sl1;
+    if (subset >= 0) {
+        if (!valid_subset(c, subset)) return fail(c, BMF_E_ARG, "subset out of range");
+        sl0 = c->P.subs[subset].slot;
+        sl1 = sl0 + 1;
+    } else if (!stage_slots(c, stage, sl0, sl1)) {
+        return fail(c, BMF_E_ARG, "stage has no subsets");
+    }
+    if (t0 < 1 || n_sweeps < 0) return fail(c, BMF_E_ARG, "need t0 >= 1 and n_sweeps >= 0");
+    if (n_sweeps > 0 && !out) return fail(c, BMF_E_ARG, "out is NULL");
+    const int64_t per = per_sweep_draws(c, sl0, sl1);
+    int64_t units = 0;
+    int n_segs = 0;
+    bmf_status s = prepare_gen(c, sl0, sl1, per, out_on_device ? 0 : 1, &units, &n_segs);
+    if (s) return s;
+    for (int i = 0; i < n_sweeps; ++i) {
+        double *dst = out_on_device ? out + (int64_t)i * per : c->gen_d;
+        enqueue_gen(c, units, n_segs, t0 + i, dst);
+        if (!out_on_device)
+            CUDA_TRY(c, cudaMemcpyAsync(out + (int64_t)i * per, c->gen_d, per * sizeof(double),
+                                        cudaMemcpyDeviceToHost, c->st));
+    }
+    CUDA_TRY(c, cudaGetLastError());
+    s = check_dev_error(c);
+    if (c->prof) collect_profile(c);
+    return s;
+}
+
 bmf_status bmf_sweep(bmf_ctx *c, int32_t subset, int32_t n_sweeps, const bmf_draws *draws,
                      bmf_sweep_stats *stats)
 {
@@ -1224,6 +1329,10 @@ bmf_status bmf_get_posterior(bmf_ctx *c, int32_t subset, int32_t factor, double 
         if (su.kept < 1) return fail(c, BMF_E_STATE, "no retained samples");
         if (!c->full_moments)
             return fail(c, BMF_E_STATE, "moment matching needs second moments (moments mode)");
+        if (su.kept < c->K + 1)
+            return fail(c, BMF_E_STATE, "subset " + std::to_string(g.sid) + " has " +
+                                            std::to_string(su.kept) + " retained samples; moment "
+                                            "matching needs at least K + 1 (a full-rank covariance)");
         if (c->K > kNarrowMaxK)
             return fail(c, BMF_E_ARG, "moment matching supports K <= 16 in this build");
         for (int f = 0; f < 2; ++f) {
@@ -1550,6 +1659,8 @@ void bmf_destroy(bmf_ctx *c)
     if (!c) return;
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->draws_d) cudaFree(c->draws_d);
+    if (c->gen_d) cudaFree(c->gen_d);
+    if (c->gen_segs_d) cudaFree(c->gen_segs_d);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (void *p : {(void *)c->adj_part, (void *)c->adj_sums, (void *)c->fval[0], (void *)c->fval[1],
                     (void *)c->lg_buf})

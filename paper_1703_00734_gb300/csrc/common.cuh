@@ -43,6 +43,7 @@ enum : uint32_t {
     ERR_NONFINITE = 1u << 1,
     ERR_TIMEOUT = 1u << 2,
     ERR_ARG = 1u << 3,
+    ERR_RNG = 1u << 4,      // chi-square rejection limit of the device generator
 };
 
 struct DevError {

@@ -1,6 +1,7 @@
 // kernels.h -- launchers of the library's CUDA kernels (internal).
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -219,6 +220,35 @@ void launch_langevin(float *theta, const float *grad, const float *xi, int64_t n
 void launch_to_float(const double *in, float *out, int64_t n, cudaStream_t st);
 void launch_sqdiff(const float *a, const float *b, const float *g, double coef, int64_t n_rows,
                    int K, int64_t ld, double *block_sums, int blocks, cudaStream_t st);
+
+// Device generator of the draws (counter-based, see rng.cu).  A segment is one stream of the
+// draw buffer: kind 1 chi-square variates (one thread each, dof0 - k for variate k), kind 2/3
+// normals (one thread per four).
+struct GenSeg {
+    int64_t unit0;   // first thread of the segment
+    int64_t count;   // numbers in the segment
+    int64_t out;     // offset in the sweep's draw buffer
+    uint64_t tag;    // subset id * 256 + factor * 16 + kind
+    double dof0;
+    int32_t kind;
+};
+struct GenParams {
+    const GenSeg *segs;
+    int n_segs;
+    int64_t n_units;
+    uint64_t seed;
+    int64_t t;       // 1-based sweep number of the batch's chains
+    double *out;
+    DevError *err;
+};
+struct GenSubset {
+    int32_t sid;
+    int64_t n, d;
+};
+void launch_gen(const GenParams &p, cudaStream_t st);
+// Segments of one sweep's buffer for the batch `subs` (id order); returns the thread count.
+int64_t gen_segments(const std::vector<GenSubset> &subs, int K, double nu0,
+                     std::vector<GenSeg> &segs);
 
 // Device helpers
 void launch_fill_gather(int K, int prec, int64_t R, const double *X, void *Xg, int ldg,

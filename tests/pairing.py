@@ -31,9 +31,13 @@ class Pair:
     """A library context and the oracle's chains on the same data."""
 
     def __init__(self, d, K, I=1, J=1, precision="fp64", burnin=0, thin=1, seed=11, center=True,
-                 order="decreasing", prior=None, **kw):
+                 order="decreasing", prior=None, gen=False, **kw):
+        """gen: draws from the counter-based generator (the library's device generator with
+        draws == NULL, the oracle's own implementation of it), else from synth."""
         from paper_1703_00734_gb300 import bmf
-        self.d, self.K, self.seed = d, K, seed
+        self.d, self.K, self.seed, self.gen = d, K, seed, gen
+        if gen:
+            kw["seed"] = seed
         self.prior = prior or oracle.NWPrior(K)
         self.burnin, self.thin = burnin, thin
         test = (d["test_row"], d["test_col"], d["test_val"]) if len(d["test_row"]) else None
@@ -50,6 +54,8 @@ class Pair:
 
     def draws(self, stage, t, subsets=None):
         subs = subsets if subsets is not None else self.p.stage_subsets(stage)
+        if self.gen:
+            return oracle.gen_batch_draws(subs, self.K, self.prior.nu0, self.seed, t + 1)
         return synth.sweep_draws([(s.n, s.d) for s in subs], self.K, self.prior.nu0,
                                  synth.rng_for(self.seed, stage, t))
 
@@ -65,7 +71,7 @@ class Pair:
                              lambda t: self.draws(stage, t0 + t), T, self.burnin, self.thin)
         stats = None
         if gpu:
-            dr = np.concatenate([self.draws(stage, t0 + t) for t in range(T)])
+            dr = None if self.gen else np.concatenate([self.draws(stage, t0 + t) for t in range(T)])
             stats = self.m.stage(stage, T, dr)
         return stats
 
