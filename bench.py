@@ -99,10 +99,10 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------------------
-def load_workload(name):
+def load_workload(name, scale=1.0):
     from paper_1703_00734_gb300 import synth
     t = time.time()
-    d = synth.make_workload(name)
+    d = synth.make_workload(name, scale=scale)
     log(f"workload {name}: N={d['N']} D={d['D']} train={len(d['row'])} "
         f"test={len(d['test_row'])} ({time.time() - t:.1f}s)")
     return d
@@ -142,7 +142,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
-    d = load_workload(args.workload)
+    d = load_workload(args.workload, args.scale)
     K, tau = d["K"], d["tau"]
     nu0 = float(K)
     test = (d["test_row"], d["test_col"], d["test_val"])
@@ -276,9 +276,110 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         out["cpu_baseline"] = cpu_baseline(d, args.cpu_seconds)
     return out
+
+
+# ---------------------------------------------------------------------------------------
+# posterior propagation on an I x J grid: three batched stages, then Algorithm 2
+# ---------------------------------------------------------------------------------------
+PP_CHUNK = 25
+
+
+def run_pp(args, rank, world, local_rank):
+    import torch
+    from paper_1703_00734_gb300 import bmf, synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    d = load_workload(args.workload, args.scale)
+    K, tau, I, J = d["K"], d["tau"], d["I"], d["J"]
+    T, B = args.steps, max(1, args.steps // 2)
+    test = (d["test_row"], d["test_col"], d["test_val"])
+    m = bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], K, tau, args.precision, I=I, J=J,
+                X0=d["X0"], W0=d["W0"], burnin=B, seed=rank, stream=stream.cuda_stream)
+    stage_ms, launches, sizes_all = [], 0, {}
+    m.profile(True)
+    with ClockSampler(local_rank) as clk:
+        for stage in (1, 2, 3):
+            sizes = []
+            for sid in range(I * J):
+                info = m.subset_info(sid)
+                if info["stage"] == stage:
+                    sizes.append((info["row1"] - info["row0"], info["col1"] - info["col0"]))
+            sizes_all[stage] = sizes
+            ms = 0.0
+            for c0 in range(0, T, PP_CHUNK):    # draws in chunks of sweeps (host memory)
+                nc = min(PP_CHUNK, T - c0)
+                host = np.concatenate([synth.sweep_draws(sizes, K, float(K),
+                                                         synth.rng_for(300 + rank, stage, t))
+                                       for t in range(c0, c0 + nc)])
+                dr = torch.from_numpy(host).to(dev)
+                torch.cuda.synchronize()
+                n0 = m.launch_count()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                m.stage(stage, nc, dr)
+                e1.record(stream)
+                e1.synchronize()
+                ms += e0.elapsed_time(e1)
+                launches += m.launch_count() - n0
+                del dr
+            stage_ms.append(ms)
+        t0 = time.perf_counter()
+        yh, r_pp = m.predict(d["test_row"], d["test_col"], d["test_val"])
+        agg_ms = (time.perf_counter() - t0) * 1e3
+    prof = m.profile_read()
+    m.close()
+    # plain sampler on the whole matrix for the same number of sweeps
+    plain = {}
+    for prec in ("fp64", args.precision):
+        mp = bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], K, tau, prec, X0=d["X0"],
+                     W0=d["W0"], test=test, burnin=B, seed=rank, stream=stream.cuda_stream)
+        ms = 0.0
+        for c0 in range(0, T, PP_CHUNK):
+            nc = min(PP_CHUNK, T - c0)
+            host = np.concatenate([synth.sweep_draws([(d["N"], d["D"])], K, float(K),
+                                                     synth.rng_for(400 + rank, t))
+                                   for t in range(c0, c0 + nc)])
+            dr = torch.from_numpy(host).to(dev)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mp.sweep(0, nc, dr)
+            b.record(stream)
+            b.synchronize()
+            ms += a.elapsed_time(b)
+            del dr
+        _, r_plain = mp.predict(d["test_row"], d["test_col"], d["test_val"])
+        plain[prec] = {"ms": ms, "sweeps_per_s": T / (ms / 1e3), "rmse": r_plain}
+        mp.close()
+    if rank != 0:
+        return None
+    M = len(d["row"])
+    total_ms = sum(stage_ms)
+    obs_sides = 2 * M   # every training entry is in exactly one subset, visited by both halves
+    kernels = {k: {"launches": n, "avg_us": t / n * 1e3} for k, (n, t) in prof.items() if n}
+    return {
+        "metric": "PP stage sweeps/s (all subsets of a stage batched)", "impl": "ours",
+        "value": 3 * T / (total_ms / 1e3), "unit": "stage sweeps/s", "n_gpus": world,
+        "steps": 3 * T, "warmup": 0, "ms_per_step": total_ms / (3 * T), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "N": d["N"], "D": d["D"], "train_obs": M, "K": K,
+                   "grid": f"{I}x{J}", "subsets_per_stage": [len(sizes_all[s]) for s in (1, 2, 3)],
+                   "sweeps_per_stage": T, "burnin": B, "precision": args.precision},
+        "stage_ms": stage_ms, "aggregate_predict_ms": agg_ms,
+        "obsK2_gflops_pp": obs_sides / 3 * 3 * T * 2 * K * K / (total_ms / 1e3) / 1e9,
+        "rmse": {"pp": r_pp, "plain_fp64": plain["fp64"]["rmse"],
+                 "plain_reduced": plain[args.precision]["rmse"],
+                 "abs_diff_vs_plain_fp64": abs(r_pp - plain["fp64"]["rmse"])},
+        "plain": plain,
+        "pp_speedup_vs_plain_fp64_same_sweeps": plain["fp64"]["ms"] / total_ms,
+        "kernels": kernels, "gpu_launches": launches, "clocks": clk.summary(),
+    }
 
 
 def traffic_for(kernel, prec):
@@ -362,12 +463,19 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink the workload (rows and columns by s, observations by s^2); "
+                         "for profiling captures only, not a bench configuration")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    from paper_1703_00734_gb300 import synth as _synth
+    pp = _synth.WORKLOADS.get(args.workload, {}).get("I", 1) > 1
     if args.impl == "reference":
         out = run_reference(args, rank)
+    elif pp:
+        out = run_pp(args, rank, world, local_rank)
     else:
         if world > 1:
             import torch

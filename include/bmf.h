@@ -180,6 +180,24 @@ int64_t bmf_draws_per_sweep(const bmf_ctx *ctx, int32_t stage, int32_t subset);
 bmf_status bmf_generate_draws(bmf_ctx *ctx, int32_t stage, int32_t subset, int64_t t0,
                               int32_t n_sweeps, double *out, int32_t out_on_device);
 
+/* Launch schedule of the sweeps (no counterpart in the paper; the sampled values do not depend
+ * on it).  chunks_x / chunks_w (1..BMF_MAX_CHUNKS): the rows of the X (W) half of a batch are
+ * split at conditional-block boundaries into this many chunks of about equal estimated cost
+ * (observations + row_weight x rows); each chunk's Gram pass runs on the context stream, the
+ * lightest rows first, and its conditional draw on a second stream as soon as that pass is
+ * done, so that the FP64 conditional of one chunk overlaps the Gram pass of the next (1: one
+ * Gram launch, then one conditional launch).  gram_blocks_per_sm (1..64): grid of a Gram
+ * launch = SMs x this.  row_weight (>= 0): cost of a row in observations for the split; 0
+ * selects a default from K and the precision.  Default {1, 1, 4, 0}. */
+#define BMF_MAX_CHUNKS 8
+typedef struct {
+    int32_t chunks_x, chunks_w;
+    int32_t gram_blocks_per_sm;
+    double row_weight;
+} bmf_schedule;
+bmf_status bmf_set_schedule(bmf_ctx *ctx, const bmf_schedule *sched);
+bmf_status bmf_get_schedule(const bmf_ctx *ctx, bmf_schedule *sched);
+
 /* n_sweeps Gibbs sweeps of one subset's chain (the whole data for a 1 x 1 grid).  The subset's
  * stage must be open (see bmf_stage).  draws: NULL for the device generator, else the buffer
  * for n_sweeps sweeps of this single-subset batch.  stats may be NULL. */

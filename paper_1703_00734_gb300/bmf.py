@@ -50,6 +50,11 @@ class KernelTime(ctypes.Structure):
                 ("total_ms", ctypes.c_double)]
 
 
+class Schedule(ctypes.Structure):
+    _fields_ = [("chunks_x", ctypes.c_int32), ("chunks_w", ctypes.c_int32),
+                ("gram_blocks_per_sm", ctypes.c_int32), ("row_weight", ctypes.c_double)]
+
+
 class SubsetInfo(ctypes.Structure):
     _fields_ = [("i", ctypes.c_int32), ("j", ctypes.c_int32), ("stage", ctypes.c_int32),
                 ("row0", ctypes.c_int64), ("row1", ctypes.c_int64), ("col0", ctypes.c_int64),
@@ -111,6 +116,10 @@ def load(path: str = LIB_PATH):
     L.bmf_langevin.restype = st
     L.bmf_aggregate_static.argtypes = [i32, i64, i32, P, P, f64, P, ctypes.POINTER(i64), P]
     L.bmf_aggregate_static.restype = st
+    L.bmf_set_schedule.argtypes = [P, ctypes.POINTER(Schedule)]
+    L.bmf_set_schedule.restype = st
+    L.bmf_get_schedule.argtypes = [P, ctypes.POINTER(Schedule)]
+    L.bmf_get_schedule.restype = st
     L.bmf_generate_draws.argtypes = [P, i32, i32, i64, i32, P, i32]
     L.bmf_generate_draws.restype = st
     L.bmf_destroy.argtypes = [P]
@@ -206,6 +215,18 @@ class BMF:
     # -- API -------------------------------------------------------------------------------
     def draws_per_sweep(self, stage=1, subset=-1):
         return int(self.L.bmf_draws_per_sweep(self.h, stage, subset))
+
+    def set_schedule(self, chunks_x=1, chunks_w=1, gram_blocks_per_sm=4, row_weight=0.0):
+        """Launch schedule (include/bmf.h, bmf_schedule); the sampled values do not depend on it."""
+        sc = Schedule(chunks_x=chunks_x, chunks_w=chunks_w, gram_blocks_per_sm=gram_blocks_per_sm,
+                      row_weight=float(row_weight))
+        self._check(self.L.bmf_set_schedule(self.h, ctypes.byref(sc)))
+
+    def get_schedule(self):
+        sc = Schedule()
+        self._check(self.L.bmf_get_schedule(self.h, ctypes.byref(sc)))
+        return dict(chunks_x=sc.chunks_x, chunks_w=sc.chunks_w,
+                    gram_blocks_per_sm=sc.gram_blocks_per_sm, row_weight=sc.row_weight)
 
     def generate_draws(self, t0, n=1, stage=1, subset=-1, out=None):
         """The device generator's draws of sweeps t0 .. t0 + n - 1 of a batch (stage, or one

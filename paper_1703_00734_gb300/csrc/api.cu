@@ -54,7 +54,9 @@ struct Side {
     int64_t *item_ptr = nullptr; // [R+1]
     GramTask *tasks = nullptr;   // warp tasks, grouped per slot
     std::vector<int64_t> slot_task;  // [S+1] first task of each slot
+    std::vector<int64_t> blk_task;   // [blocks+1] first task of each conditional block
     std::vector<int64_t> h_item_ptr;
+    std::vector<int64_t> h_obs;      // [R+1] observation offsets (chunk costs)
     int32_t *hslot = nullptr;    // [R] hyper slot or -1
     std::vector<int32_t> h_hslot;
     // rows with more than one Gram work item, their FP64 sums
@@ -81,14 +83,20 @@ struct SubState {
 
 }  // namespace
 
+constexpr int kMaxChunks = BMF_MAX_CHUNKS;
+
 struct bmf_ctx {
     ~bmf_ctx()
     {
-        if (st2) {
-            cudaStreamSynchronize(st2);
-            cudaStreamDestroy(st2);
-        }
-        for (cudaEvent_t e : {ev_fork, ev_fac[0], ev_fac[1], ev_hyp[0], ev_hyp[1]})
+        for (cudaStream_t x : {st2, st3, st4})
+            if (x) {
+                cudaStreamSynchronize(x);
+                cudaStreamDestroy(x);
+            }
+        for (cudaEvent_t e : {ev_fork, ev_fac[0], ev_fac[1], ev_hyp[0], ev_hyp[1], ev_cdone, ev_tail,
+                              ev_rmse, ev_gen[0], ev_gen[1]})
+            if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : ev_chunk)
             if (e) cudaEventDestroy(e);
     }
     int K = 0, prec = BMF_FP64;
@@ -99,7 +107,12 @@ struct bmf_ctx {
     HostPlan P;
     cudaStream_t st = nullptr;
     cudaStream_t st2 = nullptr;      // side stream: factor statistics and hyperparameter draws
+    cudaStream_t st3 = nullptr;      // conditional stream of the chunked schedule
+    cudaStream_t st4 = nullptr;      // tail stream: test RMSE and the device generator
     cudaEvent_t ev_fork = nullptr, ev_fac[2] = {nullptr, nullptr}, ev_hyp[2] = {nullptr, nullptr};
+    cudaEvent_t ev_chunk[kMaxChunks] = {}, ev_cdone = nullptr;
+    cudaEvent_t ev_tail = nullptr, ev_rmse = nullptr, ev_gen[2] = {nullptr, nullptr};
+    bmf_schedule sched = {1, 1, 4, 0.0};
     int device = 0, sms = 1;
     DevMem mem;
     Side X, W;
@@ -310,6 +323,8 @@ bmf_status upload_hslots(bmf_ctx *c, int sl)
 bmf_status check_dev_error(bmf_ctx *c)
 {
     if (c->st2) CUDA_TRY(c, cudaStreamSynchronize(c->st2));
+    if (c->st3) CUDA_TRY(c, cudaStreamSynchronize(c->st3));
+    if (c->st4) CUDA_TRY(c, cudaStreamSynchronize(c->st4));
     DevError h;
     CUDA_TRY(c, cudaMemcpyAsync(&h, c->err_d, sizeof(h), cudaMemcpyDeviceToHost, c->st));
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
@@ -354,6 +369,7 @@ bmf_status setup_side(bmf_ctx *c, Side &s, int64_t R, const std::vector<int64_t>
         }
     }
     std::vector<GramItem> items;
+    s.h_obs = ptr;
     s.h_item_ptr.assign(R + 1, 0);
     for (int64_t r = 0; r < R; ++r) {
         s.h_item_ptr[r] = (int64_t)items.size();
@@ -392,6 +408,12 @@ bmf_status setup_side(bmf_ctx *c, Side &s, int64_t R, const std::vector<int64_t>
             const int64_t r0 = xs ? g.xoff : g.woff, r1 = r0 + (xs ? g.n() : g.d());
             GramTask cur{0, 0, 0};
             for (int64_t r = r0; r < r1; ++r) {
+                // tasks never cross a conditional block, so that any block range of the batch
+                // is a task range (the chunked schedule of run_batch)
+                if ((r - r0) % kCondBlock == 0) {
+                    if (cur.n) tasks.push_back(cur), cur.n = 0;
+                    s.blk_task.push_back((int64_t)tasks.size());
+                }
                 const int64_t i0 = s.h_item_ptr[r], i1 = s.h_item_ptr[r + 1];
                 if (i1 == i0) continue;
                 const int G = (i1 - i0 > 1) ? 32 : gram_group(items[i0].count);
@@ -408,6 +430,7 @@ bmf_status setup_side(bmf_ctx *c, Side &s, int64_t R, const std::vector<int64_t>
             if (cur.n) tasks.push_back(cur);
         }
         s.slot_task[S] = (int64_t)tasks.size();
+        s.blk_task.push_back((int64_t)tasks.size());
         s.tasks = c->mem.alloc<GramTask>(tasks.size());
         if (!c->mem.ok) return fail(c, BMF_E_OOM, "device allocation failed (tasks)");
         if (!tasks.empty())
@@ -522,6 +545,37 @@ bool keep_sample(const bmf_ctx *c, int64_t t)
     return t > c->burnin && (t - c->burnin - 1) % c->thin == 0;
 }
 
+// Row chunks of one sweep half for the chunked schedule: block boundaries b0 = B[0] < ... <
+// B[n] = b1 at equal quantiles of an estimated cost (observations + row_weight x rows).
+std::vector<int64_t> chunk_bounds(const bmf_ctx *c, const Side &sd, int64_t b0, int64_t b1,
+                                  int n_chunks, int64_t r_end)
+{
+    std::vector<int64_t> B{b0};
+    const int64_t nb = b1 - b0;
+    const int n = (int)std::min<int64_t>(std::max(n_chunks, 1), std::max<int64_t>(nb, 1));
+    if (n <= 1 || nb <= 1) {
+        B.push_back(b1);
+        return B;
+    }
+    const double w = c->sched.row_weight > 0.0
+                         ? c->sched.row_weight
+                         : (c->prec == BMF_FP64 ? 1.5 : 14.0) * c->K;
+    auto row_of = [&](int64_t b) { return b == b1 ? r_end : sd.h_blocks[b].row0; };
+    std::vector<double> cum(nb + 1, 0.0);
+    for (int64_t b = b0; b < b1; ++b) {
+        const int64_t ra = row_of(b), rb = row_of(b + 1);
+        cum[b - b0 + 1] = cum[b - b0] + (double)(sd.h_obs[rb] - sd.h_obs[ra]) + w * (double)(rb - ra);
+    }
+    int64_t q = 0;
+    for (int k = 1; k < n; ++k) {
+        const double target = cum[nb] * k / n;
+        while (q < nb && cum[q] < target) ++q;
+        if (q > B.back() - b0 && q < nb) B.push_back(b0 + q);
+    }
+    B.push_back(b1);
+    return B;
+}
+
 // n sweeps of the subsets in slots [sl0, sl1) (a stage, or one subset), batched.
 bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws *draws,
                      bmf_sweep_stats *stats)
@@ -558,6 +612,11 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
     auto draws_of = [&](int it) -> const double * {
         return gen ? c->gen_d + (int64_t)(it & 1) * per : dr + (int64_t)it * per;
     };
+    const std::vector<int64_t> bounds[2] = {
+        chunk_bounds(c, c->X, c->X.slot_blk[sl0], c->X.slot_blk[sl1], c->sched.chunks_x, rx1),
+        chunk_bounds(c, c->W, c->W.slot_blk[sl0], c->W.slot_blk[sl1], c->sched.chunks_w, rw1)};
+    const size_t pbytes = c->prec == BMF_FP64 ? 8 : 4;
+    const int gram_grid = c->sms * std::max(1, c->sched.gram_blocks_per_sm);
     // hyperparameter jobs: every factor block without a per-row prior (X jobs first).  A job
     // sums the statistics slots of its subset's conditional-kernel blocks, which the standalone
     // statistics pass fills before the first sweep and the conditional kernel refreshes after.
@@ -593,6 +652,7 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
     // W | X of sweep it and the Gram pass of sweep it+1 (and symmetrically for W).
     auto side_hyper = [&](int f, int it) -> bmf_status {
         const double *d = draws_of(it);
+        if (gen && it >= 2) CUDA_TRY(c, cudaStreamWaitEvent(c->st2, c->ev_gen[it & 1], 0));
         const HyperJob *jb = c->d_jobs + (f == 0 ? 0 : nj[0]);
         HyperParams hp{K, jb, nj[f], c->stats, c->mu0_d, c->beta0, c->nu0, c->W0inv_d, d,
                        c->hyper, c->err_d};
@@ -648,18 +708,54 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
             gp.rowsum = me.rowsum;
             gp.ld_sum = part_nv(K);
             gp.nv = part_nv(K);
-            if (K > kNarrowMaxK) {
-                if (gp.n_items > 0)
-                    traced(c, c->st, f == 0 ? K_GRAM_X : K_GRAM_W, 1,
-                           [&] { launch_gram_wide(K, c->prec, gp, c->sms * 4, c->st); });
-            } else if (gp.n_tasks > 0) {
-                traced(c, c->st, f == 0 ? K_GRAM_X : K_GRAM_W, 1,
-                       [&] { launch_gram(K, c->prec, gp, c->sms * 4, c->st); });
+            const int64_t b0 = me.slot_blk[sl0], b1 = me.slot_blk[sl1];
+            // Gram pass over the rows of conditional blocks [ba, bb)
+            auto gram_chunk = [&](int64_t ba, int64_t bb) {
+                GramParams g = gp;
+                if (K > kNarrowMaxK) {
+                    const int64_t ia = ba == b1 ? i1 : me.h_item_ptr[me.h_blocks[ba].row0];
+                    const int64_t ib = bb == b1 ? i1 : me.h_item_ptr[me.h_blocks[bb].row0];
+                    g.items = me.items + ia;
+                    g.n_items = ib - ia;
+                    g.item0 = ia;
+                    g.part = static_cast<char *>(c->part) + (ia - i0) * c->ld_part * pbytes;
+                    if (g.n_items > 0)
+                        traced(c, c->st, f == 0 ? K_GRAM_X : K_GRAM_W, 1,
+                               [&] { launch_gram_wide(K, c->prec, g, gram_grid, c->st); });
+                } else {
+                    g.tasks = me.tasks + me.blk_task[ba];
+                    g.n_tasks = me.blk_task[bb] - me.blk_task[ba];
+                    if (g.n_tasks > 0)
+                        traced(c, c->st, f == 0 ? K_GRAM_X : K_GRAM_W, 1,
+                               [&] { launch_gram(K, c->prec, g, gram_grid, c->st); });
+                }
+            };
+            const std::vector<int64_t> &B = bounds[f];
+            const int nch = (int)B.size() - 1;
+            cudaStream_t cs = nch == 1 ? c->st : c->st3;
+            if (nch == 1) gram_chunk(b0, b1);
+            if (f == 0) {
+                // the previous sweep's RMSE pass reads the gathered copies this sweep rewrites;
+                // the generator fills this sweep's draws on the tail stream
+                if (it > 0 && tt1 > tt0) CUDA_TRY(c, cudaStreamWaitEvent(cs, c->ev_rmse, 0));
+                if (gen && it >= 2) CUDA_TRY(c, cudaStreamWaitEvent(cs, c->ev_gen[it & 1], 0));
             }
-            if (hyp[f]) CUDA_TRY(c, cudaStreamWaitEvent(c->st, c->ev_hyp[f], 0));
+            if (nch == 1) {
+                if (hyp[f]) CUDA_TRY(c, cudaStreamWaitEvent(c->st, c->ev_hyp[f], 0));
+            } else {
+                // chunked schedule: the Gram passes run in order on the main stream, lightest
+                // rows first (rows are in decreasing degree order); each chunk's conditional
+                // follows on the conditional stream as soon as its Gram pass is done, so the
+                // FP64-bound conditional of one chunk overlaps the gather-bound Gram pass of the
+                // next
+                for (int q = nch - 1; q >= 0; --q) {
+                    gram_chunk(B[q], B[q + 1]);
+                    CUDA_TRY(c, cudaEventRecord(c->ev_chunk[q], c->st));
+                }
+                if (hyp[f]) CUDA_TRY(c, cudaStreamWaitEvent(c->st3, c->ev_hyp[f], 0));
+            }
             CondParams cp;
             cp.K = K;
-            const int64_t b0 = me.slot_blk[sl0], b1 = me.slot_blk[sl1];
             cp.blocks = me.blocks + b0;
             cp.blk0 = me.stat0 + b0;
             cp.row0 = r0;
@@ -688,29 +784,63 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
             cp.S2 = me.S2;
             cp.stats = c->stats;
             cp.err = c->err_d;
-            if (b1 > b0)
-                traced(c, c->st, f == 0 ? K_COND_X : K_COND_W, 1, [&] {
+            auto cond_chunk = [&](int64_t ba, int64_t bb, cudaStream_t sx) {
+                if (bb <= ba) return;
+                CondParams q = cp;
+                q.blocks = me.blocks + ba;
+                q.blk0 = me.stat0 + ba;
+                traced(c, sx, f == 0 ? K_COND_X : K_COND_W, 1, [&] {
                     if (K > kNarrowMaxK)
-                        launch_cond_wide(c->prec, cp, (int)(b1 - b0), c->st);
+                        launch_cond_wide(c->prec, q, (int)(bb - ba), sx);
                     else
-                        launch_cond(c->prec, cp, (int)(b1 - b0), c->st);
+                        launch_cond(c->prec, q, (int)(bb - ba), sx);
                 });
+            };
+            if (nch == 1) {
+                cond_chunk(b0, b1, c->st);
+            } else {
+                for (int q = nch - 1; q >= 0; --q) {
+                    CUDA_TRY(c, cudaStreamWaitEvent(c->st3, c->ev_chunk[q], 0));
+                    cond_chunk(B[q], B[q + 1], c->st3);
+                }
+                CUDA_TRY(c, cudaEventRecord(c->ev_cdone, c->st3));
+                CUDA_TRY(c, cudaStreamWaitEvent(c->st, c->ev_cdone, 0));
+            }
             if (hyp[f] && it + 1 < n_sweeps) {
                 CUDA_TRY(c, cudaEventRecord(c->ev_fac[f], c->st));
                 CUDA_TRY(c, cudaStreamWaitEvent(c->st2, c->ev_fac[f], 0));
                 if ((s = side_hyper(f, it + 1))) return s;
             }
         }
+        // tail of the sweep on its own stream, overlapping the next sweep's Gram pass: the
+        // test RMSE of this sample, then the draws of sweep t + 2 into this sweep's buffer
+        // (every reader of that buffer is ordered before this point)
+        const bool tail_gen = gen && it + 2 < n_sweeps;
+        if (tt1 > tt0 || tail_gen) {
+            CUDA_TRY(c, cudaEventRecord(c->ev_tail, c->st));
+            CUDA_TRY(c, cudaStreamWaitEvent(c->st4, c->ev_tail, 0));
+        }
         if (tt1 > tt0) {
             RmseParams rp{K, c->prec, tt0, tt1, c->trow, c->tcol, c->tval, c->X.G, c->W.G, c->ldg,
-                          keep ? 1 : 0, c->ysum, (double)kept, c->rmse_part};
-            traced(c, c->st, K_RMSE, 2, [&] {
-                launch_rmse(rp, c->rmse_blocks, c->st);
-                launch_rmse_final(c->rmse_part, c->rmse_blocks, c->rmse_out, c->st);
+                          keep ? 1 : 0, c->ysum, kept > 0 ? 1.0 / (double)kept : 0.0,
+                          c->rmse_part};
+            traced(c, c->st4, K_RMSE, 2, [&] {
+                launch_rmse(rp, c->rmse_blocks, c->st4);
+                launch_rmse_final(c->rmse_part, c->rmse_blocks, c->rmse_out, c->st4);
             });
+            CUDA_TRY(c, cudaEventRecord(c->ev_rmse, c->st4));
         }
-        if (gen && it + 2 < n_sweeps)
-            enqueue_gen(c, gen_units, gen_segs, t + 2, c->gen_d + (int64_t)(it & 1) * per);
+        if (tail_gen) {
+            GenParams gp{c->gen_segs_d, gen_segs, gen_units, c->seed, t + 2,
+                         c->gen_d + (int64_t)(it & 1) * per, c->err_d};
+            traced(c, c->st4, K_GEN, 1, [&] { launch_gen(gp, c->st4); });
+            CUDA_TRY(c, cudaEventRecord(c->ev_gen[it & 1], c->st4));
+        }
+    }
+    // the context stream is complete when the call returns
+    if (n_sweeps > 0) {
+        CUDA_TRY(c, cudaEventRecord(c->ev_tail, c->st4));
+        CUDA_TRY(c, cudaStreamWaitEvent(c->st, c->ev_tail, 0));
     }
     CUDA_TRY(c, cudaGetLastError());
     for (int sl = sl0; sl < sl1; ++sl) {
@@ -998,8 +1128,13 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
         int lo = 0, hi = 0;
         cudaDeviceGetStreamPriorityRange(&lo, &hi);
         bool ok = cudaStreamCreateWithPriority(&c->st2, cudaStreamNonBlocking, hi) == cudaSuccess;
-        for (cudaEvent_t *e : {&c->ev_fork, &c->ev_fac[0], &c->ev_fac[1], &c->ev_hyp[0], &c->ev_hyp[1]})
+        ok = ok && cudaStreamCreateWithPriority(&c->st3, cudaStreamNonBlocking, hi) == cudaSuccess;
+        ok = ok && cudaStreamCreateWithPriority(&c->st4, cudaStreamNonBlocking, hi) == cudaSuccess;
+        for (cudaEvent_t *e : {&c->ev_fork, &c->ev_fac[0], &c->ev_fac[1], &c->ev_hyp[0], &c->ev_hyp[1],
+                               &c->ev_cdone, &c->ev_tail, &c->ev_rmse, &c->ev_gen[0], &c->ev_gen[1]})
             ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+        for (cudaEvent_t &e : c->ev_chunk)
+            ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
         if (!ok) return bail(BMF_E_CUDA, "stream/event creation failed");
     }
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -1122,6 +1257,26 @@ int64_t bmf_draws_per_sweep(const bmf_ctx *c, int32_t stage, int32_t subset)
     int sl0, sl1;
     if (!stage_slots(c, stage, sl0, sl1)) return -1;
     return per_sweep_draws(c, sl0, sl1);
+}
+
+bmf_status bmf_set_schedule(bmf_ctx *c, const bmf_schedule *s)
+{
+    if (!c || !s) return BMF_E_ARG;
+    if (s->chunks_x < 1 || s->chunks_x > kMaxChunks || s->chunks_w < 1 || s->chunks_w > kMaxChunks)
+        return fail(c, BMF_E_ARG, "chunks must be in 1.." + std::to_string(kMaxChunks));
+    if (s->gram_blocks_per_sm < 1 || s->gram_blocks_per_sm > 64)
+        return fail(c, BMF_E_ARG, "gram_blocks_per_sm must be in 1..64");
+    if (!(s->row_weight >= 0.0) || !std::isfinite(s->row_weight))
+        return fail(c, BMF_E_ARG, "row_weight must be finite and >= 0");
+    c->sched = *s;
+    return BMF_OK;
+}
+
+bmf_status bmf_get_schedule(const bmf_ctx *c, bmf_schedule *s)
+{
+    if (!c || !s) return BMF_E_ARG;
+    *s = c->sched;
+    return BMF_OK;
 }
 
 bmf_status bmf_generate_draws(bmf_ctx *c, int32_t stage, int32_t subset, int64_t t0,

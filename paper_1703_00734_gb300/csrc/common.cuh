@@ -55,4 +55,18 @@ struct DevError {
 // Laid out contiguously per slot: [mu (K)][Lambda (ntri)][b (K)].
 __host__ __device__ constexpr int hyper_slot_len(int K) { return K + ntri(K) + K; }
 
+// FP32 -> FP64 by rebuilding the IEEE-754 fields on the integer pipe (exact for every normal
+// float; zeros, subnormals, infinities and NaNs take the hardware conversion).  On this GPU the
+// conversion instruction occupies the FP64 pipe, which this kernel is bound by.
+__device__ __forceinline__ double widen(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const uint32_t hi = (u & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((u & 0x7fffffu) >> 3);
+    const uint32_t lo = u << 29;
+    return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
 }  // namespace bmf

@@ -30,19 +30,6 @@ __device__ __forceinline__ __nv_bfloat16 to_gather<__nv_bfloat16>(double x)
     return __double2bfloat16(x);
 }
 
-// FP32 -> FP64 by rebuilding the IEEE-754 fields on the integer pipe (exact for every normal
-// float; zeros, subnormals, infinities and NaNs take the hardware conversion).  On this GPU the
-// conversion instruction occupies the FP64 pipe, which this kernel is bound by.
-__device__ __forceinline__ double widen(float f)
-{
-    const uint32_t u = __float_as_uint(f);
-    const uint32_t e = (u >> 23) & 0xffu;
-    if (e == 0u || e == 0xffu) return (double)f;
-    const uint32_t hi = (u & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((u & 0x7fffffu) >> 3);
-    const uint32_t lo = u << 29;
-    return __hiloint2double((int)hi, (int)lo);
-}
-__device__ __forceinline__ double widen(double d) { return d; }
 
 // Shared-memory slots per thread: the packed matrix (ntri(K)), the right-hand side / solution
 // (K) and the reciprocal pivots (K).

@@ -127,7 +127,7 @@ struct RmseParams {
     int ldg;
     int keep;
     double *ysum;            // running sum of predictions over kept samples
-    double kept_after;       // number of kept samples after this sweep (for the mean)
+    double inv_kept;         // 1 / (kept samples after this sweep), 0 when none (no mean)
     double *partial;         // [blocks x 2]
 };
 void launch_rmse(const RmseParams &a, int blocks, cudaStream_t st);

@@ -351,21 +351,25 @@ template <typename GT>
 __global__ void __launch_bounds__(256) rmse_kernel(RmseParams a)
 {
     const GT *Xg = static_cast<const GT *>(a.Xg), *Wg = static_cast<const GT *>(a.Wg);
+    // the dot product in the gather precision, widened on the integer pipe; five FP64
+    // operations per entry (this pass shares the FP64 pipe with the conditional draws)
     double s0 = 0.0, s1 = 0.0;
+    const bool mean = a.inv_kept > 0.0;
     for (int64_t e = a.t0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.t1;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const double yh = (double)dot_rows(Xg + (int64_t)a.trow[e] * a.ldg,
-                                           Wg + (int64_t)a.tcol[e] * a.ldg, a.ldg);
-        const double d0 = a.tval[e] - yh;
-        s0 += d0 * d0;
-        double ys = a.ysum[e];
+        const double yh = widen(dot_rows(Xg + (int64_t)a.trow[e] * a.ldg,
+                                         Wg + (int64_t)a.tcol[e] * a.ldg, a.ldg));
+        const double y = a.tval[e];
+        const double d0 = y - yh;
+        s0 = fma(d0, d0, s0);
         if (a.keep) {
-            ys += yh;
+            const double ys = a.ysum[e] + yh;
             a.ysum[e] = ys;
-        }
-        if (a.kept_after > 0) {
-            const double d1 = a.tval[e] - ys / a.kept_after;
-            s1 += d1 * d1;
+            const double d1 = fma(-ys, a.inv_kept, y);
+            s1 = fma(d1, d1, s1);
+        } else if (mean) {
+            const double d1 = fma(-a.ysum[e], a.inv_kept, y);
+            s1 = fma(d1, d1, s1);
         }
     }
     __shared__ double red[2][256];

@@ -1,0 +1,65 @@
+"""The launch schedule (bmf_set_schedule: row chunks per sweep half, Gram grid) changes only
+how the work is launched: the sampled states must be bit-identical under every schedule, and
+the chunked path must keep FP64 parity with the oracle."""
+import numpy as np
+import pytest
+
+from paper_1703_00734_gb300 import synth
+from pairing import Pair
+
+pytestmark = pytest.mark.gpu
+
+SCHEDULES = [(1, 1, 4, 0.0), (2, 3, 2, 0.0), (8, 8, 1, 0.0), (4, 2, 4, 500.0)]
+
+
+def run(d, K, prec, sched, I=1, J=1, sweeps=3):
+    from paper_1703_00734_gb300 import bmf
+    m = bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], K, d["tau"], prec, I=I, J=J,
+                X0=d["X0"], W0=d["W0"], seed=3, burnin=1,
+                test=(d["test_row"], d["test_col"], d["test_val"]))
+    m.set_schedule(*sched)
+    assert m.get_schedule()["chunks_x"] == sched[0]
+    out = []
+    stages = (1,) if I * J == 1 else (1, 2, 3)
+    for stage in stages:
+        st = m.stage(stage, sweeps, None)
+        out.append(st["rmse_sample"])
+        for sid in range(I * J):
+            if m.subset_info(sid)["stage"] == stage:
+                X, W, h = m.get_state(sid)
+                out += [X, W, h["LamX"], h["LamW"]]
+    m.close()
+    return out
+
+
+@pytest.mark.parametrize("K,prec,I,J", [(5, "fp32", 1, 1), (10, "fp64", 1, 1), (16, "bf16", 1, 1),
+                                        (24, "fp32", 1, 1), (4, "fp32", 2, 3)])
+def test_states_identical_under_every_schedule(K, prec, I, J):
+    d = synth.make_workload(None, N=900, D=500, M=40_000, pattern="zipf", K=K, sigma=0.5,
+                            tau=4.0, seed=60 + K, s_row=1.2, s_col=1.2)
+    ref = run(d, K, prec, SCHEDULES[0], I, J, sweeps=K + 2 if I * J > 1 else 3)
+    for sc in SCHEDULES[1:]:
+        got = run(d, K, prec, sc, I, J, sweeps=K + 2 if I * J > 1 else 3)
+        for a, b in zip(ref, got):
+            assert np.array_equal(a, b, equal_nan=True), sc
+
+
+def test_chunked_schedule_fp64_parity():
+    d = synth.make_workload(None, N=700, D=300, M=30_000, pattern="zipf", K=6, sigma=0.5,
+                            tau=4.0, seed=71, s_row=1.2, s_col=1.2)
+    pr = Pair(d, 6)
+    pr.m.set_schedule(4, 3, 2)
+    pr.run_stage(1, 2)
+    pr.compare_subset(0, rel=1e-8)
+
+
+def test_schedule_argument_errors():
+    from paper_1703_00734_gb300 import bmf
+    d = synth.make_workload(None, N=40, D=30, M=300, pattern="uniform", K=2, sigma=0.5,
+                            tau=4.0, seed=1)
+    m = bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], 2, d["tau"])
+    for bad in [(0, 1, 4, 0.0), (1, 9, 4, 0.0), (1, 1, 0, 0.0), (1, 1, 4, -1.0)]:
+        with pytest.raises(bmf.BmfError) as e:
+            m.set_schedule(*bad)
+        assert e.value.status == 1
+    m.close()
