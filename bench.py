@@ -8,8 +8,14 @@ The headline `value` is sweeps/s of the reduced-precision path (FP32 gathers and
 Cholesky/Wishart), inputs resident in HBM; the plain FP64 GPU sweep and the test RMSE of both
 are reported beside it.  `--impl reference` times the FP64 CPU oracle instead.
 
+Other workloads (--workload): a workload with an I x J grid (pp4x4-100000x20000-20M-k16) runs
+the three batched posterior-propagation stages, aggregation and prediction against the plain
+FP64 and reduced-precision samplers at the same sweep count; uniform-200000x50000-50M-k64 times
+the log-joint adjoint, Langevin moves and Gibbs sweeps at K = 64; any other named workload runs
+the plain-sweep benchmark above on it.
+
 Prints ONE JSON line (rank 0).  For --gpus N > 1 (torchrun) every rank runs an independent
-replica of the workload (the plain sweep does not shard) and value sums them.
+replica of the workload (one chain does not shard across GPUs) and value sums them.
 """
 from __future__ import annotations
 
@@ -249,7 +255,7 @@ def run_ours(args, rank, world, local_rank):
               key=lambda k: kernels[k]["avg_us"] * kernels[k]["launches"])
     kd = kernels[dom]
     roof = {"kernel": dom, "bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
-            "unit": kd["unit"], "frac": kd["frac"], "traffic": traffic_for(dom, args.precision),
+            "unit": kd["unit"], "frac": kd["frac"], "traffic": traffic_for(dom, args.precision, args.workload),
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if kd["unit"] == "GB/s"
             else "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"}
     out = {
@@ -382,15 +388,119 @@ def run_pp(args, rank, world, local_rank):
     }
 
 
-def traffic_for(kernel, prec):
-    """DRAM bytes per launch from the committed ncu summary, if one matches."""
+# ---------------------------------------------------------------------------------------
+# the adjoint of the masked log-joint, Langevin moves and Gibbs sweeps at K = 64
+# ---------------------------------------------------------------------------------------
+def run_adjoint(args, rank, world, local_rank):
+    import torch
+    from paper_1703_00734_gb300 import bmf
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    d = load_workload(args.workload, args.scale)
+    K, tau = d["K"], d["tau"]
+    N, D, M = d["N"], d["D"], len(d["row"])
+    S, Wm = args.steps, args.warmup
+    m = bmf.BMF(N, D, d["row"], d["col"], d["val"], K, tau, "fp32", X0=d["X0"], W0=d["W0"],
+                test=(d["test_row"], d["test_col"], d["test_val"]), burnin=1, seed=rank,
+                stream=stream.cuda_stream)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    # Gibbs sweeps (device generator for the draws)
+    m.sweep(0, Wm, None)
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    with ClockSampler(local_rank) as clk:
+        a.record(stream)
+        st = m.sweep(0, S, None)
+        b.record(stream)
+        b.synchronize()
+        gibbs_ms = a.elapsed_time(b) / S
+        # the adjoint at the current sample
+        X, W, hyp = m.get_state(0)
+        ld = (K + 3) // 4 * 4
+        dX = torch.zeros((N, ld), dtype=torch.float32, device=dev)
+        dW = torch.zeros((D, ld), dtype=torch.float32, device=dev)
+        dX[:, :K] = torch.from_numpy(X.astype(np.float32)).to(dev)
+        dW[:, :K] = torch.from_numpy(W.astype(np.float32)).to(dev)
+        gX, gW = torch.empty_like(dX), torch.empty_like(dW)
+        la = float(np.log(tau))
+        for _ in range(Wm):
+            m.logjoint_grad(0, dX.data_ptr(), dW.data_ptr(), ld, la, gX.data_ptr(), gW.data_ptr())
+        torch.cuda.synchronize()
+        n0 = m.launch_count()
+        a.record(stream)
+        for _ in range(S):
+            m.logjoint_grad(0, dX.data_ptr(), dW.data_ptr(), ld, la, gX.data_ptr(), gW.data_ptr())
+        b.record(stream)
+        b.synchronize()
+        grad_ms = a.elapsed_time(b) / S
+        launches = m.launch_count() - n0
+        m.profile(True)
+        m.logjoint_grad(0, dX.data_ptr(), dW.data_ptr(), ld, la, gX.data_ptr(), gW.data_ptr())
+        prof = m.profile_read()
+        m.profile(False)
+        # Langevin moves: unadjusted, then Metropolis-adjusted, eps small enough to accept
+        L = min(S, 10)
+        rng = np.random.default_rng(100 + rank)
+        xi = torch.from_numpy(rng.standard_normal(L * (N + D) * K).astype(np.float32)).to(dev)
+        eps = 1e-6
+        torch.cuda.synchronize()
+        a.record(stream)
+        m.langevin(0, L, dX.data_ptr(), dW.data_ptr(), ld, la, eps, xi.data_ptr())
+        b.record(stream)
+        b.synchronize()
+        ula_ms = a.elapsed_time(b) / L
+        a.record(stream)
+        eps_mh = 1e-11     # Metropolis-adjusted moves in (N + D) K dimensions need tiny steps
+        acc, _ = m.langevin(0, L, dX.data_ptr(), dW.data_ptr(), ld, la, eps_mh, xi.data_ptr(),
+                            uniforms=rng.random(L))
+        b.record(stream)
+        b.synchronize()
+        mala_ms = a.elapsed_time(b) / L
+    m.close()
+    if rank != 0:
+        return None
+    # algorithmic bytes of one gradient evaluation: each of the two passes reads every
+    # observation's index, value and FP32 partner row (8 + 4K bytes per observation and side)
+    per_obs_side = 4 + 4 + 4 * K
+    algo = 2 * M * per_obs_side
+    items = {k: (n, t) for k, (n, t) in prof.items() if n}
+    adj_ms = items.get("adjoint", (1, grad_ms))[1] / max(items.get("adjoint", (1, 0))[0], 1)
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    ach = algo / (grad_ms / 1e3) / 1e9
+    return {
+        "metric": "log-joint gradient evaluations/s (adjoint, K=64)", "impl": "ours",
+        "value": 1e3 / grad_ms, "unit": "grad evals/s", "n_gpus": world, "steps": S,
+        "warmup": Wm, "ms_per_step": grad_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "N": N, "D": D, "train_obs": M, "K": K,
+                   "l2": "inputs larger than L2"},
+        "gibbs": {"sweeps_per_s": 1e3 / gibbs_ms, "ms_per_sweep": gibbs_ms,
+                  "rmse_mean": st["rmse_mean"], "precision": "fp32 (split TF32 Gram)"},
+        "langevin": {"ula_steps_per_s": 1e3 / ula_ms, "mala_steps_per_s": 1e3 / mala_ms,
+                     "mala_accepted": acc, "mala_steps": L, "eps_ula": eps, "eps_mala": eps_mh},
+        "roofline": {"kernel": "adjoint (both passes, whole evaluation)", "bound": "hbm",
+                     "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                     "traffic": None, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+        "adjoint_launch_ms": adj_ms, "gpu_launches": launches, "clocks": clk.summary(),
+    }
+
+
+MODES = {"uniform-200000x50000-50M-k64": "adjoint"}
+
+
+def traffic_for(kernel, prec, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary, if one
+    matches (null otherwise)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     for line in open(path):
         f = line.split()
         if len(f) >= 4 and not line.startswith("#") and f[0] == kernel and f[1] == prec \
-                and f[2] == WORKLOAD:
+                and f[2] == workload:
             return float(f[3])
     return None
 
@@ -476,6 +586,8 @@ def main():
         out = run_reference(args, rank)
     elif pp:
         out = run_pp(args, rank, world, local_rank)
+    elif MODES.get(args.workload) == "adjoint":
+        out = run_adjoint(args, rank, world, local_rank)
     else:
         if world > 1:
             import torch

@@ -198,6 +198,15 @@ typedef struct {
 bmf_status bmf_set_schedule(bmf_ctx *ctx, const bmf_schedule *sched);
 bmf_status bmf_get_schedule(const bmf_ctx *ctx, bmf_schedule *sched);
 
+/* Schedule tuner: times candidate schedules (Gram grid 2/4/8 blocks per SM, then 1-4 row chunks
+ * for each half, then the split weight) on the batch of `stage` (subset < 0) or of one subset,
+ * one untimed and sweeps_per_trial timed sweeps each with the device generator, and installs the
+ * fastest.  Every trial starts from the same state and the chains are restored afterwards (state,
+ * gathered copies, moment sums, hyperparameters, running test predictions, sweep counters), so
+ * the call changes no sampled value.  The batch's stage must be open.  best: host, nullable. */
+bmf_status bmf_autotune(bmf_ctx *ctx, int32_t stage, int32_t subset, int32_t sweeps_per_trial,
+                        bmf_schedule *best);
+
 /* n_sweeps Gibbs sweeps of one subset's chain (the whole data for a 1 x 1 grid).  The subset's
  * stage must be open (see bmf_stage).  draws: NULL for the device generator, else the buffer
  * for n_sweeps sweeps of this single-subset batch.  stats may be NULL. */

@@ -120,6 +120,8 @@ def load(path: str = LIB_PATH):
     L.bmf_set_schedule.restype = st
     L.bmf_get_schedule.argtypes = [P, ctypes.POINTER(Schedule)]
     L.bmf_get_schedule.restype = st
+    L.bmf_autotune.argtypes = [P, i32, i32, i32, ctypes.POINTER(Schedule)]
+    L.bmf_autotune.restype = st
     L.bmf_generate_draws.argtypes = [P, i32, i32, i64, i32, P, i32]
     L.bmf_generate_draws.restype = st
     L.bmf_destroy.argtypes = [P]
@@ -225,6 +227,15 @@ class BMF:
     def get_schedule(self):
         sc = Schedule()
         self._check(self.L.bmf_get_schedule(self.h, ctypes.byref(sc)))
+        return dict(chunks_x=sc.chunks_x, chunks_w=sc.chunks_w,
+                    gram_blocks_per_sm=sc.gram_blocks_per_sm, row_weight=sc.row_weight)
+
+    def autotune(self, stage=1, subset=-1, sweeps_per_trial=3):
+        """Time candidate launch schedules on a batch and install the fastest (the chains are
+        restored; no sampled value changes).  Returns the chosen schedule."""
+        sc = Schedule()
+        self._check(self.L.bmf_autotune(self.h, stage, subset, int(sweeps_per_trial),
+                                        ctypes.byref(sc)))
         return dict(chunks_x=sc.chunks_x, chunks_w=sc.chunks_w,
                     gram_blocks_per_sm=sc.gram_blocks_per_sm, row_weight=sc.row_weight)
 

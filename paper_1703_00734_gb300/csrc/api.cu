@@ -123,6 +123,8 @@ struct bmf_ctx {
     double *stats = nullptr;
     int64_t stats_cap = 0;           // chunks
     HyperJob *d_jobs = nullptr;
+    HyperJob *d_jobs2 = nullptr;     // the same jobs over the first-level partials
+    double *stats2 = nullptr;        // [2 S x kStatParts x (K + ntri(K))] first-level partials
     double *mu0_d = nullptr, *W0inv_d = nullptr;
     int32_t *trow = nullptr, *tcol = nullptr;
     double *tval = nullptr, *ysum = nullptr;
@@ -166,7 +168,8 @@ namespace {
 
 constexpr int kHyperJobsMax = 1 << 16;
 constexpr int kSweepMaxK = 64;
-constexpr int kNarrowMaxK = 16;   // thread-per-row kernels up to here, warp-per-row beyond
+constexpr int kNarrowMaxK = 16;   // CUDA-core Gram pass up to here, tensor cores beyond
+constexpr int kTeamMinK = 13;     // conditional: one thread per row below, a team per row from here
 
 enum { K_STATS = 0, K_HYPER, K_GRAM_X, K_COND_X, K_GRAM_W, K_COND_W, K_RMSE, K_ADJ, K_GEN, K_NCLASS };
 const char *kClassName[K_NCLASS] = {"stats", "hyper", "gram_x", "cond_x", "gram_w", "cond_w", "rmse", "adjoint", "gen"};
@@ -644,6 +647,15 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
     if (!jobs.empty())
         CUDA_TRY(c, cudaMemcpyAsync(c->d_jobs, jobs.data(), jobs.size() * sizeof(HyperJob),
                                     cudaMemcpyHostToDevice, c->st));
+    if (!jobs.empty()) {
+        std::vector<HyperJob> jobs2(jobs);
+        for (size_t q = 0; q < jobs2.size(); ++q) {
+            jobs2[q].chunk0 = (int32_t)(q * kStatParts);
+            jobs2[q].chunk1 = (int32_t)((q + 1) * kStatParts);
+        }
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_jobs2, jobs2.data(), jobs2.size() * sizeof(HyperJob),
+                                    cudaMemcpyHostToDevice, c->st));
+    }
     const int64_t hyper_len = 2 * (int64_t)(sl1 - sl0) * HB;
     const int64_t zx_len = (rx1 - rx0) * K;
     int64_t kept = c->ss[g0.sid].kept;
@@ -653,10 +665,13 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
     auto side_hyper = [&](int f, int it) -> bmf_status {
         const double *d = draws_of(it);
         if (gen && it >= 2) CUDA_TRY(c, cudaStreamWaitEvent(c->st2, c->ev_gen[it & 1], 0));
-        const HyperJob *jb = c->d_jobs + (f == 0 ? 0 : nj[0]);
-        HyperParams hp{K, jb, nj[f], c->stats, c->mu0_d, c->beta0, c->nu0, c->W0inv_d, d,
-                       c->hyper, c->err_d};
-        traced(c, c->st2, K_HYPER, 1, [&] { launch_hyper(hp, c->st2); });
+        const int j0 = f == 0 ? 0 : nj[0];
+        HyperParams hp{K, c->d_jobs2 + j0, nj[f], c->stats2, c->mu0_d, c->beta0, c->nu0,
+                       c->W0inv_d, d, c->hyper, c->err_d};
+        traced(c, c->st2, K_HYPER, 2, [&] {
+            launch_stats_reduce(K, c->d_jobs + j0, nj[f], j0, c->stats, c->stats2, c->st2);
+            launch_hyper(hp, c->st2);
+        });
         CUDA_TRY(c, cudaEventRecord(c->ev_hyp[f], c->st2));
         return BMF_OK;
     };
@@ -784,14 +799,16 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
             cp.S2 = me.S2;
             cp.stats = c->stats;
             cp.err = c->err_d;
+            // lanes per row of the conditional: one thread per row below K = 13, a team above
+            const int team = K >= kTeamMinK ? cond_team_size(K) : 1;
             auto cond_chunk = [&](int64_t ba, int64_t bb, cudaStream_t sx) {
                 if (bb <= ba) return;
                 CondParams q = cp;
                 q.blocks = me.blocks + ba;
                 q.blk0 = me.stat0 + ba;
                 traced(c, sx, f == 0 ? K_COND_X : K_COND_W, 1, [&] {
-                    if (K > kNarrowMaxK)
-                        launch_cond_wide(c->prec, q, (int)(bb - ba), sx);
+                    if (team > 1)
+                        launch_cond_team(c->prec, q, (int)(bb - ba), team, sx);
                     else
                         launch_cond(c->prec, q, (int)(bb - ba), sx);
                 });
@@ -1176,6 +1193,8 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
     c->stats_cap = (int64_t)(c->X.h_blocks.size() + c->W.h_blocks.size());
     c->stats = c->mem.alloc<double>(c->stats_cap * (K + ntri(K)));
     c->d_jobs = c->mem.alloc<HyperJob>(kHyperJobsMax);
+    c->d_jobs2 = c->mem.alloc<HyperJob>(kHyperJobsMax);
+    c->stats2 = c->mem.alloc<double>((size_t)2 * S * kStatParts * (K + ntri(K)));
     for (int f = 0; f < 2; ++f) {
         Side &sd = f == 0 ? c->X : c->W;
         std::vector<StatChunk> ch(sd.h_blocks.size());
@@ -1276,6 +1295,148 @@ bmf_status bmf_get_schedule(const bmf_ctx *c, bmf_schedule *s)
 {
     if (!c || !s) return BMF_E_ARG;
     *s = c->sched;
+    return BMF_OK;
+}
+
+// Everything a batch of sweeps changes, for the schedule tuner: FP64 state, gathered copies,
+// moment sums (SoA) of the batch's rows, its hyperparameter slots, the running test predictions
+// and the per-subset counters.
+struct BatchSnapshot {
+    DevMem mem;
+    struct Part {
+        void *dst;
+        const void *src;
+        size_t width, height, spitch;
+    };
+    std::vector<Part> parts;
+    std::vector<SubState> ss;
+    bool ok = true;
+    void add(bmf_ctx *c, void *live, size_t width, size_t height = 1, size_t pitch = 0)
+    {
+        if (!width || !height) return;
+        char *b = mem.alloc<char>(width * height);
+        if (!b) {
+            ok = false;
+            return;
+        }
+        parts.push_back(Part{b, live, width, height, pitch ? pitch : width});
+    }
+    bmf_status take(bmf_ctx *c)
+    {
+        for (const Part &q : parts)
+            CUDA_TRY(c, cudaMemcpy2DAsync(q.dst, q.width, q.src, q.spitch, q.width, q.height,
+                                          cudaMemcpyDeviceToDevice, c->st));
+        return BMF_OK;
+    }
+    bmf_status restore(bmf_ctx *c)
+    {
+        for (const Part &q : parts)
+            CUDA_TRY(c, cudaMemcpy2DAsync(const_cast<void *>(q.src), q.spitch, q.dst, q.width,
+                                          q.width, q.height, cudaMemcpyDeviceToDevice, c->st));
+        CUDA_TRY(c, cudaStreamSynchronize(c->st));
+        return BMF_OK;
+    }
+};
+
+bmf_status bmf_autotune(bmf_ctx *c, int32_t stage, int32_t subset, int32_t sweeps_per_trial,
+                        bmf_schedule *best_out)
+{
+    if (!c) return BMF_E_ARG;
+    if (sweeps_per_trial < 1) return fail(c, BMF_E_ARG, "sweeps_per_trial must be >= 1");
+    int sl0, sl1;
+    if (subset >= 0) {
+        if (!valid_subset(c, subset)) return fail(c, BMF_E_ARG, "subset out of range");
+        sl0 = c->P.subs[subset].slot;
+        sl1 = sl0 + 1;
+    } else if (!stage_slots(c, stage, sl0, sl1)) {
+        return fail(c, BMF_E_ARG, "stage has no subsets");
+    }
+    if (geom_of_slot(c, sl0).stage != c->stage_open)
+        return fail(c, BMF_E_STATE, "the batch's stage is not the open stage");
+    const int K = c->K;
+    const size_t gb = c->prec == BMF_FP64 ? 8 : (c->prec == BMF_FP32 ? 4 : 2);
+    const SubsetGeom &g0 = geom_of_slot(c, sl0), &gl = geom_of_slot(c, sl1 - 1);
+    BatchSnapshot snap;
+    for (int f = 0; f < 2; ++f) {
+        Side &sd = f == 0 ? c->X : c->W;
+        const int64_t r0 = f == 0 ? g0.xoff : g0.woff;
+        const int64_t r1 = f == 0 ? gl.xoff + gl.n() : gl.woff + gl.d();
+        const size_t n = (size_t)(r1 - r0);
+        snap.add(c, sd.F + r0 * K, n * K * sizeof(double));
+        snap.add(c, static_cast<char *>(sd.G) + r0 * c->ldg * gb, n * c->ldg * gb);
+        snap.add(c, sd.S1 + r0, n * sizeof(double), K, sd.R * sizeof(double));
+        snap.add(c, sd.S2 + r0, n * sizeof(double), ntri(K), sd.R * sizeof(double));
+    }
+    snap.add(c, c->hyper + (int64_t)2 * sl0 * hyper_slot_len(K),
+             (size_t)2 * (sl1 - sl0) * hyper_slot_len(K) * sizeof(double));
+    const int64_t tt0 = g0.test_off, tt1 = gl.test_off + gl.n_test;
+    snap.add(c, c->ysum + tt0, (size_t)(tt1 - tt0) * sizeof(double));
+    if (!snap.ok || !snap.mem.ok) return fail(c, BMF_E_OOM, "device allocation failed (tuner)");
+    bmf_status s = snap.take(c);
+    if (s) return s;
+    snap.ss = c->ss;
+    const bmf_schedule keep = c->sched;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto trial = [&](const bmf_schedule &sc, float *ms) -> bmf_status {
+        c->sched = sc;
+        bmf_status st = run_batch(c, sl0, sl1, 1, nullptr, nullptr);
+        if (!st) {
+            cudaEventRecord(e0, c->st);
+            st = run_batch(c, sl0, sl1, sweeps_per_trial, nullptr, nullptr);
+            cudaEventRecord(e1, c->st);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(ms, e0, e1);
+        }
+        c->ss = snap.ss;
+        bmf_status rs = snap.restore(c);
+        return st ? st : rs;
+    };
+    bmf_schedule best = keep;
+    float best_ms = 0.f;
+    std::vector<bmf_schedule> cands;
+    // coordinate search: Gram grid, then row chunks of each half, then the split weight
+    auto run_all = [&](const std::vector<bmf_schedule> &cs) -> bmf_status {
+        for (const bmf_schedule &sc : cs) {
+            float ms = 0.f;
+            bmf_status st = trial(sc, &ms);
+            if (st) return st;
+            if (best_ms == 0.f || ms < best_ms) {
+                best_ms = ms;
+                best = sc;
+            }
+        }
+        return BMF_OK;
+    };
+    bmf_schedule b0{1, 1, 4, 0.0};
+    cands = {b0};
+    for (int g : {2, 8}) cands.push_back(bmf_schedule{1, 1, g, 0.0});
+    s = run_all(cands);
+    for (int f = 0; f < 2 && !s; ++f) {
+        cands.clear();
+        for (int ch : {2, 3, 4}) {
+            bmf_schedule sc = best;
+            (f == 0 ? sc.chunks_x : sc.chunks_w) = ch;
+            cands.push_back(sc);
+        }
+        s = run_all(cands);
+    }
+    if (!s && (best.chunks_x > 1 || best.chunks_w > 1)) {
+        const double w0 = (c->prec == BMF_FP64 ? 1.5 : 14.0) * K;
+        cands.clear();
+        for (double m : {0.3, 3.0}) {
+            bmf_schedule sc = best;
+            sc.row_weight = w0 * m;
+            cands.push_back(sc);
+        }
+        s = run_all(cands);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->sched = s ? keep : best;
+    if (s) return s;
+    if (best_out) *best_out = best;
     return BMF_OK;
 }
 

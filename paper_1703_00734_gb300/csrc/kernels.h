@@ -116,6 +116,10 @@ struct HyperParams {
     DevError *err;
 };
 void launch_hyper(const HyperParams &a, cudaStream_t st);
+// First level of the statistics sum: partials (j0 + j) * kStatParts + p of job j (see misc.cu).
+constexpr int kStatParts = 64;
+void launch_stats_reduce(int K, const HyperJob *jobs, int n_jobs, int j0, const double *stats,
+                         double *out, cudaStream_t st);
 
 // Test-set predictions of the current sample, running mean, squared errors.
 struct RmseParams {
@@ -186,7 +190,9 @@ void launch_predict(int K, int64_t n, const int32_t *row, const int32_t *col, co
 int wide_kt(int K);
 int wide_part_ld(int K);
 void launch_gram_wide(int K, int prec, const GramParams &a, int grid, cudaStream_t st);
-void launch_cond_wide(int prec, const CondParams &a, int n_blocks, cudaStream_t st);
+// Conditional draw with a team of `team` lanes (4, 8, 16 or 32) per row (wide.cu).
+void launch_cond_team(int prec, const CondParams &a, int n_blocks, int team, cudaStream_t st);
+int cond_team_size(int K);
 
 // Adjoint of the masked log-joint (adjoint.cu).
 int adjoint_kt(int K);          // template width (K rounded up to 4, 8, 12, 16, 32 or 64)

@@ -149,6 +149,41 @@ __device__ void block_spd_inverse_from_chol(const double *Lm, double *Out, doubl
 }
 
 // ------------------------------------------------------------------------------------------
+// First level of the statistics sum of the hyperparameter step: block (p, j) sums, entry by
+// entry in chunk order, the p-th of kStatParts equal runs of job j's chunks into partial
+// (j0 + j) * kStatParts + p (zero for an empty run).  The hyperparameter kernel then sums the
+// kStatParts partials of its job in order.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) stats_reduce_kernel(int K, const HyperJob *__restrict__ jobs,
+                                                           int j0, const double *__restrict__ stats,
+                                                           double *__restrict__ out)
+{
+    const int NS = K + ntri(K);
+    const HyperJob jb = jobs[blockIdx.y];
+    const int n = jb.chunk1 - jb.chunk0;
+    const int len = (n + kStatParts - 1) / kStatParts;
+    const int c0 = jb.chunk0 + min(n, (int)blockIdx.x * len), c1 = jb.chunk0 + min(n, ((int)blockIdx.x + 1) * len);
+    double *dst = out + ((int64_t)(j0 + blockIdx.y) * kStatParts + blockIdx.x) * NS;
+    for (int e = threadIdx.x; e < NS; e += blockDim.x) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        int c = c0;
+        for (; c + 3 < c1; c += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] += stats[(int64_t)(c + u) * NS + e];
+        }
+        for (; c < c1; ++c) acc[0] += stats[(int64_t)c * NS + e];
+        dst[e] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    }
+}
+
+void launch_stats_reduce(int K, const HyperJob *jobs, int n_jobs, int j0, const double *stats,
+                         double *out, cudaStream_t st)
+{
+    if (n_jobs <= 0) return;
+    stats_reduce_kernel<<<dim3(kStatParts, n_jobs), 256, 0, st>>>(K, jobs, j0, stats, out);
+}
+
+// ------------------------------------------------------------------------------------------
 // Normal-Wishart hyperparameter draw: one block per (subset, factor) job.
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) hyper_kernel(HyperParams a)

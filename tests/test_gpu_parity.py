@@ -123,3 +123,12 @@ def test_error_paths():
     with pytest.raises(bmf.BmfError) as e:
         m.stage(3, 1, np.zeros(m.draws_per_sweep(3)))
     assert e.value.status == 8
+
+
+@pytest.mark.parametrize("K", [3, 7, 12])
+def test_thread_per_row_conditional_on_large_halves(K):
+    """The thread-per-row conditional (K <= 12) on halves of thousands of rows: FP64 parity."""
+    d = small(N=9000, D=8300, M=120_000, K=K, seed=90 + K, pattern="zipf")
+    pr = Pair(d, K)
+    pr.run_stage(1, 1)
+    pr.compare_subset(0)

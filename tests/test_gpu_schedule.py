@@ -63,3 +63,33 @@ def test_schedule_argument_errors():
             m.set_schedule(*bad)
         assert e.value.status == 1
     m.close()
+
+
+@pytest.mark.parametrize("I,J,stage", [(1, 1, 1), (2, 3, 2)])
+def test_autotune_restores_the_chain(I, J, stage):
+    from paper_1703_00734_gb300 import bmf
+    d = synth.make_workload(None, N=800, D=400, M=30_000, pattern="zipf", K=6, sigma=0.5,
+                            tau=4.0, seed=81, s_row=1.2, s_col=1.2)
+    test = (d["test_row"], d["test_col"], d["test_val"])
+
+    def chain(tune):
+        m = bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], 6, d["tau"], "fp32", I=I, J=J,
+                    X0=d["X0"], W0=d["W0"], seed=4, burnin=1, test=test, moments="full")
+        for s in range(1, stage):
+            m.stage(s, 8, None)
+        m.stage(stage, 2, None)
+        sc = m.autotune(stage, -1, 2) if tune else None
+        st = m.stage(stage, 3, None)
+        out = [st["rmse_sample"], st["rmse_mean"], st["sweeps"], st["kept"]]
+        for sid in range(I * J):
+            if m.subset_info(sid)["stage"] == stage:
+                X, W, h = m.get_state(sid)
+                out += [X, W, h["LamX"], h["LamW"], *m.get_moments(sid, 0)[:2]]
+        m.close()
+        return out, sc
+
+    ref, _ = chain(False)
+    got, sc = chain(True)
+    assert 1 <= sc["chunks_x"] <= 8 and sc["gram_blocks_per_sm"] in (2, 4, 8)
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b, equal_nan=True)
