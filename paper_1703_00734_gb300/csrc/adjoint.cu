@@ -113,22 +113,23 @@ __global__ void __launch_bounds__(kAdjRows) adjoint_rows_kernel(AdjointParams a)
         float *g = a.grad + n * a.ld;
         const int h = a.row_hslot[row];
         const double *hp = h >= 0 ? a.hyper + (int64_t)h * hyper_slot_len(K) : nullptr;
+        float qrow = 0.f;
         for (int i = 0; i < K; ++i) {
             float s = 0.f;
             for (int64_t it = i0; it < i1; ++it) s += a.part[(it - a.item_base) * (int64_t)LD + i];
-            // prior term L (x - mu) = L x - b
-            double lx = 0.0;
+            // prior term L (x - mu) = L x - b, in FP32 like the data term
+            float lx = 0.f;
             for (int k = 0; k < K; ++k) {
                 const int e = i >= k ? tri(i, k) : tri(k, i);
-                const double l = hp ? hp[K + e] : a.prior_L[(int64_t)e * a.R + row];
-                lx = fma(l, (double)x[k], lx);
+                const float l = (float)(hp ? hp[K + e] : a.prior_L[(int64_t)e * a.R + row]);
+                lx = fmaf(l, x[k], lx);
             }
-            const double b = hp ? hp[K + ntri(K) + i] : a.prior_b[(int64_t)i * a.R + row];
-            const double pg = lx - b;
-            g[i] = (float)((double)a.alpha * (double)s - pg);
+            const float b = (float)(hp ? hp[K + ntri(K) + i] : a.prior_b[(int64_t)i * a.R + row]);
+            g[i] = (float)a.alpha * s - (lx - b);
             // (x - mu)^T L (x - mu) = x^T L x - 2 x^T b + mu^T b: the last term is constant
-            quad += (double)x[i] * (lx - 2.0 * b);
+            qrow = fmaf(x[i], lx - 2.f * b, qrow);
         }
+        quad = (double)qrow;
         for (int i = K; i < a.ld; ++i) g[i] = 0.f;
         if (a.count_r2)
             for (int64_t it = i0; it < i1; ++it) r2 += (double)a.part[(it - a.item_base) * (int64_t)LD + KT];

@@ -45,7 +45,10 @@ int gram_parts(int K, int prec)
 
 int gram_part_ld(int K, int prec) { return gram_parts(K, prec) * ep_for(padded_k(K), prec); }
 
-int gram_group(int64_t count) { return count <= 16 ? 8 : (count <= 48 ? 16 : 32); }
+// Lanes per row by its observation count: fewer lanes per row means more rows per warp and a
+// shorter reduce-scatter per row; measured on this GPU (69,878 x 10,677 Zipf workload, K = 10)
+// the X-side pass took 118 us with these thresholds against 140 us with (16, 48).
+int gram_group(int64_t count) { return count <= 64 ? 8 : (count <= 256 ? 16 : 32); }
 
 __device__ __forceinline__ float madd(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double madd(double a, double b, double c) { return fma(a, b, c); }

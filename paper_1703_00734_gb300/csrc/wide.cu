@@ -160,19 +160,31 @@ __global__ void __launch_bounds__(128) gram_wide_bf16(GramParams a)
         float acc[NTL][4];
 #pragma unroll
         for (int t = 0; t < NTL; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
-        for (int o0 = 0; o0 < m.count; o0 += kWideObs) {
-            // stage: lane o gathers observation o0 + o (zero row past the end)
-            const int o = lane;
-            __nv_bfloat16 *row = S + o * LDS;
-            if (o0 + o < m.count) {
-                const int64_t q = m.begin + o0 + o;
-                const int c = __ldg(a.idx + q);
-                const float y = __ldg(val + q);
-                const uint4 *src = reinterpret_cast<const uint4 *>(P + (int64_t)c * a.ldP);
+        // software pipeline: lane o holds in registers the row and value of observation
+        // o0 + 32 + o (gathered while the tensor cores work on step o0) and the index of
+        // observation o0 + 64 + o
+        uint4 nxt[KT / 8];
+        float ny = 0.f;
+        bool nvalid = lane < m.count;
+        int cnext = 0;
+        {
+            const int c0 = nvalid ? __ldg(a.idx + m.begin + lane) : 0;
+            if (nvalid) {
+                ny = __ldg(val + m.begin + lane);
+                const uint4 *src = reinterpret_cast<const uint4 *>(P + (int64_t)c0 * a.ldP);
 #pragma unroll
-                for (int v = 0; v < KT / 8; ++v) reinterpret_cast<uint4 *>(row)[v] = __ldg(src + v);
-                const __nv_bfloat16 hi = __float2bfloat16_rn(y);
-                const __nv_bfloat16 lo = __float2bfloat16_rn(y - __bfloat162float(hi));
+                for (int v = 0; v < KT / 8; ++v) nxt[v] = __ldg(src + v);
+            }
+            cnext = kWideObs + lane < m.count ? __ldg(a.idx + m.begin + kWideObs + lane) : 0;
+        }
+        for (int o0 = 0; o0 < m.count; o0 += kWideObs) {
+            // stage: lane o writes observation o0 + o (zero row past the end)
+            __nv_bfloat16 *row = S + lane * LDS;
+            if (nvalid) {
+#pragma unroll
+                for (int v = 0; v < KT / 8; ++v) reinterpret_cast<uint4 *>(row)[v] = nxt[v];
+                const __nv_bfloat16 hi = __float2bfloat16_rn(ny);
+                const __nv_bfloat16 lo = __float2bfloat16_rn(ny - __bfloat162float(hi));
                 uint4 tail = make_uint4(0u, 0u, 0u, 0u);
                 tail.x = (uint32_t)__bfloat16_as_ushort(hi) | ((uint32_t)__bfloat16_as_ushort(lo) << 16);
                 reinterpret_cast<uint4 *>(row)[KT / 8] = tail;
@@ -181,6 +193,17 @@ __global__ void __launch_bounds__(128) gram_wide_bf16(GramParams a)
                 for (int v = 0; v <= KT / 8; ++v) reinterpret_cast<uint4 *>(row)[v] = make_uint4(0u, 0u, 0u, 0u);
             }
             __syncwarp();
+            {
+                const int o1 = o0 + kWideObs + lane;
+                nvalid = o1 < m.count;
+                if (nvalid) {
+                    ny = __ldg(val + m.begin + o1);
+                    const uint4 *src = reinterpret_cast<const uint4 *>(P + (int64_t)cnext * a.ldP);
+#pragma unroll
+                    for (int v = 0; v < KT / 8; ++v) nxt[v] = __ldg(src + v);
+                }
+                cnext = o1 + kWideObs < m.count ? __ldg(a.idx + m.begin + o1 + kWideObs) : 0;
+            }
             // two k-steps of 16 observations
 #pragma unroll
             for (int ks = 0; ks < kWideObs / 16; ++ks) {
@@ -443,10 +466,17 @@ __device__ __forceinline__ void decode_packed(int e, int &i, int &j)
 
 int cond_team_size(int K) { return K <= 16 ? 4 : (K <= 32 ? 8 : (K <= 48 ? 16 : 32)); }
 
-// Doubles per team in shared memory: the packed matrix, right-hand side and pivots, padded so
-// that the teams of one half-warp start in different banks (stride = T mod 16 doubles past a
-// multiple of 16: the 16 / T teams of a half-warp cover the 32 banks once).
-__host__ __device__ constexpr int team_stride(int K, int T) { return (ntri(K) + 2 * K + 15) / 16 * 16 + T % 16; }
+// Doubles per team in shared memory: the packed matrix, right-hand side, pivots and (teams of 8
+// or more lanes) a contiguous copy of the current column, padded so that the teams of one
+// half-warp start in different banks (stride = T mod 16 doubles past a multiple of 16: the
+// 16 / T teams of a half-warp cover the 32 banks once).  The column copy removes the strided
+// reads of the trailing update; for 4-lane teams (K <= 16) the extra shared memory would cost
+// a resident block per SM, which measured slower.
+__host__ __device__ constexpr bool team_colcopy(int T) { return T >= 8; }
+__host__ __device__ constexpr int team_stride(int K, int T)
+{
+    return (ntri(K) + (team_colcopy(T) ? 3 : 2) * K + 15) / 16 * 16 + T % 16;
+}
 
 template <typename GT, typename AT, int T>
 __global__ void __launch_bounds__(32 * kWideWarps) cond_team_kernel(CondParams a)
@@ -457,7 +487,7 @@ __global__ void __launch_bounds__(32 * kWideWarps) cond_team_kernel(CondParams a
     const int tl = threadIdx.x % T, tm = threadIdx.x / T;
     const unsigned mask = T == 32 ? 0xffffffffu : (((1u << T) - 1u) << ((threadIdx.x & 31) & ~(T - 1)));
     const int per_team = team_stride(K, T);
-    double *M = smw + tm * per_team, *B = M + NT, *RI = B + K;
+    double *M = smw + tm * per_team, *B = M + NT, *RI = B + K, *CK = RI + K;
     double *XS = smw + NTEAM * per_team;     // [kCondBlock][K]: x of the block's rows
     const CondBlock blk = a.blocks[blockIdx.x];
     const int64_t R = a.R;
@@ -496,7 +526,12 @@ __global__ void __launch_bounds__(32 * kWideWarps) cond_team_kernel(CondParams a
             const double rs = ok ? rsqrt(d) : 0.0;
             __syncwarp(mask);
             if (ok) {
-                for (int i = k + 1 + tl; i < K; i += T) M[tri(i, k)] *= rs;
+                // the scaled column also goes to CK[i], contiguous, for the trailing update
+                for (int i = k + 1 + tl; i < K; i += T) {
+                    const double l = M[tri(i, k)] * rs;
+                    M[tri(i, k)] = l;
+                    if constexpr (team_colcopy(T)) CK[i] = l;
+                }
                 if (tl == 0) {
                     M[kk] = d * rs;
                     RI[k] = rs;
@@ -512,7 +547,10 @@ __global__ void __launch_bounds__(32 * kWideWarps) cond_team_kernel(CondParams a
                     ++i;
                 }
                 while (i < K) {
-                    M[tri(i, j)] = fma(-M[tri(i, k)], M[tri(j, k)], M[tri(i, j)]);
+                    if constexpr (team_colcopy(T))
+                        M[tri(i, j)] = fma(-CK[i], CK[j], M[tri(i, j)]);
+                    else
+                        M[tri(i, j)] = fma(-M[tri(i, k)], M[tri(j, k)], M[tri(i, j)]);
                     j += T;
                     while (i < K && j > i) {
                         j -= i - k;

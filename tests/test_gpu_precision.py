@@ -26,7 +26,8 @@ U_ACC = 2.0 ** -24
 
 
 def lanes_for(count):
-    return 8 if count <= 16 else (16 if count <= 48 else 32)
+    """Lanes per row of the K <= 16 Gram pass (8 up to 64 observations, 16 up to 256)."""
+    return 8 if count <= 64 else (16 if count <= 256 else 32)
 
 
 def seq_len(n, K):
