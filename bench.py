@@ -155,9 +155,13 @@ def run_ours(args, rank, world, local_rank):
     W, S = args.warmup, args.steps
 
     def context(prec):
-        return bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], K, tau, prec, X0=d["X0"],
-                       W0=d["W0"], test=test, burnin=args.burnin, seed=rank,
-                       stream=stream.cuda_stream)
+        m = bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], K, tau, prec, X0=d["X0"],
+                    W0=d["W0"], test=test, burnin=args.burnin, seed=rank, stream=stream.cuda_stream)
+        if not args.no_tune:
+            schedules[prec] = m.autotune(1, -1, 3)   # restores the chain: no value changes
+        return m
+
+    schedules = {}
 
     per = None
     # ---- headline: reduced-precision path, inputs resident ---------------------------
@@ -270,6 +274,7 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "inputs larger than L2 (observation lists 144 MB > 129 MB L2)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "obsK2_gflops": gflops,
+        "schedule": schedules,
         "rmse": {"reduced": rmse_red, "reduced_at_fp64_steps": rmse_same,
                  "fp64": fp64["rmse_mean"] if fp64 else None,
                  "abs_diff": abs(rmse_same - fp64["rmse_mean"]) if fp64 else None},
@@ -306,10 +311,12 @@ def run_pp(args, rank, world, local_rank):
     test = (d["test_row"], d["test_col"], d["test_val"])
     m = bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], K, tau, args.precision, I=I, J=J,
                 X0=d["X0"], W0=d["W0"], burnin=B, seed=rank, stream=stream.cuda_stream)
-    stage_ms, launches, sizes_all = [], 0, {}
-    m.profile(True)
+    stage_ms, launches, sizes_all, schedules = [], 0, {}, {}
     with ClockSampler(local_rank) as clk:
         for stage in (1, 2, 3):
+            m.stage(stage, 0, None)                  # opens the stage (priors installed)
+            if not args.no_tune:
+                schedules[stage] = m.autotune(stage, -1, 3)
             sizes = []
             for sid in range(I * J):
                 info = m.subset_info(sid)
@@ -319,6 +326,9 @@ def run_pp(args, rank, world, local_rank):
             ms = 0.0
             for c0 in range(0, T, PP_CHUNK):    # draws in chunks of sweeps (host memory)
                 nc = min(PP_CHUNK, T - c0)
+                # per-kernel event tracing on the first chunk of each stage only (tracing turns
+                # the graph launch off)
+                m.profile(c0 == 0)
                 host = np.concatenate([synth.sweep_draws(sizes, K, float(K),
                                                          synth.rng_for(300 + rank, stage, t))
                                        for t in range(c0, c0 + nc)])
@@ -345,6 +355,8 @@ def run_pp(args, rank, world, local_rank):
     for prec in ("fp64", args.precision):
         mp = bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], K, tau, prec, X0=d["X0"],
                      W0=d["W0"], test=test, burnin=B, seed=rank, stream=stream.cuda_stream)
+        if not args.no_tune:
+            schedules["plain_" + prec] = mp.autotune(1, -1, 3)
         ms = 0.0
         for c0 in range(0, T, PP_CHUNK):
             nc = min(PP_CHUNK, T - c0)
@@ -385,6 +397,7 @@ def run_pp(args, rank, world, local_rank):
         "plain": plain,
         "pp_speedup_vs_plain_fp64_same_sweeps": plain["fp64"]["ms"] / total_ms,
         "kernels": kernels, "gpu_launches": launches, "clocks": clk.summary(),
+        "schedule": schedules,
     }
 
 
@@ -572,6 +585,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=20)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default launch schedule instead of running the schedule tuner")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload (rows and columns by s, observations by s^2); "

@@ -188,22 +188,26 @@ bmf_status bmf_generate_draws(bmf_ctx *ctx, int32_t stage, int32_t subset, int64
  * done, so that the FP64 conditional of one chunk overlaps the Gram pass of the next (1: one
  * Gram launch, then one conditional launch).  gram_blocks_per_sm (1..64): grid of a Gram
  * launch = SMs x this.  row_weight (>= 0): cost of a row in observations for the split; 0
- * selects a default from K and the precision.  Default {1, 1, 4, 0}. */
+ * selects a default from K and the precision.  Default {1, 1, 4, 0, 0}. */
 #define BMF_MAX_CHUNKS 8
 typedef struct {
     int32_t chunks_x, chunks_w;
     int32_t gram_blocks_per_sm;
     double row_weight;
+    int32_t graph;     /* 1: capture each call's launch sequence into one CUDA graph and launch it
+                          once (kept and updated in place across calls of the same shape); 0: launch
+                          directly.  Ignored while profiling is on. */
 } bmf_schedule;
 bmf_status bmf_set_schedule(bmf_ctx *ctx, const bmf_schedule *sched);
 bmf_status bmf_get_schedule(const bmf_ctx *ctx, bmf_schedule *sched);
 
-/* Schedule tuner: times candidate schedules (Gram grid 2/4/8 blocks per SM, then 1-4 row chunks
- * for each half, then the split weight) on the batch of `stage` (subset < 0) or of one subset,
- * one untimed and sweeps_per_trial timed sweeps each with the device generator, and installs the
- * fastest.  Every trial starts from the same state and the chains are restored afterwards (state,
- * gathered copies, moment sums, hyperparameters, running test predictions, sweep counters), so
- * the call changes no sampled value.  The batch's stage must be open.  best: host, nullable. */
+/* Schedule tuner: on the batch of `stage` (subset < 0) or of one subset, times candidate
+ * schedules -- Gram grid 2/4/8 blocks per SM, then 1-4 row chunks for each half, then the split
+ * weight, then the CUDA-graph launch -- with one untimed and sweeps_per_trial timed sweeps each
+ * (device generator), and installs the fastest.  Every trial starts from the same state and the
+ * chains are restored afterwards (state, gathered copies, moment sums, hyperparameters, running
+ * test predictions, sweep counters), so the call changes no sampled value.  The batch's stage
+ * must be open.  best: host, nullable. */
 bmf_status bmf_autotune(bmf_ctx *ctx, int32_t stage, int32_t subset, int32_t sweeps_per_trial,
                         bmf_schedule *best);
 

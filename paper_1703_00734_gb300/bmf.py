@@ -52,7 +52,8 @@ class KernelTime(ctypes.Structure):
 
 class Schedule(ctypes.Structure):
     _fields_ = [("chunks_x", ctypes.c_int32), ("chunks_w", ctypes.c_int32),
-                ("gram_blocks_per_sm", ctypes.c_int32), ("row_weight", ctypes.c_double)]
+                ("gram_blocks_per_sm", ctypes.c_int32), ("row_weight", ctypes.c_double),
+                ("graph", ctypes.c_int32)]
 
 
 class SubsetInfo(ctypes.Structure):
@@ -218,17 +219,19 @@ class BMF:
     def draws_per_sweep(self, stage=1, subset=-1):
         return int(self.L.bmf_draws_per_sweep(self.h, stage, subset))
 
-    def set_schedule(self, chunks_x=1, chunks_w=1, gram_blocks_per_sm=4, row_weight=0.0):
+    def set_schedule(self, chunks_x=1, chunks_w=1, gram_blocks_per_sm=4, row_weight=0.0,
+                     graph=0):
         """Launch schedule (include/bmf.h, bmf_schedule); the sampled values do not depend on it."""
         sc = Schedule(chunks_x=chunks_x, chunks_w=chunks_w, gram_blocks_per_sm=gram_blocks_per_sm,
-                      row_weight=float(row_weight))
+                      row_weight=float(row_weight), graph=int(graph))
         self._check(self.L.bmf_set_schedule(self.h, ctypes.byref(sc)))
 
     def get_schedule(self):
         sc = Schedule()
         self._check(self.L.bmf_get_schedule(self.h, ctypes.byref(sc)))
         return dict(chunks_x=sc.chunks_x, chunks_w=sc.chunks_w,
-                    gram_blocks_per_sm=sc.gram_blocks_per_sm, row_weight=sc.row_weight)
+                    gram_blocks_per_sm=sc.gram_blocks_per_sm, row_weight=sc.row_weight,
+                    graph=sc.graph)
 
     def autotune(self, stage=1, subset=-1, sweeps_per_trial=3):
         """Time candidate launch schedules on a batch and install the fastest (the chains are
@@ -237,7 +240,8 @@ class BMF:
         self._check(self.L.bmf_autotune(self.h, stage, subset, int(sweeps_per_trial),
                                         ctypes.byref(sc)))
         return dict(chunks_x=sc.chunks_x, chunks_w=sc.chunks_w,
-                    gram_blocks_per_sm=sc.gram_blocks_per_sm, row_weight=sc.row_weight)
+                    gram_blocks_per_sm=sc.gram_blocks_per_sm, row_weight=sc.row_weight,
+                    graph=sc.graph)
 
     def generate_draws(self, t0, n=1, stage=1, subset=-1, out=None):
         """The device generator's draws of sweeps t0 .. t0 + n - 1 of a batch (stage, or one

@@ -88,16 +88,17 @@ constexpr int kMaxChunks = BMF_MAX_CHUNKS;
 struct bmf_ctx {
     ~bmf_ctx()
     {
-        for (cudaStream_t x : {st2, st3, st4})
+        for (cudaStream_t x : {st2, st3, st4, st5, cap})
             if (x) {
                 cudaStreamSynchronize(x);
                 cudaStreamDestroy(x);
             }
         for (cudaEvent_t e : {ev_fork, ev_fac[0], ev_fac[1], ev_hyp[0], ev_hyp[1], ev_cdone, ev_tail,
-                              ev_rmse, ev_gen[0], ev_gen[1]})
+                              ev_tail2, ev_rmse, ev_gen[0], ev_gen[1]})
             if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : ev_chunk)
             if (e) cudaEventDestroy(e);
+        if (gexec) cudaGraphExecDestroy(gexec);
     }
     int K = 0, prec = BMF_FP64;
     double tau = 1.0, beta0 = 2.0, nu0 = 1.0, eps_rel = 1e-6;
@@ -108,11 +109,15 @@ struct bmf_ctx {
     cudaStream_t st = nullptr;
     cudaStream_t st2 = nullptr;      // side stream: factor statistics and hyperparameter draws
     cudaStream_t st3 = nullptr;      // conditional stream of the chunked schedule
-    cudaStream_t st4 = nullptr;      // tail stream: test RMSE and the device generator
+    cudaStream_t st4 = nullptr;      // tail stream: test RMSE
+    cudaStream_t st5 = nullptr;      // generator stream: the draws of the sweep after next
+    cudaStream_t cap = nullptr;      // capture stream of the graph schedule (the context stream
+                                     // may be the legacy default stream, which cannot capture)
     cudaEvent_t ev_fork = nullptr, ev_fac[2] = {nullptr, nullptr}, ev_hyp[2] = {nullptr, nullptr};
     cudaEvent_t ev_chunk[kMaxChunks] = {}, ev_cdone = nullptr;
-    cudaEvent_t ev_tail = nullptr, ev_rmse = nullptr, ev_gen[2] = {nullptr, nullptr};
-    bmf_schedule sched = {1, 1, 4, 0.0};
+    cudaEvent_t ev_tail = nullptr, ev_tail2 = nullptr, ev_rmse = nullptr, ev_gen[2] = {nullptr, nullptr};
+    bmf_schedule sched = {1, 1, 4, 0.0, 0};
+    cudaGraphExec_t gexec = nullptr;  // the last captured sweep loop (graph schedule)
     int device = 0, sms = 1;
     DevMem mem;
     Side X, W;
@@ -328,6 +333,7 @@ bmf_status check_dev_error(bmf_ctx *c)
     if (c->st2) CUDA_TRY(c, cudaStreamSynchronize(c->st2));
     if (c->st3) CUDA_TRY(c, cudaStreamSynchronize(c->st3));
     if (c->st4) CUDA_TRY(c, cudaStreamSynchronize(c->st4));
+    if (c->st5) CUDA_TRY(c, cudaStreamSynchronize(c->st5));
     DevError h;
     CUDA_TRY(c, cudaMemcpyAsync(&h, c->err_d, sizeof(h), cudaMemcpyDeviceToHost, c->st));
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
@@ -579,6 +585,24 @@ std::vector<int64_t> chunk_bounds(const bmf_ctx *c, const Side &sd, int64_t b0, 
     return B;
 }
 
+// Graph schedule: while a call's launch sequence is captured, the context's main stream is the
+// capture stream; the guard ends a capture left open by an early error return (discarding the
+// graph) and gives the context its stream back.
+struct CaptureGuard {
+    bmf_ctx *c = nullptr;
+    cudaStream_t user = nullptr;
+    bool active = false;
+    ~CaptureGuard()
+    {
+        if (!active) return;
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(c->st, &g);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        c->st = user;
+    }
+};
+
 // n sweeps of the subsets in slots [sl0, sl1) (a stage, or one subset), batched.
 bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws *draws,
                      bmf_sweep_stats *stats)
@@ -676,6 +700,29 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
         return BMF_OK;
     };
     const bool hyp[2] = {nj[0] > 0, nj[1] > 0};
+    bool used_tail = false, used_gen = false;
+    // graph schedule: the whole launch sequence of the call (all streams) is captured into one
+    // CUDA graph and launched once (the executable graph is kept and updated in place when the
+    // next call has the same shape)
+    CaptureGuard capture;
+    const bool use_graph = c->sched.graph && !c->prof && n_sweeps > 0;
+    if (use_graph) {
+        capture.c = c;
+        capture.user = c->st;
+        const cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(c->cap, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(c->cap, &g);
+                if (g) cudaGraphDestroy(g);
+            }
+            return fail(c, BMF_E_CUDA, std::string("stream capture failed: ") + cudaGetErrorString(e));
+        }
+        c->st = c->cap;
+        capture.active = true;
+    }
     if (n_sweeps > 0 && (hyp[0] || hyp[1])) {
         // statistics of the state at the start of the call (the conditional kernel keeps them
         // current from then on)
@@ -829,14 +876,15 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
                 if ((s = side_hyper(f, it + 1))) return s;
             }
         }
-        // tail of the sweep on its own stream, overlapping the next sweep's Gram pass: the
-        // test RMSE of this sample, then the draws of sweep t + 2 into this sweep's buffer
-        // (every reader of that buffer is ordered before this point)
+        // tail of the sweep on two streams, overlapping the next sweep's Gram pass (which
+        // leaves the FP64 pipes idle): the test RMSE of this sample, and the draws of sweep
+        // t + 2 into this sweep's buffer (every reader of that buffer is ordered before here)
         const bool tail_gen = gen && it + 2 < n_sweeps;
-        if (tt1 > tt0 || tail_gen) {
-            CUDA_TRY(c, cudaEventRecord(c->ev_tail, c->st));
-            CUDA_TRY(c, cudaStreamWaitEvent(c->st4, c->ev_tail, 0));
-        }
+        used_tail |= tt1 > tt0;
+        used_gen |= tail_gen;
+        if (tt1 > tt0 || tail_gen) CUDA_TRY(c, cudaEventRecord(c->ev_tail, c->st));
+        if (tt1 > tt0) CUDA_TRY(c, cudaStreamWaitEvent(c->st4, c->ev_tail, 0));
+        if (tail_gen) CUDA_TRY(c, cudaStreamWaitEvent(c->st5, c->ev_tail, 0));
         if (tt1 > tt0) {
             RmseParams rp{K, c->prec, tt0, tt1, c->trow, c->tcol, c->tval, c->X.G, c->W.G, c->ldg,
                           keep ? 1 : 0, c->ysum, kept > 0 ? 1.0 / (double)kept : 0.0,
@@ -850,14 +898,47 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
         if (tail_gen) {
             GenParams gp{c->gen_segs_d, gen_segs, gen_units, c->seed, t + 2,
                          c->gen_d + (int64_t)(it & 1) * per, c->err_d};
-            traced(c, c->st4, K_GEN, 1, [&] { launch_gen(gp, c->st4); });
-            CUDA_TRY(c, cudaEventRecord(c->ev_gen[it & 1], c->st4));
+            traced(c, c->st5, K_GEN, 1, [&] { launch_gen(gp, c->st5); });
+            CUDA_TRY(c, cudaEventRecord(c->ev_gen[it & 1], c->st5));
         }
     }
     // the context stream is complete when the call returns
-    if (n_sweeps > 0) {
+    // (only streams this call used: under the graph schedule the others are not part of the
+    // capture)
+    if (used_tail) {
         CUDA_TRY(c, cudaEventRecord(c->ev_tail, c->st4));
         CUDA_TRY(c, cudaStreamWaitEvent(c->st, c->ev_tail, 0));
+    }
+    if (used_gen) {
+        CUDA_TRY(c, cudaEventRecord(c->ev_tail2, c->st5));
+        CUDA_TRY(c, cudaStreamWaitEvent(c->st, c->ev_tail2, 0));
+    }
+    if (use_graph) {
+        cudaGraph_t g = nullptr;
+        capture.active = false;
+        const cudaError_t ee = cudaStreamEndCapture(c->st, &g);
+        c->st = capture.user;
+        if (ee != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return fail(c, BMF_E_CUDA, std::string("stream capture failed: ") + cudaGetErrorString(ee));
+        }
+        bool updated = false;
+        if (c->gexec) {
+            cudaGraphExecUpdateResultInfo info;
+            updated = cudaGraphExecUpdate(c->gexec, g, &info) == cudaSuccess;
+            if (!updated) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(c->gexec);
+                c->gexec = nullptr;
+            }
+        }
+        cudaError_t e = updated ? cudaSuccess : cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->gexec = nullptr;
+            return fail(c, BMF_E_CUDA, std::string("graph instantiation failed: ") + cudaGetErrorString(e));
+        }
+        CUDA_TRY(c, cudaGraphLaunch(c->gexec, c->st));
     }
     CUDA_TRY(c, cudaGetLastError());
     for (int sl = sl0; sl < sl1; ++sl) {
@@ -1147,8 +1228,11 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
         bool ok = cudaStreamCreateWithPriority(&c->st2, cudaStreamNonBlocking, hi) == cudaSuccess;
         ok = ok && cudaStreamCreateWithPriority(&c->st3, cudaStreamNonBlocking, hi) == cudaSuccess;
         ok = ok && cudaStreamCreateWithPriority(&c->st4, cudaStreamNonBlocking, hi) == cudaSuccess;
+        ok = ok && cudaStreamCreateWithPriority(&c->st5, cudaStreamNonBlocking, hi) == cudaSuccess;
+        ok = ok && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) == cudaSuccess;
         for (cudaEvent_t *e : {&c->ev_fork, &c->ev_fac[0], &c->ev_fac[1], &c->ev_hyp[0], &c->ev_hyp[1],
-                               &c->ev_cdone, &c->ev_tail, &c->ev_rmse, &c->ev_gen[0], &c->ev_gen[1]})
+                               &c->ev_cdone, &c->ev_tail, &c->ev_tail2, &c->ev_rmse, &c->ev_gen[0],
+                               &c->ev_gen[1]})
             ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
         for (cudaEvent_t &e : c->ev_chunk)
             ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
@@ -1287,6 +1371,7 @@ bmf_status bmf_set_schedule(bmf_ctx *c, const bmf_schedule *s)
         return fail(c, BMF_E_ARG, "gram_blocks_per_sm must be in 1..64");
     if (!(s->row_weight >= 0.0) || !std::isfinite(s->row_weight))
         return fail(c, BMF_E_ARG, "row_weight must be finite and >= 0");
+    if (s->graph != 0 && s->graph != 1) return fail(c, BMF_E_ARG, "graph must be 0 or 1");
     c->sched = *s;
     return BMF_OK;
 }
@@ -1409,9 +1494,9 @@ bmf_status bmf_autotune(bmf_ctx *c, int32_t stage, int32_t subset, int32_t sweep
         }
         return BMF_OK;
     };
-    bmf_schedule b0{1, 1, 4, 0.0};
+    bmf_schedule b0{1, 1, 4, 0.0, 0};
     cands = {b0};
-    for (int g : {2, 8}) cands.push_back(bmf_schedule{1, 1, g, 0.0});
+    for (int g : {2, 8}) cands.push_back(bmf_schedule{1, 1, g, 0.0, 0});
     s = run_all(cands);
     for (int f = 0; f < 2 && !s; ++f) {
         cands.clear();
@@ -1431,6 +1516,11 @@ bmf_status bmf_autotune(bmf_ctx *c, int32_t stage, int32_t subset, int32_t sweep
             cands.push_back(sc);
         }
         s = run_all(cands);
+    }
+    if (!s) {
+        bmf_schedule sc = best;
+        sc.graph = 1;
+        s = run_all({sc});
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

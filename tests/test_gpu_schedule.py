@@ -9,7 +9,8 @@ from pairing import Pair
 
 pytestmark = pytest.mark.gpu
 
-SCHEDULES = [(1, 1, 4, 0.0), (2, 3, 2, 0.0), (8, 8, 1, 0.0), (4, 2, 4, 500.0)]
+SCHEDULES = [(1, 1, 4, 0.0, 0), (2, 3, 2, 0.0, 0), (8, 8, 1, 0.0, 0), (4, 2, 4, 500.0, 0),
+             (1, 1, 4, 0.0, 1), (3, 2, 8, 0.0, 1)]
 
 
 def run(d, K, prec, sched, I=1, J=1, sweeps=3):
@@ -51,6 +52,10 @@ def test_chunked_schedule_fp64_parity():
     pr.m.set_schedule(4, 3, 2)
     pr.run_stage(1, 2)
     pr.compare_subset(0, rel=1e-8)
+    pr.m.set_schedule(2, 2, 4, graph=1)      # and the graph-captured launch, twice (update path)
+    pr.run_stage(1, 2, t0=2)
+    pr.run_stage(1, 2, t0=4)
+    pr.compare_subset(0, rel=1e-7)
 
 
 def test_schedule_argument_errors():
@@ -58,7 +63,7 @@ def test_schedule_argument_errors():
     d = synth.make_workload(None, N=40, D=30, M=300, pattern="uniform", K=2, sigma=0.5,
                             tau=4.0, seed=1)
     m = bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], 2, d["tau"])
-    for bad in [(0, 1, 4, 0.0), (1, 9, 4, 0.0), (1, 1, 0, 0.0), (1, 1, 4, -1.0)]:
+    for bad in [(0, 1, 4, 0.0), (1, 9, 4, 0.0), (1, 1, 0, 0.0), (1, 1, 4, -1.0), (1, 1, 4, 0.0, 2)]:
         with pytest.raises(bmf.BmfError) as e:
             m.set_schedule(*bad)
         assert e.value.status == 1
