@@ -983,8 +983,6 @@ bmf_status finalize_stage(bmf_ctx *c, int stage)
             return fail(c, BMF_E_STATE, "subset " + std::to_string(g.sid) + " has " +
                                             std::to_string(su.kept) + " retained samples; moment "
                                             "matching needs at least K + 1 (a full-rank covariance)");
-        if (c->K > kNarrowMaxK)
-            return fail(c, BMF_E_ARG, "moment matching supports K <= 16 in this build");
         for (int f = 0; f < 2; ++f) {
             Side &sd = f == 0 ? c->X : c->W;
             MMParams mp{c->K, f == 0 ? g.xoff : g.woff,
@@ -1100,7 +1098,8 @@ bmf_status aggregate_all(bmf_ctx *c, int64_t *n_corrected)
                                         cudaMemcpyHostToDevice, c->st));
             AggParams ap{K, n, ns, base_d, sd.mm_mu, sd.mm_L, sd.R, c->eps_rel, out, c->ncorr_d,
                          c->err_d};
-            launch_aggregate(ap, c->st);
+            if (!launch_aggregate(ap, c->st))
+                return fail(c, BMF_E_OOM, "device allocation failed (aggregation scratch)");
             CUDA_TRY(c, cudaStreamSynchronize(c->st));
         }
     }
@@ -1739,8 +1738,6 @@ bmf_status bmf_get_posterior(bmf_ctx *c, int32_t subset, int32_t factor, double 
             return fail(c, BMF_E_STATE, "subset " + std::to_string(g.sid) + " has " +
                                             std::to_string(su.kept) + " retained samples; moment "
                                             "matching needs at least K + 1 (a full-rank covariance)");
-        if (c->K > kNarrowMaxK)
-            return fail(c, BMF_E_ARG, "moment matching supports K <= 16 in this build");
         for (int f = 0; f < 2; ++f) {
             Side &sd = f == 0 ? c->X : c->W;
             MMParams mp{c->K, f == 0 ? g.xoff : g.woff, f == 0 ? g.xoff + g.n() : g.woff + g.d(),

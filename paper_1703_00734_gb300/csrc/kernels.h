@@ -179,7 +179,7 @@ struct AggParams {
     unsigned long long *n_corrected;
     DevError *err;
 };
-void launch_aggregate(const AggParams &a, cudaStream_t st);
+bool launch_aggregate(const AggParams &a, cudaStream_t st);   // false: scratch allocation failed
 
 // y_hat = offset + xm[row]^T wm[col] for host-given entries (original order means).
 void launch_predict(int K, int64_t n, const int32_t *row, const int32_t *col, const double *Xm,

@@ -466,13 +466,23 @@ void launch_rmse_final(const double *partial, int blocks, double *out2, cudaStre
 }
 
 // ------------------------------------------------------------------------------------------
-// Thread-per-row FP64 helpers on packed lower matrices in interleaved shared memory.
+// Thread-per-row FP64 helpers on packed lower matrices in interleaved shared memory: entry e of
+// a thread's matrix at base[e * rb], rb = threads per block (32, fewer when K is large enough
+// that 32 rows' matrices would not fit in shared memory).
 // ------------------------------------------------------------------------------------------
 constexpr int kRowBlock = 32;
-#define RS(base, e) (base)[(e) * kRowBlock]
+constexpr size_t kRowSmemCap = 200 * 1024;
+#define RS(base, e) (base)[(e) * rb]
+
+// Threads per block of a thread-per-row kernel holding `per_row` doubles per row.
+static int row_block(size_t per_row)
+{
+    const size_t fit = kRowSmemCap / (per_row * sizeof(double));
+    return (int)(fit >= (size_t)kRowBlock ? kRowBlock : (fit < 1 ? 1 : fit));
+}
 
 // In-place packed lower Cholesky; returns false if a pivot is not > 0.
-__device__ bool row_chol(double *P, int K)
+__device__ bool row_chol(double *P, int K, int rb)
 {
     for (int j = 0; j < K; ++j) {
         const int jj = tri(j, 0);
@@ -492,7 +502,7 @@ __device__ bool row_chol(double *P, int K)
 }
 
 // Solve (L L^T) x = b in place in vector v (interleaved), L packed in P.
-__device__ void row_solve(const double *P, double *v, int K)
+__device__ void row_solve(const double *P, double *v, int K, int rb)
 {
     for (int i = 0; i < K; ++i) {
         const int ii = tri(i, 0);
@@ -508,11 +518,11 @@ __device__ void row_solve(const double *P, double *v, int K)
 }
 
 // Inverse of L L^T (L packed in P) into packed Out: column c from (L L^T) x = e_c, using tmp[K].
-__device__ void row_inverse(const double *P, double *Out, double *tmp, int K)
+__device__ void row_inverse(const double *P, double *Out, double *tmp, int K, int rb)
 {
     for (int c = 0; c < K; ++c) {
         for (int i = 0; i < K; ++i) RS(tmp, i) = (i == c) ? 1.0 : 0.0;
-        row_solve(P, tmp, K);
+        row_solve(P, tmp, K, rb);
         for (int i = c; i < K; ++i) RS(Out, tri(i, c)) = RS(tmp, i);
     }
 }
@@ -523,22 +533,21 @@ __device__ void row_inverse(const double *P, double *Out, double *tmp, int K)
 __global__ void __launch_bounds__(kRowBlock) mm_kernel(MMParams a)
 {
     extern __shared__ double sm[];
-    const int t = threadIdx.x;
-    const int64_t r = a.r0 + (int64_t)blockIdx.x * kRowBlock + t;
+    const int t = threadIdx.x, rb = blockDim.x;
+    const int64_t r = a.r0 + (int64_t)blockIdx.x * rb + t;
     if (r >= a.r1) return;
     const int K = a.K, NT = ntri(K);
-    double *Sg = sm + t, *Lm = Sg + NT * kRowBlock, *mu = Lm + NT * kRowBlock,
-           *tmp = mu + K * kRowBlock;
+    double *Sg = sm + t, *Lm = Sg + NT * rb, *mu = Lm + NT * rb, *tmp = mu + K * rb;
     for (int i = 0; i < K; ++i) RS(mu, i) = a.S1[(int64_t)i * a.R + r] / a.S;
     for (int i = 0; i < K; ++i)
         for (int j = 0; j <= i; ++j)
             RS(Sg, tri(i, j)) = a.S2[(int64_t)tri(i, j) * a.R + r] / a.S - RS(mu, i) * RS(mu, j);
-    if (!row_chol(Sg, K)) {
+    if (!row_chol(Sg, K, rb)) {
         atomicOr(&a.err->flags, ERR_NOT_PD);
         atomicMin(&a.err->first_bad_row, (int)r);
         return;
     }
-    row_inverse(Sg, Lm, tmp, K);
+    row_inverse(Sg, Lm, tmp, K, rb);
     for (int i = 0; i < K; ++i) a.mu[r * K + i] = RS(mu, i);
     for (int e = 0; e < NT; ++e) a.L[(int64_t)e * a.R + r] = RS(Lm, e);
     for (int i = 0; i < K; ++i) {
@@ -553,10 +562,12 @@ void launch_mm(const MMParams &a, cudaStream_t st)
 {
     const int64_t n = a.r1 - a.r0;
     if (n <= 0) return;
-    const size_t smem = (size_t)(2 * ntri(a.K) + 2 * a.K) * kRowBlock * sizeof(double);
+    const size_t per_row = (size_t)(2 * ntri(a.K) + 2 * a.K);
+    const int rb = row_block(per_row);
+    const size_t smem = per_row * rb * sizeof(double);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(mm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    mm_kernel<<<(int)((n + kRowBlock - 1) / kRowBlock), kRowBlock, smem, st>>>(a);
+    mm_kernel<<<(int)((n + rb - 1) / rb), rb, smem, st>>>(a);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -637,11 +648,11 @@ __device__ double jacobi_min_eig(double *a, int K)
 __global__ void __launch_bounds__(kRowBlock) aggregate_kernel(AggParams a, double *jac_scratch)
 {
     extern __shared__ double sm[];
-    const int t = threadIdx.x;
-    const int64_t n = (int64_t)blockIdx.x * kRowBlock + t;
+    const int t = threadIdx.x, rb = blockDim.x;
+    const int64_t n = (int64_t)blockIdx.x * rb + t;
     if (n >= a.n_rows) return;
     const int K = a.K, NT = ntri(K), J = a.J;
-    double *Ls = sm + t, *Dm = Ls + NT * kRowBlock, *h = Dm + NT * kRowBlock;
+    double *Ls = sm + t, *Dm = Ls + NT * rb, *h = Dm + NT * rb;
     const int64_t r1 = a.sub_base[0] + n;
     const double c0 = 2.0 - (double)J;
     double mean_diag = 0.0;
@@ -704,30 +715,34 @@ __global__ void __launch_bounds__(kRowBlock) aggregate_kernel(AggParams a, doubl
             RS(h, i) += s;
         }
     }
-    if (!row_chol(Ls, K)) {
+    if (!row_chol(Ls, K, rb)) {
         atomicOr(&a.err->flags, ERR_NOT_PD);
         atomicMin(&a.err->first_bad_row, (int)n);
         return;
     }
-    row_solve(Ls, h, K);
+    row_solve(Ls, h, K, rb);
     for (int i = 0; i < K; ++i) a.out[n * K + i] = RS(h, i);
     if (ncorr) atomicAdd(a.n_corrected, ncorr);
 }
 
-void launch_aggregate(const AggParams &a, cudaStream_t st)
+bool launch_aggregate(const AggParams &a, cudaStream_t st)
 {
-    if (a.n_rows <= 0) return;
+    if (a.n_rows <= 0) return true;
     // per-row K x K scratch for the factorisation test and the Jacobi fallback
     double *scr = nullptr;
-    if (cudaMallocAsync(&scr, (size_t)a.n_rows * a.K * a.K * sizeof(double), st) != cudaSuccess)
-        return;
-    const size_t smem = (size_t)(2 * ntri(a.K) + a.K) * kRowBlock * sizeof(double);
+    if (cudaMallocAsync(&scr, (size_t)a.n_rows * a.K * a.K * sizeof(double), st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const size_t per_row = (size_t)(2 * ntri(a.K) + a.K);
+    const int rb = row_block(per_row);
+    const size_t smem = per_row * rb * sizeof(double);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(aggregate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-    aggregate_kernel<<<(int)((a.n_rows + kRowBlock - 1) / kRowBlock), kRowBlock, smem, st>>>(a,
-                                                                                           scr);
+    aggregate_kernel<<<(int)((a.n_rows + rb - 1) / rb), rb, smem, st>>>(a, scr);
     cudaFreeAsync(scr, st);
+    return true;
 }
 
 // ------------------------------------------------------------------------------------------

@@ -435,9 +435,10 @@ void launch_gram_wide(int K, int prec, const GramParams &a, int grid, cudaStream
 }
 
 // ------------------------------------------------------------------------------------------
-// Conditional draw for K >= 13: a team of T lanes per row (T = 4 for K <= 16, 8 for K <= 32,
-// 16 for K <= 48, 32 above), 32 / T rows per warp at a time; below K = 13 one thread per row
-// (cond.cu) is as fast (measured on this GPU: equal at K = 10, the team form 18% faster at 16).
+// Conditional draw for K >= 13: a team of T lanes per row (T = 4 for K <= 16, 16 for K <= 48,
+// 32 above), 32 / T rows per warp at a time; below K = 13 one thread per row (cond.cu) is as
+// fast.  Measured on this GPU: equal at K = 10, the team form 18% faster at K = 16; at K = 32
+// teams of 16 lanes 7% faster than teams of 8 and 20% faster than 32.
 // The row's packed matrix lives in shared memory; the team factors it right-looking (each step:
 // the pivot, read by every lane, then the column scaled and the trailing triangle updated with
 // the entries spread over the team), then solves column by column.  On this GPU the FP64 pipe
@@ -464,7 +465,7 @@ __device__ __forceinline__ void decode_packed(int e, int &i, int &j)
     j = e - i * (i + 1) / 2;
 }
 
-int cond_team_size(int K) { return K <= 16 ? 4 : (K <= 32 ? 8 : (K <= 48 ? 16 : 32)); }
+int cond_team_size(int K) { return K <= 16 ? 4 : (K <= 48 ? 16 : 32); }
 
 // Doubles per team in shared memory: the packed matrix, right-hand side, pivots and (teams of 8
 // or more lanes) a contiguous copy of the current column, padded so that the teams of one

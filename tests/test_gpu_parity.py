@@ -132,3 +132,42 @@ def test_thread_per_row_conditional_on_large_halves(K):
     pr = Pair(d, K)
     pr.run_stage(1, 1)
     pr.compare_subset(0)
+
+
+def test_fault_injection_on_the_host():
+    """Faults made on the host give their documented status and leave the GPU usable: an
+    out-of-range index, a forced non-positive-definite prior (BMF_E_NOT_PD, then BMF_E_STATE
+    until bmf_set_state), and a tuner call on a stage that is not open."""
+    from paper_1703_00734_gb300 import bmf
+    d = small(N=60, D=40, M=800, K=3, seed=23)
+    for bad in (d["N"], -1):
+        row = d["row"].copy()
+        row[5] = bad
+        with pytest.raises(bmf.BmfError) as e:
+            bmf.BMF(d["N"], d["D"], row, d["col"], d["val"], 3, 1.0, X0=d["X0"], W0=d["W0"])
+        assert e.value.status == 1
+    m = bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], 3, 4.0, X0=d["X0"], W0=d["W0"],
+                seed=2)
+    n = d["N"]
+    mu = np.zeros((n, 3))
+    m.set_prior(0, bmf.FACTOR_X, mu, np.tile(-np.eye(3) * 1e3, (n, 1, 1)))
+    with pytest.raises(bmf.BmfError) as e:
+        m.sweep(0, 1, None)
+    assert e.value.status == 3 and "arena row" in str(e.value)
+    with pytest.raises(bmf.BmfError) as e:
+        m.sweep(0, 1, None)
+    assert e.value.status == 8
+    X0 = d["X0"][m.perm()[0]]
+    W0 = d["W0"][m.perm()[1]]
+    m.set_state(0, X0, W0)
+    m.set_prior(0, bmf.FACTOR_X, mu, np.tile(np.eye(3), (n, 1, 1)))
+    st = m.sweep(0, 2, None)
+    assert st["sweeps"] >= 2
+    X, W, _ = m.get_state(0)
+    assert np.all(np.isfinite(X)) and np.all(np.isfinite(W))
+    m.close()
+    m = bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], 3, 4.0, I=2, J=2)
+    with pytest.raises(bmf.BmfError) as e:
+        m.autotune(2, -1, 1)
+    assert e.value.status == 8
+    m.close()

@@ -5,8 +5,9 @@ first-order bound of test_gpu_precision.py."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1703_00734_gb300 import synth
-from pairing import Pair
+from pairing import Pair, assert_rows_close
 from test_gpu_precision import run_reduced
 
 pytestmark = pytest.mark.gpu
@@ -46,3 +47,31 @@ def test_wide_fp32_split_tf32_within_bound(K):
     d["tau"] = 1.5625
     qx, qw = run_reduced(d, K, "fp32", 2.0 ** -21)
     print(f"fp32 (split TF32) K={K}: worst err/bound X {qx:.3f} W {qw:.3f}")
+
+
+@pytest.mark.parametrize("K", [20, 40])
+def test_wide_pp_stages_moment_matching_and_aggregation(K):
+    """Three PP stages at K > 16 (tensor-core Gram path, team conditional, moment matching and
+    Algorithm 2 with fewer rows per block) against the oracle, FP64."""
+    d = synth.make_workload(None, N=240, D=160, M=9000, pattern="uniform", K=K, sigma=0.5,
+                            tau=4.0, seed=100 + K)
+    pr = Pair(d, K, I=2, J=2, burnin=3)
+    T = 3 + 2 * K
+    for stage in (1, 2, 3):
+        pr.run_stage(stage, T)
+        for s in pr.p.stage_subsets(stage):
+            pr.compare_subset(s.sid, rel=1e-7)
+        pr.finish_stage(stage)
+        for s in pr.p.stage_subsets(stage):
+            for f in (0, 1):
+                mu, Lam = pr.m.get_posterior(s.sid, f)
+                fm = pr.finals[s.sid]
+                assert_rows_close(mu, fm[2 * f], 1e-6, f"MM mean {s.sid}/{f}")
+                assert_rows_close(Lam.reshape(len(Lam), -1), fm[2 * f + 1].reshape(len(Lam), -1),
+                                  1e-6, f"MM precision {s.sid}/{f}")
+    Xm_o, Wm_o, nc_o = oracle.aggregate_plan(pr.p, pr.finals, K)
+    Xm, Wm, nc = pr.m.posterior_means()
+    assert nc == nc_o
+    rr, cr = np.argsort(pr.p.row_perm), np.argsort(pr.p.col_perm)
+    assert_rows_close(Xm, Xm_o[rr], 1e-6, "aggregated X")
+    assert_rows_close(Wm, Wm_o[cr], 1e-6, "aggregated W")
