@@ -141,7 +141,9 @@ __global__ void __launch_bounds__(kCondBlock) cond_kernel(CondParams a)
         for (int i = 0; i < K; ++i) SM(B0 + i) = 0.0;
     }
     // 7. statistics of the new state for the next hyperparameter draw: per block, sum x and
-    //    the packed lower sum x x^T over the block's rows (thread e computes entry e, in row order)
+    //    the packed lower sum x x^T over the block's rows (thread e computes entry e, in row
+    //    order); skipped when the caller computes them on another stream (stats == nullptr)
+    if (a.stats == nullptr) return;
     __syncthreads();
     const int NS = K + NT;
     double *out = a.stats + (a.blk0 + blockIdx.x) * (int64_t)NS;

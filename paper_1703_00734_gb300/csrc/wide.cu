@@ -613,8 +613,9 @@ __global__ void __launch_bounds__(32 * kWideWarps) cond_team_kernel(CondParams a
         }
         __syncwarp(mask);
     }
+    // 7. per-block statistics of the new state (unless computed on another stream)
+    if (a.stats == nullptr) return;
     __syncthreads();
-    // 7. per-block statistics of the new state
     const int NS = K + NT;
     double *out = a.stats + (a.blk0 + blockIdx.x) * (int64_t)NS;
     for (int e = threadIdx.x; e < NS; e += blockDim.x) {
