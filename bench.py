@@ -191,10 +191,15 @@ def run_ours(args, rank, world, local_rank):
         ms = float(t.item())
     rmse_red = st["rmse_mean"]
     # ---- per-kernel timing over the same number of steps (profiling pass) ------------
+    # one launch per kernel and half (no row chunks), so that each launch's event time is the
+    # kernel's own duration and not shared with an overlapping chunk on another stream
+    tuned = m.get_schedule()
+    m.set_schedule(1, 1, tuned["gram_blocks_per_sm"], 0.0, 0)
     m.profile(True)
     m.sweep(0, S, dr[W * per:(W + S) * per])
     prof = m.profile_read()
     m.profile(False)
+    m.set_schedule(**tuned)
     # ---- e2e: host (pinned) draws copied in every step, stats read back ---------------
     pinned = torch.from_numpy(host[W * per:(W + S) * per].copy()).pin_memory()
     torch.cuda.synchronize()

@@ -163,9 +163,156 @@ __global__ void __launch_bounds__(kCondBlock) cond_kernel(CondParams a)
 #undef SM
 }
 
+// ------------------------------------------------------------------------------------------
+// The same conditional with K known at compile time (K = 4, 5, 10: the sizes the compiler keeps
+// entirely in registers): the packed matrix, right-hand side and pivots live in registers (fully
+// unrolled loops with constant indices), so the FP64 chain is not interleaved with
+// shared-memory loads.  Same operations in the same order as cond_kernel;
+// shared memory holds only the block's new rows for the statistics epilogue.
+// ------------------------------------------------------------------------------------------
+template <int K, typename GT, typename AT>
+__global__ void __launch_bounds__(kCondBlock) cond_kernel_k(CondParams a)
+{
+    constexpr int NT = ntri(K);
+    __shared__ double XS[K][kCondBlock];
+    const int t = threadIdx.x;
+    const CondBlock blk = a.blocks[blockIdx.x];
+    const int64_t r = blk.row0 + t;
+    const bool active = t < blk.n;
+    const int64_t R = a.R;
+    double M[NT], B[K], RI[K];
+    bool ok = active;
+    if (active) {
+        const int prhs = a.part_rhs;
+        const int64_t i0 = a.item_ptr[r], i1 = a.item_ptr[r + 1];
+        const int mi = a.multi_idx[r];
+        if (mi >= 0) {
+            const double *p = a.rowsum + (int64_t)mi * a.ld_sum;
+#pragma unroll
+            for (int e = 0; e < NT; ++e) M[e] = p[e];
+#pragma unroll
+            for (int i = 0; i < K; ++i) B[i] = p[prhs + i];
+        } else if (i1 > i0) {
+            const AT *p = static_cast<const AT *>(a.part) + (i0 - a.item0) * (int64_t)a.ld;
+#pragma unroll
+            for (int e = 0; e < NT; ++e) M[e] = widen(p[e]);
+#pragma unroll
+            for (int i = 0; i < K; ++i) B[i] = widen(p[prhs + i]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < NT; ++e) M[e] = 0.0;
+#pragma unroll
+            for (int i = 0; i < K; ++i) B[i] = 0.0;
+        }
+        const int h = a.row_hslot[r];
+        const double tau = a.tau;
+        if (h >= 0) {
+            const double *hp = a.hyper + (int64_t)h * hyper_slot_len(K);
+#pragma unroll
+            for (int e = 0; e < NT; ++e) M[e] = fma(tau, M[e], hp[K + e]);
+#pragma unroll
+            for (int i = 0; i < K; ++i) B[i] = fma(tau, B[i], hp[K + NT + i]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < NT; ++e) M[e] = fma(tau, M[e], a.prior_L[(int64_t)e * R + r]);
+#pragma unroll
+            for (int i = 0; i < K; ++i) B[i] = fma(tau, B[i], a.prior_b[(int64_t)i * R + r]);
+        }
+        // Cholesky (Crout order), as in cond_kernel
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            double d = M[tri(j, j)];
+#pragma unroll
+            for (int k = 0; k < j; ++k) d = fma(-M[tri(j, k)], M[tri(j, k)], d);
+            if (!(d > 0.0)) ok = false;
+            const double rs = rsqrt(d);
+            RI[j] = rs;
+            M[tri(j, j)] = d * rs;
+#pragma unroll
+            for (int i = j + 1; i < K; ++i) {
+                double s2 = M[tri(i, j)];
+#pragma unroll
+                for (int k = 0; k < j; ++k) s2 = fma(-M[tri(i, k)], M[tri(j, k)], s2);
+                M[tri(i, j)] = s2 * rs;
+            }
+        }
+        if (!ok) {
+            atomicOr(&a.err->flags, ERR_NOT_PD);
+            atomicMin(&a.err->first_bad_row, (int)r);
+        }
+    }
+    if (ok) {
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            double s2 = B[i];
+#pragma unroll
+            for (int k = 0; k < i; ++k) s2 = fma(-M[tri(i, k)], B[k], s2);
+            B[i] = s2 * RI[i];
+        }
+        const double *z = a.z + (r - a.row0) * K;
+#pragma unroll
+        for (int i = K - 1; i >= 0; --i) {
+            double s2 = B[i] + z[i];
+#pragma unroll
+            for (int k = i + 1; k < K; ++k) s2 = fma(-M[tri(k, i)], B[k], s2);
+            B[i] = s2 * RI[i];
+        }
+        double *xr = a.X + r * K;
+        GT *g = static_cast<GT *>(a.Xg) + r * a.ldg;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            xr[i] = B[i];
+            g[i] = to_gather<GT>(B[i]);
+        }
+        for (int i = K; i < a.ldg; ++i) g[i] = to_gather<GT>(0.0);
+        if (a.keep) {
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                a.S1[(int64_t)i * R + r] += B[i];
+                if (a.full)
+#pragma unroll
+                    for (int j = 0; j <= i; ++j) a.S2[(int64_t)tri(i, j) * R + r] += B[i] * B[j];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < K; ++i) B[i] = 0.0;
+    }
+    if (a.stats == nullptr) return;
+#pragma unroll
+    for (int i = 0; i < K; ++i) XS[i][t] = B[i];
+    __syncthreads();
+    constexpr int NS = K + NT;
+    double *out = a.stats + (a.blk0 + blockIdx.x) * (int64_t)NS;
+    for (int e = t; e < NS; e += kCondBlock) {
+        double s2 = 0.0;
+        if (e < K) {
+            for (int q = 0; q < blk.n; ++q) s2 += XS[e][q];
+        } else {
+            int i = 0;
+            while ((i + 1) * (i + 2) / 2 <= e - K) ++i;
+            const int j = e - K - i * (i + 1) / 2;
+            for (int q = 0; q < blk.n; ++q) s2 = fma(XS[i][q], XS[j][q], s2);
+        }
+        out[e] = s2;
+    }
+}
+
+template <typename GT, typename AT>
+static bool launch_cond_fixed(const CondParams &a, int n_blocks, cudaStream_t st)
+{
+    switch (a.K) {
+    case 4: cond_kernel_k<4, GT, AT><<<n_blocks, kCondBlock, 0, st>>>(a); return true;
+    case 5: cond_kernel_k<5, GT, AT><<<n_blocks, kCondBlock, 0, st>>>(a); return true;
+    case 10: cond_kernel_k<10, GT, AT><<<n_blocks, kCondBlock, 0, st>>>(a); return true;
+    default: return false;
+    }
+}
+
 template <typename GT, typename AT>
 static void launch_cond_t(const CondParams &a, int n_blocks, cudaStream_t st)
 {
+    if (launch_cond_fixed<GT, AT>(a, n_blocks, st)) return;
     const size_t smem = (size_t)cond_slots(a.K) * kCondBlock * sizeof(double);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(cond_kernel<GT, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize,

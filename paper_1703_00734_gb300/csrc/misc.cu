@@ -24,11 +24,10 @@ __device__ __forceinline__ void decode_tri(int e, int &i, int &j)
 }
 
 // ------------------------------------------------------------------------------------------
-// Factor statistics: per chunk of rows, sum_x [K] then packed lower sum_x x^T [ntri(K)].
-// Work item (e, g) of a block sums entry e over the chunk's rows r with r % G == g (G row groups,
-// G = 256 / NS when the NS entries fit in the block several times, else 1), with two
-// accumulators (alternate rows); the groups' partials are then added in group order, so every
-// sum has a fixed order.
+// Factor statistics: per chunk of rows, sum_x [K] then packed lower sum_x x^T [ntri(K)], each
+// entry summed over the chunk's rows in row order -- the order of the conditional kernels'
+// statistics epilogue, so that a call's first hyperparameter draw (statistics from this kernel)
+// equals the draw the previous call's last sweep would have made (statistics from the epilogue).
 // ------------------------------------------------------------------------------------------
 constexpr int kStatThreads = 256, kStatTile = 32, kStatMaxPer = 9;
 
@@ -36,28 +35,25 @@ __global__ void __launch_bounds__(kStatThreads)
 stats_kernel(int K, const StatChunk *__restrict__ chunks, const double *__restrict__ X,
              const double *__restrict__ W, double *__restrict__ out)
 {
-    extern __shared__ double tile[];  // [kStatTile][K], then [G][NS] group partials
+    extern __shared__ double tile[];  // [kStatTile][K]
     const StatChunk c = chunks[blockIdx.x];
     const double *A = c.arena ? W : X;
     const int NS = K + ntri(K);
-    const int G = NS <= kStatThreads ? kStatThreads / NS : 1;
     const int t = threadIdx.x;
-    double s0[kStatMaxPer], s1[kStatMaxPer];
-    int ei[kStatMaxPer], ej[kStatMaxPer], eg[kStatMaxPer];
+    double acc[kStatMaxPer];
+    int ei[kStatMaxPer], ej[kStatMaxPer];
 #pragma unroll
     for (int q = 0; q < kStatMaxPer; ++q) {
-        s0[q] = s1[q] = 0.0;
-        const int item = t + q * kStatThreads;
-        const int e = item % NS, g = item / NS;
-        eg[q] = g;
-        if (g >= G) {
-            ei[q] = -1;
-            ej[q] = -1;
-        } else if (e < K) {
+        acc[q] = 0.0;
+        const int e = t + q * kStatThreads;
+        if (e < K) {
             ei[q] = e;
             ej[q] = -1;
-        } else {
+        } else if (e < NS) {
             decode_tri(e - K, ei[q], ej[q]);
+        } else {
+            ei[q] = -1;
+            ej[q] = -1;
         }
     }
     for (int64_t r0 = c.r0; r0 < c.r1; r0 += kStatTile) {
@@ -69,37 +65,18 @@ stats_kernel(int K, const StatChunk *__restrict__ chunks, const double *__restri
         for (int q = 0; q < kStatMaxPer; ++q) {
             if (ei[q] < 0) continue;
             const int i = ei[q], j = ej[q];
-            double a0 = s0[q], a1 = s1[q];
-            if (j < 0) {
-                for (int rr = eg[q]; rr < rows; rr += 2 * G) {
-                    a0 += tile[rr * K + i];
-                    if (rr + G < rows) a1 += tile[(rr + G) * K + i];
-                }
-            } else {
-                for (int rr = eg[q]; rr < rows; rr += 2 * G) {
-                    a0 = fma(tile[rr * K + i], tile[rr * K + j], a0);
-                    if (rr + G < rows) a1 = fma(tile[(rr + G) * K + i], tile[(rr + G) * K + j], a1);
-                }
-            }
-            s0[q] = a0;
-            s1[q] = a1;
+            double s = acc[q];
+            if (j < 0)
+                for (int rr = 0; rr < rows; ++rr) s += tile[rr * K + i];
+            else
+                for (int rr = 0; rr < rows; ++rr) s = fma(tile[rr * K + i], tile[rr * K + j], s);
+            acc[q] = s;
         }
     }
-    if (G == 1) {
 #pragma unroll
-        for (int q = 0; q < kStatMaxPer; ++q) {
-            const int e = t + q * kStatThreads;
-            if (e < NS) out[(int64_t)c.out * NS + e] = s0[q] + s1[q];
-        }
-        return;
-    }
-    double *part = tile + kStatTile * K;   // [G][NS]
-    if (t < G * NS) part[t] = s0[0] + s1[0];
-    __syncthreads();
-    for (int e = t; e < NS; e += kStatThreads) {
-        double v = 0.0;
-        for (int g = 0; g < G; ++g) v += part[g * NS + e];
-        out[(int64_t)c.out * NS + e] = v;
+    for (int q = 0; q < kStatMaxPer; ++q) {
+        const int e = t + q * kStatThreads;
+        if (e < NS) out[(int64_t)c.out * NS + e] = acc[q];
     }
 }
 
@@ -107,8 +84,8 @@ void launch_stats(int K, const StatChunk *chunks, int n_chunks, const double *X,
                   double *out, cudaStream_t st)
 {
     if (n_chunks <= 0) return;
-    const size_t smem = ((size_t)kStatTile * K + kStatThreads) * sizeof(double);
-    stats_kernel<<<n_chunks, kStatThreads, smem, st>>>(K, chunks, X, W, out);
+    stats_kernel<<<n_chunks, kStatThreads, kStatTile * K * sizeof(double), st>>>(K, chunks, X, W,
+                                                                                 out);
 }
 
 // ------------------------------------------------------------------------------------------
