@@ -164,10 +164,11 @@ __global__ void __launch_bounds__(kCondBlock) cond_kernel(CondParams a)
 }
 
 // ------------------------------------------------------------------------------------------
-// The same conditional with K known at compile time (K = 4, 5, 10: the sizes the compiler keeps
-// entirely in registers): the packed matrix, right-hand side and pivots live in registers (fully
-// unrolled loops with constant indices), so the FP64 chain is not interleaved with
-// shared-memory loads.  Same operations in the same order as cond_kernel;
+// The same conditional with K known at compile time: the packed matrix, right-hand side and
+// pivots live in registers (fully unrolled loops with constant indices), so the FP64 chain is
+// not interleaved with shared-memory loads.  Instantiated for K = 1, 3, 4, 5, 10, 11, 12, the
+// sizes the compiler keeps entirely in registers (for K = 2 and 6-9 it places the matrix in
+// local memory, so those take cond_kernel).  Same operations in the same order as cond_kernel;
 // shared memory holds only the block's new rows for the statistics epilogue.
 // ------------------------------------------------------------------------------------------
 template <int K, typename GT, typename AT>
@@ -302,9 +303,13 @@ template <typename GT, typename AT>
 static bool launch_cond_fixed(const CondParams &a, int n_blocks, cudaStream_t st)
 {
     switch (a.K) {
+    case 1: cond_kernel_k<1, GT, AT><<<n_blocks, kCondBlock, 0, st>>>(a); return true;
+    case 3: cond_kernel_k<3, GT, AT><<<n_blocks, kCondBlock, 0, st>>>(a); return true;
     case 4: cond_kernel_k<4, GT, AT><<<n_blocks, kCondBlock, 0, st>>>(a); return true;
     case 5: cond_kernel_k<5, GT, AT><<<n_blocks, kCondBlock, 0, st>>>(a); return true;
     case 10: cond_kernel_k<10, GT, AT><<<n_blocks, kCondBlock, 0, st>>>(a); return true;
+    case 11: cond_kernel_k<11, GT, AT><<<n_blocks, kCondBlock, 0, st>>>(a); return true;
+    case 12: cond_kernel_k<12, GT, AT><<<n_blocks, kCondBlock, 0, st>>>(a); return true;
     default: return false;
     }
 }
