@@ -31,6 +31,11 @@ __device__ __forceinline__ __nv_bfloat16 to_gather<__nv_bfloat16>(double x)
 }
 
 
+// Interleave stride of the per-thread shared-memory slots: one past the block size, so that the
+// statistics epilogue (thread e reading entry i of every row) touches a different bank for each
+// entry instead of the same bank for all.
+constexpr int kCondStride = kCondBlock + 1;
+
 // Shared-memory slots per thread: the packed matrix (ntri(K)), the right-hand side / solution
 // (K) and the reciprocal pivots (K).
 static inline int cond_slots(int K) { return ntri(K) + 2 * K; }
@@ -46,8 +51,8 @@ __global__ void __launch_bounds__(kCondBlock) cond_kernel(CondParams a)
     const int K = a.K;
     const int NT = ntri(K);
     const int64_t R = a.R;
-    double *M = sm + t;                       // M[e * kCondBlock] is entry e of this thread
-#define SM(e) M[(e) * kCondBlock]
+    double *M = sm + t;                       // M[e * kCondStride] is entry e of this thread
+#define SM(e) M[(e) * kCondStride]
     const int B0 = NT, RI = NT + K;           // rhs/solution at B0 + i, reciprocal pivot at RI + i
     bool ok = active;
     if (active) {
@@ -150,13 +155,13 @@ __global__ void __launch_bounds__(kCondBlock) cond_kernel(CondParams a)
     for (int e = t; e < NS; e += kCondBlock) {
         double s = 0.0;
         if (e < K) {
-            for (int q = 0; q < blk.n; ++q) s += sm[(B0 + e) * kCondBlock + q];
+            for (int q = 0; q < blk.n; ++q) s += sm[(B0 + e) * kCondStride + q];
         } else {
             int i = 0;
             while ((i + 1) * (i + 2) / 2 <= e - K) ++i;
             const int j = e - K - i * (i + 1) / 2;
             for (int q = 0; q < blk.n; ++q)
-                s = fma(sm[(B0 + i) * kCondBlock + q], sm[(B0 + j) * kCondBlock + q], s);
+                s = fma(sm[(B0 + i) * kCondStride + q], sm[(B0 + j) * kCondStride + q], s);
         }
         out[e] = s;
     }
@@ -175,7 +180,7 @@ template <int K, typename GT, typename AT>
 __global__ void __launch_bounds__(kCondBlock) cond_kernel_k(CondParams a)
 {
     constexpr int NT = ntri(K);
-    __shared__ double XS[K][kCondBlock];
+    __shared__ double XS[K][kCondStride];
     const int t = threadIdx.x;
     const CondBlock blk = a.blocks[blockIdx.x];
     const int64_t r = blk.row0 + t;
@@ -318,7 +323,7 @@ template <typename GT, typename AT>
 static void launch_cond_t(const CondParams &a, int n_blocks, cudaStream_t st)
 {
     if (launch_cond_fixed<GT, AT>(a, n_blocks, st)) return;
-    const size_t smem = (size_t)cond_slots(a.K) * kCondBlock * sizeof(double);
+    const size_t smem = (size_t)cond_slots(a.K) * kCondStride * sizeof(double);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(cond_kernel<GT, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
