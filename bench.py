@@ -103,6 +103,30 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------------
+# ranks (torchrun, one process per GPU): replicas of the workload, timed together
+# ---------------------------------------------------------------------------------------
+def barrier(world):
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+
+
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time (every rank gets it)."""
+    if world == 1:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, max_ms, world):
+    """Units all ranks processed per second of the slowest rank's time."""
+    return world * units_per_rank / (max_ms / 1e3)
+
+
+# ---------------------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------------------
 def load_workload(name, scale=1.0):
@@ -172,8 +196,7 @@ def run_ours(args, rank, world, local_rank):
     dr = torch.from_numpy(host).to(dev)
     m.sweep(0, W, dr[: W * per])
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    barrier(world)
     n0 = m.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local_rank) as clk:
@@ -185,10 +208,8 @@ def run_ours(args, rank, world, local_rank):
     ms = e0.elapsed_time(e1)
     launches = m.launch_count() - n0
     torch.cuda.synchronize()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    barrier(world)
+    ms = max_over_ranks(ms, world, dev)
     rmse_red = st["rmse_mean"]
     # ---- per-kernel timing over the same number of steps (profiling pass) ------------
     # one launch per kernel and half (no row chunks), so that each launch's event time is the
@@ -238,7 +259,7 @@ def run_ours(args, rank, world, local_rank):
         del drr
     if rank != 0:
         return None
-    sweeps_s = world * S / (ms / 1e3)
+    sweeps_s = whole_job_rate(S, ms, world)
     M = len(d["row"])
     gflops = 2 * M * 2 * K * K * sweeps_s / 1e9
     # roofline of the dominant kernel class
@@ -604,19 +625,20 @@ def main():
     pp = _synth.WORKLOADS.get(args.workload, {}).get("I", 1) > 1
     if args.impl == "reference":
         out = run_reference(args, rank)
-    elif pp:
-        out = run_pp(args, rank, world, local_rank)
-    elif MODES.get(args.workload) == "adjoint":
-        out = run_adjoint(args, rank, world, local_rank)
     else:
         if world > 1:
             import torch
             torch.cuda.set_device(local_rank)
             torch.distributed.init_process_group("nccl")
-        out = run_ours(args, rank, world, local_rank)
+        if pp:
+            out = run_pp(args, rank, world, local_rank)
+        elif MODES.get(args.workload) == "adjoint":
+            out = run_adjoint(args, rank, world, local_rank)
+        else:
+            out = run_ours(args, rank, world, local_rank)
         if world > 1:
+            barrier(world)
             import torch
-            torch.distributed.barrier()
             torch.distributed.destroy_process_group()
     if out is not None:
         print(json.dumps(out), flush=True)
