@@ -160,31 +160,37 @@ __global__ void __launch_bounds__(128) gram_wide_bf16(GramParams a)
         float acc[NTL][4];
 #pragma unroll
         for (int t = 0; t < NTL; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
-        // software pipeline: lane o holds in registers the row and value of observation
-        // o0 + 32 + o (gathered while the tensor cores work on step o0) and the index of
-        // observation o0 + 64 + o
-        uint4 nxt[KT / 8];
-        float ny = 0.f;
-        bool nvalid = lane < m.count;
+        // software pipeline: lane o holds in registers the rows and values of observation
+        // o0 + o + 32 d for the next D steps d = 0..D-1 (gathered while the tensor cores work on
+        // earlier steps) and the index of observation o0 + o + 32 D; D = 2 while the registers
+        // allow it (KT <= 48), else 1
+        constexpr int D = KT <= 48 ? 2 : 1;
+        uint4 nxt[D][KT / 8];
+        float ny[D];
+        bool nvalid[D];
         int cnext = 0;
-        {
-            const int c0 = nvalid ? __ldg(a.idx + m.begin + lane) : 0;
-            if (nvalid) {
-                ny = __ldg(val + m.begin + lane);
-                const uint4 *src = reinterpret_cast<const uint4 *>(P + (int64_t)c0 * a.ldP);
 #pragma unroll
-                for (int v = 0; v < KT / 8; ++v) nxt[v] = __ldg(src + v);
+        for (int dd = 0; dd < D; ++dd) {
+            const int od = dd * kWideObs + lane;
+            nvalid[dd] = od < m.count;
+            ny[dd] = 0.f;
+            const int cd = nvalid[dd] ? __ldg(a.idx + m.begin + od) : 0;
+            if (nvalid[dd]) {
+                ny[dd] = __ldg(val + m.begin + od);
+                const uint4 *src = reinterpret_cast<const uint4 *>(P + (int64_t)cd * a.ldP);
+#pragma unroll
+                for (int v = 0; v < KT / 8; ++v) nxt[dd][v] = __ldg(src + v);
             }
-            cnext = kWideObs + lane < m.count ? __ldg(a.idx + m.begin + kWideObs + lane) : 0;
         }
+        cnext = D * kWideObs + lane < m.count ? __ldg(a.idx + m.begin + D * kWideObs + lane) : 0;
         for (int o0 = 0; o0 < m.count; o0 += kWideObs) {
             // stage: lane o writes observation o0 + o (zero row past the end)
             __nv_bfloat16 *row = S + lane * LDS;
-            if (nvalid) {
+            if (nvalid[0]) {
 #pragma unroll
-                for (int v = 0; v < KT / 8; ++v) reinterpret_cast<uint4 *>(row)[v] = nxt[v];
-                const __nv_bfloat16 hi = __float2bfloat16_rn(ny);
-                const __nv_bfloat16 lo = __float2bfloat16_rn(ny - __bfloat162float(hi));
+                for (int v = 0; v < KT / 8; ++v) reinterpret_cast<uint4 *>(row)[v] = nxt[0][v];
+                const __nv_bfloat16 hi = __float2bfloat16_rn(ny[0]);
+                const __nv_bfloat16 lo = __float2bfloat16_rn(ny[0] - __bfloat162float(hi));
                 uint4 tail = make_uint4(0u, 0u, 0u, 0u);
                 tail.x = (uint32_t)__bfloat16_as_ushort(hi) | ((uint32_t)__bfloat16_as_ushort(lo) << 16);
                 reinterpret_cast<uint4 *>(row)[KT / 8] = tail;
@@ -194,13 +200,20 @@ __global__ void __launch_bounds__(128) gram_wide_bf16(GramParams a)
             }
             __syncwarp();
             {
-                const int o1 = o0 + kWideObs + lane;
-                nvalid = o1 < m.count;
-                if (nvalid) {
-                    ny = __ldg(val + m.begin + o1);
+#pragma unroll
+                for (int dd = 0; dd + 1 < D; ++dd) {
+                    nvalid[dd] = nvalid[dd + 1];
+                    ny[dd] = ny[dd + 1];
+#pragma unroll
+                    for (int v = 0; v < KT / 8; ++v) nxt[dd][v] = nxt[dd + 1][v];
+                }
+                const int o1 = o0 + D * kWideObs + lane;
+                nvalid[D - 1] = o1 < m.count;
+                if (nvalid[D - 1]) {
+                    ny[D - 1] = __ldg(val + m.begin + o1);
                     const uint4 *src = reinterpret_cast<const uint4 *>(P + (int64_t)cnext * a.ldP);
 #pragma unroll
-                    for (int v = 0; v < KT / 8; ++v) nxt[v] = __ldg(src + v);
+                    for (int v = 0; v < KT / 8; ++v) nxt[D - 1][v] = __ldg(src + v);
                 }
                 cnext = o1 + kWideObs < m.count ? __ldg(a.idx + m.begin + o1 + kWideObs) : 0;
             }
