@@ -46,7 +46,8 @@ class Pair:
                          beta0=self.prior.beta0, nu0=self.prior.nu0, mu0=self.prior.mu0,
                          W0_prior=self.prior.W0, center=center, order=order, **kw)
         self.p = oracle.plan(d["N"], d["D"], d["row"], d["col"], d["val"], I, J,
-                             order=order, center=center)
+                             order=order, center=center, row_bounds=kw.get("row_bounds"),
+                             col_bounds=kw.get("col_bounds"))
         self.X0 = d["X0"][self.p.row_perm]
         self.W0 = d["W0"][self.p.col_perm]
         self.finals = {}

@@ -171,3 +171,32 @@ def test_fault_injection_on_the_host():
         m.autotune(2, -1, 1)
     assert e.value.status == 8
     m.close()
+
+
+def test_pp_with_empty_subsets_and_zero_sweep_calls():
+    """A 2 x 2 grid whose off-diagonal blocks hold no observations (their chains sample the
+    prior and the propagated summaries), and calls of zero sweeps, against the oracle."""
+    d = small(N=120, D=100, M=3000, K=3, seed=31)
+    rb, cb = np.array([0, 60, 120]), np.array([0, 50, 100])
+    # keep only observations in the diagonal blocks of the original order, no reordering
+    keep = ((d["row"] < 60) & (d["col"] < 50)) | ((d["row"] >= 60) & (d["col"] >= 50))
+    for k in ("row", "col", "val"):
+        d[k] = d[k][keep]
+    tk = ((d["test_row"] < 60) & (d["test_col"] < 50)) | ((d["test_row"] >= 60) & (d["test_col"] >= 50))
+    for k in ("test_row", "test_col", "test_val"):
+        d[k] = d[k][tk]
+    pr = Pair(d, 3, I=2, J=2, burnin=2, order="none", row_bounds=rb, col_bounds=cb)
+    for s in pr.p.subsets:
+        if s.i != s.j:
+            assert s.nnz == 0
+    for stage in (1, 2, 3):
+        pr.m.stage(stage, 0, None)
+        pr.run_stage(stage, 8)
+        for s in pr.p.stage_subsets(stage):
+            pr.compare_subset(s.sid, rel=1e-7)
+        pr.finish_stage(stage)
+    Xm_o, Wm_o, nc_o = oracle.aggregate_plan(pr.p, pr.finals, 3)
+    Xm, Wm, nc = pr.m.posterior_means()
+    assert nc == nc_o
+    assert_rows_close(Xm, Xm_o, 1e-6, "aggregated X")
+    assert_rows_close(Wm, Wm_o, 1e-6, "aggregated W")
