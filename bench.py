@@ -64,11 +64,19 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
         return self
+
+    def wait_first(self, limit=3.0):
+        """Block until the sampler has written its first line (or `limit` seconds)."""
+        t_end = time.time() + limit
+        while self.proc and self.path and time.time() < t_end:
+            if os.path.getsize(self.path) > 0:
+                return
+            time.sleep(0.02)
 
     def __exit__(self, *exc):
         if self.proc:
@@ -194,19 +202,27 @@ def run_ours(args, rank, world, local_rank):
     host = make_draws(d, K, nu0, W + S, seed=100 + rank)
     assert host.size == per * (W + S)
     dr = torch.from_numpy(host).to(dev)
+    # clock samples (nvidia-smi, every 100 ms) from the warm-up through the timed region and
+    # 0.3 s of the same (untimed) sweeps after it, so that a short timed region still has
+    # samples taken under the same load
+    clk = ClockSampler(local_rank).__enter__()
+    clk.wait_first()
     m.sweep(0, W, dr[: W * per])
     torch.cuda.synchronize()
     barrier(world)
     n0 = m.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local_rank) as clk:
-        torch.cuda.synchronize()
-        e0.record(stream)
-        st = m.sweep(0, S, dr[W * per:(W + S) * per])
-        e1.record(stream)
-        e1.synchronize()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    st = m.sweep(0, S, dr[W * per:(W + S) * per])
+    e1.record(stream)
+    e1.synchronize()
     ms = e0.elapsed_time(e1)
     launches = m.launch_count() - n0
+    t_end = time.perf_counter() + 0.3
+    while time.perf_counter() < t_end:
+        m.sweep(0, S, dr[W * per:(W + S) * per])
+    clk.__exit__(None, None, None)
     torch.cuda.synchronize()
     barrier(world)
     ms = max_over_ranks(ms, world, dev)
