@@ -179,9 +179,14 @@ __device__ __forceinline__ void gram_task(const GramParams &a, const GramTask &t
     const int64_t item = tk.item0 + (has ? g : 0);
     const GramItem m = a.items[item - a.item0];
     const int cnt = has ? m.count : 0;
-    AT acc[EP];
+    // accumulators of this group width: the entries rounded up to a multiple of G (the
+    // reduce-scatter halves the set log2(G) times), not to the part width, when one part holds
+    // all of them
+    constexpr int NV = gram_nv(KT);
+    constexpr int EPG = NV <= EP ? (NV + G - 1) / G * G : EP;
+    AT acc[EPG];
 #pragma unroll
-    for (int v = 0; v < EP; ++v) acc[v] = AT(0);
+    for (int v = 0; v < EPG; ++v) acc[v] = AT(0);
     // two observations per lane per iteration (lane order li, li+G, li+2G, ... is kept), so
     // that two gathers are in flight before either is consumed
     int e = li;
@@ -192,8 +197,8 @@ __device__ __forceinline__ void gram_task(const GramParams &a, const GramTask &t
         AT w0[KT], w1[KT];
         load_row<KT>(P + (int64_t)c0 * a.ldP, w0);
         load_row<KT>(P + (int64_t)c1 * a.ldP, w1);
-        accum_all<KT, EP, PART * EP, 0, AT>(acc, w0, y0);
-        accum_all<KT, EP, PART * EP, 0, AT>(acc, w1, y1);
+        accum_all<KT, EPG, PART * EP, 0, AT>(acc, w0, y0);
+        accum_all<KT, EPG, PART * EP, 0, AT>(acc, w1, y1);
     }
     if (e < cnt) {
         const int64_t q = m.begin + e;
@@ -201,10 +206,10 @@ __device__ __forceinline__ void gram_task(const GramParams &a, const GramTask &t
         const AT y = __ldg(val + q);
         AT w[KT];
         load_row<KT>(P + (int64_t)c * a.ldP, w);
-        accum_all<KT, EP, PART * EP, 0, AT>(acc, w, y);
+        accum_all<KT, EPG, PART * EP, 0, AT>(acc, w, y);
     }
-    rs_group<EP, G / 2, EP, AT>(acc, lane);
-    constexpr int PER = EP / G;
+    rs_group<EPG, G / 2, EPG, AT>(acc, lane);
+    constexpr int PER = EPG / G;
     if (has) {
         AT *dst = part + (item - a.item0) * (int64_t)a.ld + PART * EP + li * PER;
 #pragma unroll
