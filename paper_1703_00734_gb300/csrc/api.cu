@@ -129,6 +129,8 @@ struct bmf_ctx {
     int64_t stats_cap = 0;           // chunks
     HyperJob *d_jobs = nullptr;
     HyperJob *d_jobs2 = nullptr;     // the same jobs over the first-level partials
+    std::vector<HyperJob> jobs_up;   // the job list last uploaded (skip identical uploads)
+    std::vector<char> stats_ok;      // [S] per slot: c->stats hold the statistics of its state
     double *stats2 = nullptr;        // [2 S x kStatParts x (K + ntri(K))] first-level partials
     double *mu0_d = nullptr, *W0inv_d = nullptr;
     int32_t *trow = nullptr, *tcol = nullptr;
@@ -668,10 +670,11 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
     }
     if ((int64_t)jobs.size() > kHyperJobsMax)
         return fail(c, BMF_E_ARG, "internal: too many hyperparameter jobs");
-    if (!jobs.empty())
+    const bool same_jobs = jobs.size() == c->jobs_up.size() &&
+                           std::memcmp(jobs.data(), c->jobs_up.data(), jobs.size() * sizeof(HyperJob)) == 0;
+    if (!jobs.empty() && !same_jobs) {
         CUDA_TRY(c, cudaMemcpyAsync(c->d_jobs, jobs.data(), jobs.size() * sizeof(HyperJob),
                                     cudaMemcpyHostToDevice, c->st));
-    if (!jobs.empty()) {
         std::vector<HyperJob> jobs2(jobs);
         for (size_t q = 0; q < jobs2.size(); ++q) {
             jobs2[q].chunk0 = (int32_t)(q * kStatParts);
@@ -679,6 +682,7 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
         }
         CUDA_TRY(c, cudaMemcpyAsync(c->d_jobs2, jobs2.data(), jobs2.size() * sizeof(HyperJob),
                                     cudaMemcpyHostToDevice, c->st));
+        c->jobs_up = jobs;
     }
     const int64_t hyper_len = 2 * (int64_t)(sl1 - sl0) * HB;
     const int64_t zx_len = (rx1 - rx0) * K;
@@ -724,12 +728,14 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
         capture.active = true;
     }
     if (n_sweeps > 0 && (hyp[0] || hyp[1])) {
-        // statistics of the state at the start of the call (the conditional kernel keeps them
-        // current from then on)
+        // statistics of the state at the start of the call, unless the last sweep of these
+        // slots left them current (the conditional kernel keeps them current from then on)
         CUDA_TRY(c, cudaEventRecord(c->ev_fork, c->st));
         CUDA_TRY(c, cudaStreamWaitEvent(c->st2, c->ev_fork, 0));
+        bool current = true;
+        for (int sl = sl0; sl < sl1; ++sl) current = current && c->stats_ok[sl];
         for (int f = 0; f < 2; ++f) {
-            if (!hyp[f]) continue;
+            if (!hyp[f] || current) continue;
             const Side &sd = f == 0 ? c->X : c->W;
             const int64_t b0 = sd.slot_blk[sl0], b1 = sd.slot_blk[sl1];
             traced(c, c->st2, K_STATS, 1, [&] {
@@ -739,6 +745,8 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
         for (int f = 0; f < 2; ++f)
             if (hyp[f] && (s = side_hyper(f, 0))) return s;
     }
+    // from here the batch's statistics are in flux until the call completes
+    for (int sl = sl0; sl < sl1 && n_sweeps > 0; ++sl) c->stats_ok[sl] = 0;
     for (int it = 0; it < n_sweeps; ++it) {
         const double *d = draws_of(it);
         const int64_t t = t_start + it + 1;
@@ -946,8 +954,11 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
         su.t = t_start + n_sweeps;
         su.kept = kept;
         su.finalized = false;
+        if (n_sweeps > 0) c->stats_ok[sl] = 1;
     }
     s = check_dev_error(c);
+    if (s)
+        for (int sl = sl0; sl < sl1; ++sl) c->stats_ok[sl] = 0;
     if (c->prof) collect_profile(c);
     if (s) return s;
     if (stats) {
@@ -1005,6 +1016,7 @@ bmf_status install_prior_from(bmf_ctx *c, int dst_sid, int f, int src_sid)
                   sd.mm_mu, sd.mm_L, sd.mm_b, sd.pL, sd.pb, sd.F, sd.G, c->ldg, c->prec};
     launch_propagate(pp, c->st);
     c->ss[dst_sid].prior[f] = 1;
+    c->stats_ok[gd.slot] = 0;    // the propagated factor starts at the propagated mean
     refresh_hslots(c, gd.slot);
     return upload_hslots(c, gd.slot);
 }
@@ -1335,6 +1347,7 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
     launch_fill_gather(K, c->prec, c->P.RX, c->X.F, c->X.G, c->ldg, c->st);
     launch_fill_gather(K, c->prec, c->P.RW, c->W.F, c->W.G, c->ldg, c->st);
     c->ss.assign(S, SubState());
+    c->stats_ok.assign(S, 0);
     for (int sl = 0; sl < S; ++sl) {
         refresh_hslots(c, sl);
         s = upload_hslots(c, sl);
@@ -1475,6 +1488,7 @@ bmf_status bmf_autotune(bmf_ctx *c, int32_t stage, int32_t subset, int32_t sweep
         }
         c->ss = snap.ss;
         bmf_status rs = snap.restore(c);
+        for (int sl = sl0; sl < sl1; ++sl) c->stats_ok[sl] = 0;   // statistics of a trial
         return st ? st : rs;
     };
     bmf_schedule best = keep;
@@ -1686,6 +1700,7 @@ bmf_status bmf_set_state(bmf_ctx *c, int32_t subset, const double *X, const doub
     CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
     c->failed = false;
+    c->stats_ok[g.slot] = 0;
     return BMF_OK;
 }
 
