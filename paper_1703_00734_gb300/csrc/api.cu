@@ -94,11 +94,12 @@ struct bmf_ctx {
                 cudaStreamDestroy(x);
             }
         for (cudaEvent_t e : {ev_fork, ev_fac[0], ev_fac[1], ev_hyp[0], ev_hyp[1], ev_cdone, ev_tail,
-                              ev_tail2, ev_rmse, ev_gen[0], ev_gen[1]})
+                              ev_tail2, ev_rmse, ev_gen[0], ev_gen[1], ev_copy})
             if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : ev_chunk)
             if (e) cudaEventDestroy(e);
         if (gexec) cudaGraphExecDestroy(gexec);
+        if (rb) cudaFreeHost(rb);
     }
     int K = 0, prec = BMF_FP64;
     double tau = 1.0, beta0 = 2.0, nu0 = 1.0, eps_rel = 1e-6;
@@ -116,6 +117,11 @@ struct bmf_ctx {
     cudaEvent_t ev_fork = nullptr, ev_fac[2] = {nullptr, nullptr}, ev_hyp[2] = {nullptr, nullptr};
     cudaEvent_t ev_chunk[kMaxChunks] = {}, ev_cdone = nullptr;
     cudaEvent_t ev_tail = nullptr, ev_tail2 = nullptr, ev_rmse = nullptr, ev_gen[2] = {nullptr, nullptr};
+    cudaEvent_t ev_copy = nullptr;   // host draw buffer on the device (copied on the generator stream)
+    struct Readback {
+        DevError err;
+        double rmse[2];
+    } *rb = nullptr;                 // pinned host block: the end-of-call readback
     bmf_schedule sched = {1, 1, 4, 0.0, 0};
     cudaGraphExec_t gexec = nullptr;  // the last captured sweep loop (graph schedule)
     int device = 0, sms = 1;
@@ -330,6 +336,8 @@ bmf_status upload_hslots(bmf_ctx *c, int sl)
     return BMF_OK;
 }
 
+bmf_status dev_error_status(bmf_ctx *c, const DevError &h);
+
 bmf_status check_dev_error(bmf_ctx *c)
 {
     if (c->st2) CUDA_TRY(c, cudaStreamSynchronize(c->st2));
@@ -339,6 +347,12 @@ bmf_status check_dev_error(bmf_ctx *c)
     DevError h;
     CUDA_TRY(c, cudaMemcpyAsync(&h, c->err_d, sizeof(h), cudaMemcpyDeviceToHost, c->st));
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    return dev_error_status(c, h);
+}
+
+// Status of a device error word read back to the host (clears the word on the device).
+bmf_status dev_error_status(bmf_ctx *c, const DevError &h)
+{
     if (h.flags) {
         DevError z = {0u, INT32_MAX};
         cudaMemcpy(c->err_d, &z, sizeof(z), cudaMemcpyHostToDevice);
@@ -481,7 +495,8 @@ bmf_status setup_side(bmf_ctx *c, Side &s, int64_t R, const std::vector<int64_t>
 }
 
 // Draw buffer of a call on the device.
-bmf_status stage_draws(bmf_ctx *c, const bmf_draws *d, int64_t need, const double **out)
+bmf_status stage_draws(bmf_ctx *c, const bmf_draws *d, int64_t need, const double **out,
+                       cudaStream_t copy_st)
 {
     if (!d) {
         *out = nullptr;   // the device generator fills the sweep buffers
@@ -503,7 +518,7 @@ bmf_status stage_draws(bmf_ctx *c, const bmf_draws *d, int64_t need, const doubl
         c->draws_cap = need;
     }
     CUDA_TRY(c, cudaMemcpyAsync(c->draws_d, d->ptr, need * sizeof(double), cudaMemcpyHostToDevice,
-                                c->st));
+                                copy_st));
     *out = c->draws_d;
     return BMF_OK;
 }
@@ -625,8 +640,22 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
     const int64_t tt0 = g0.test_off, tt1 = gl.test_off + gl.n_test;
     const int64_t per = per_sweep_draws(c, sl0, sl1);
     const double *dr = nullptr;
-    bmf_status s = stage_draws(c, draws, per * n_sweeps, &dr);
+    const bool use_graph = c->sched.graph && !c->prof && n_sweeps > 0;
+    // host draw buffers are copied on the generator stream (idle with host draws), so that the
+    // first Gram pass, which needs no draws, starts at once; the first readers wait for it
+    const bool copy_async = draws && !draws->on_device && !use_graph && n_sweeps > 0;
+    bmf_status s = stage_draws(c, draws, per * n_sweeps, &dr, copy_async ? c->st5 : c->st);
     if (s) return s;
+    // the caller's host buffer is read until the copy completes: never return before that
+    struct CopyWait {
+        cudaStream_t st;
+        bool on;
+        ~CopyWait()
+        {
+            if (on) cudaStreamSynchronize(st);
+        }
+    } copy_wait{c->st5, copy_async};
+    if (copy_async) CUDA_TRY(c, cudaEventRecord(c->ev_copy, c->st5));
     // with the device generator, sweep it's draws live in ring buffer it % 2: the main stream
     // fills sweep it + 2 after sweep it's conditionals, which are ordered after every reader
     // of that buffer (the side stream's hyperparameter draw of sweep it finishes before them)
@@ -709,7 +738,6 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
     // CUDA graph and launched once (the executable graph is kept and updated in place when the
     // next call has the same shape)
     CaptureGuard capture;
-    const bool use_graph = c->sched.graph && !c->prof && n_sweeps > 0;
     if (use_graph) {
         capture.c = c;
         capture.user = c->st;
@@ -732,6 +760,7 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
         // slots left them current (the conditional kernel keeps them current from then on)
         CUDA_TRY(c, cudaEventRecord(c->ev_fork, c->st));
         CUDA_TRY(c, cudaStreamWaitEvent(c->st2, c->ev_fork, 0));
+        if (copy_async) CUDA_TRY(c, cudaStreamWaitEvent(c->st2, c->ev_copy, 0));
         bool current = true;
         for (int sl = sl0; sl < sl1; ++sl) current = current && c->stats_ok[sl];
         for (int f = 0; f < 2; ++f) {
@@ -808,6 +837,7 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
                 // the previous sweep's RMSE pass reads the gathered copies this sweep rewrites;
                 // the generator fills this sweep's draws on the tail stream
                 if (it > 0 && tt1 > tt0) CUDA_TRY(c, cudaStreamWaitEvent(cs, c->ev_rmse, 0));
+                if (it == 0 && copy_async) CUDA_TRY(c, cudaStreamWaitEvent(cs, c->ev_copy, 0));
                 if (gen && it >= 2) CUDA_TRY(c, cudaStreamWaitEvent(cs, c->ev_gen[it & 1], 0));
             }
             if (nch == 1) {
@@ -956,7 +986,14 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
         su.finalized = false;
         if (n_sweeps > 0) c->stats_ok[sl] = 1;
     }
-    s = check_dev_error(c);
+    // every stream of the call has joined the context stream: one readback, one synchronisation
+    const bool want_rmse = stats && tt1 > tt0 && n_sweeps > 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&c->rb->err, c->err_d, sizeof(DevError), cudaMemcpyDeviceToHost, c->st));
+    if (want_rmse)
+        CUDA_TRY(c, cudaMemcpyAsync(c->rb->rmse, c->rmse_out, 2 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    s = dev_error_status(c, c->rb->err);
     if (s)
         for (int sl = sl0; sl < sl1; ++sl) c->stats_ok[sl] = 0;
     if (c->prof) collect_profile(c);
@@ -965,12 +1002,10 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
         stats->sweeps = t_start + n_sweeps;
         stats->kept = kept;
         stats->rmse_sample = stats->rmse_mean = NAN;
-        if (tt1 > tt0 && n_sweeps > 0) {
-            double h[2];
-            CUDA_TRY(c, cudaMemcpy(h, c->rmse_out, sizeof(h), cudaMemcpyDeviceToHost));
+        if (want_rmse) {
             const double n = (double)(tt1 - tt0);
-            stats->rmse_sample = std::sqrt(h[0] / n);
-            if (kept > 0) stats->rmse_mean = std::sqrt(h[1] / n);
+            stats->rmse_sample = std::sqrt(c->rb->rmse[0] / n);
+            if (kept > 0) stats->rmse_mean = std::sqrt(c->rb->rmse[1] / n);
         }
     }
     return BMF_OK;
@@ -1243,10 +1278,11 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
         ok = ok && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) == cudaSuccess;
         for (cudaEvent_t *e : {&c->ev_fork, &c->ev_fac[0], &c->ev_fac[1], &c->ev_hyp[0], &c->ev_hyp[1],
                                &c->ev_cdone, &c->ev_tail, &c->ev_tail2, &c->ev_rmse, &c->ev_gen[0],
-                               &c->ev_gen[1]})
+                               &c->ev_gen[1], &c->ev_copy})
             ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
         for (cudaEvent_t &e : c->ev_chunk)
             ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+        ok = ok && cudaMallocHost(&c->rb, sizeof(*c->rb)) == cudaSuccess;
         if (!ok) return bail(BMF_E_CUDA, "stream/event creation failed");
     }
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
