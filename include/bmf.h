@@ -110,7 +110,7 @@ enum { BMF_FACTOR_X = 0, BMF_FACTOR_W = 1 };
 #define BMF_MAX_K 64
 
 typedef struct {
-    int32_t K;         /* latent dimension, 1..BMF_MAX_K (Gibbs sweeps: K <= 16 in this build) */
+    int32_t K;         /* latent dimension, 1..BMF_MAX_K */
     int32_t precision; /* BMF_FP64 / BMF_FP32 / BMF_BF16 */
     double tau;        /* noise precision (Eq. 3), > 0 */
     double beta0;      /* Normal-Wishart beta0 > 0 */
