@@ -1982,7 +1982,7 @@ bmf_status logjoint(bmf_ctx *c, int32_t subset, const float *X, const float *W, 
         ap.alpha = alpha;
         ap.count_r2 = f == 0 ? 1 : 0;
         ap.block_sums = c->adj_sums + (f == 0 ? 0 : 2 * nb[0]);
-        traced(c, c->st, K_ADJ, 2, [&] { launch_adjoint(ap, c->sms * 4, c->st); });
+        traced(c, c->st, K_ADJ, 2, [&] { launch_adjoint(ap, c->sms * 8, c->st); });
     }
     CUDA_TRY(c, cudaGetLastError());
     std::vector<double> h(2 * (nb[0] + nb[1]));

@@ -85,7 +85,8 @@ def _close_rows(g, ref, rel, what):
     assert err < rel, f"{what}: worst relative error {err:.2e}"
 
 
-@pytest.mark.parametrize("K,with_sweep", [(5, True), (16, True), (10, False), (64, False)])
+@pytest.mark.parametrize("K,with_sweep", [(5, True), (16, True), (10, False), (20, True), (40, False),
+                                           (64, False), (64, True)])
 def test_logjoint_grad_matches_oracle(K, with_sweep):
     torch, bmf, m, s, X, W, ld, prior = _setup(K, with_sweep)
     la = np.log(1 / 0.09)
