@@ -12,7 +12,7 @@
 // item (at most 1024 observations of one row).  K <= 16: lanes over observations, each lane
 // gathers its partner row twice (dot product, then accumulation) and a butterfly
 // reduce-scatter writes the item's K gradient entries and its sum of r^2.  K > 16: groups of
-// K/4 lanes (rounded up to 8 or 16) per observation, four features per lane, so that a partner
+// 4 (K <= 32) or 8 (K <= 64) lanes per observation, eight features per lane, so that a partner
 // row is read once, as consecutive 16-byte pieces; the dot product is reduced within the group
 // and the gradient partial across the groups at the end of the item.  Pass 2: one warp per row
 // (lanes over features) sums the row's item partials in item order and adds the prior term,
@@ -101,58 +101,75 @@ __global__ void __launch_bounds__(256) adjoint_items_kernel(AdjointParams a)
     }
 }
 
-// Pass 1 for K > 16 (KT = 32 or 64): G = KT / 4 lanes per observation, 32 / G observations per
-// warp step and two steps in flight.  Lane li of a group owns features 4 li .. 4 li + 3; a lane
-// whose first feature is past K loads nothing (rows are 16-byte aligned with a pitch that is a
-// multiple of 4 floats and at least K, so every piece a lane does load lies inside its row).
+// Pass 1 for K > 16 (KT = 32 or 64): F = 8 features per lane, G = KT / F lanes per
+// observation, 32 / G observations per warp step and two steps in flight.  Lane li of a group
+// owns features 8 li .. 8 li + 7 as two 16-byte pieces; a piece whose first feature is past K
+// is not loaded (rows are 16-byte aligned with a pitch that is a multiple of 4 floats and at
+// least K, so every piece that is loaded lies inside its row).
 template <int KT>
 __global__ void __launch_bounds__(256) adjoint_items_grouped_kernel(AdjointParams a)
 {
-    constexpr int G = KT / 4, NG = 32 / G, LD = (KT + 1 + 31) / 32 * 32;
-    static_assert(G * NG == 32, "group width must divide the warp");
+    constexpr int F = 8, PC = F / 4, G = KT / F, NG = 32 / G, LD = (KT + 1 + 31) / 32 * 32;
+    static_assert(G * NG == 32 && G * F == KT, "group shape");
     const int lane = threadIdx.x & 31, g = lane / G, li = lane % G;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int K = a.K, f0 = 4 * li;
-    const bool mine = f0 < K;
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int K = a.K, f0 = F * li;
     for (int64_t it = warp; it < a.n_items; it += nw) {
         const GramItem m = a.items[it];
-        float4 x = zero;
-        if (mine) {
-            x = __ldg(reinterpret_cast<const float4 *>(a.self + (int64_t)(m.row - a.self0) * a.ld + f0));
-            if (f0 + 1 >= K) x.y = 0.f;
-            if (f0 + 2 >= K) x.z = 0.f;
-            if (f0 + 3 >= K) x.w = 0.f;
+        float x[F];
+        const float *xs = a.self + (int64_t)(m.row - a.self0) * a.ld + f0;
+#pragma unroll
+        for (int j = 0; j < PC; ++j) {
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (f0 + 4 * j < K) q = __ldg(reinterpret_cast<const float4 *>(xs + 4 * j));
+            x[4 * j] = q.x;
+            x[4 * j + 1] = q.y;
+            x[4 * j + 2] = q.z;
+            x[4 * j + 3] = q.w;
         }
-        float4 acc = zero;
+#pragma unroll
+        for (int f = 0; f < F; ++f)
+            if (f0 + f >= K) x[f] = 0.f;   // padding of the caller's rows is not read as data
+        float acc[F];
+#pragma unroll
+        for (int f = 0; f < F; ++f) acc[f] = 0.f;
         float r2 = 0.f;
         for (int e0 = 0; e0 < m.count; e0 += 2 * NG) {
             const int ea = e0 + g, eb = e0 + NG + g;
             const bool va = ea < m.count, vb = eb < m.count;
-            float ya = 0.f, yb = 0.f;
-            float4 pa = zero, pb = zero;
+            float ya = 0.f, yb = 0.f, pa[F], pb[F];
+            const float *ra_row = nullptr, *rb_row = nullptr;
             if (va) {
                 const int64_t q = m.begin + ea;
                 ya = __ldg(a.val + q);
-                if (mine)
-                    pa = __ldg(reinterpret_cast<const float4 *>(
-                        a.other + (int64_t)(__ldg(a.idx + q) - a.other0) * a.ld + f0));
+                ra_row = a.other + (int64_t)(__ldg(a.idx + q) - a.other0) * a.ld + f0;
             }
             if (vb) {
                 const int64_t q = m.begin + eb;
                 yb = __ldg(a.val + q);
-                if (mine)
-                    pb = __ldg(reinterpret_cast<const float4 *>(
-                        a.other + (int64_t)(__ldg(a.idx + q) - a.other0) * a.ld + f0));
+                rb_row = a.other + (int64_t)(__ldg(a.idx + q) - a.other0) * a.ld + f0;
             }
-            float da = x.x * pa.x, db = x.x * pb.x;
-            da = fmaf(x.y, pa.y, da);
-            db = fmaf(x.y, pb.y, db);
-            da = fmaf(x.z, pa.z, da);
-            db = fmaf(x.z, pb.z, db);
-            da = fmaf(x.w, pa.w, da);
-            db = fmaf(x.w, pb.w, db);
+#pragma unroll
+            for (int j = 0; j < PC; ++j) {
+                float4 u = make_float4(0.f, 0.f, 0.f, 0.f), v = u;
+                if (va && f0 + 4 * j < K) u = __ldg(reinterpret_cast<const float4 *>(ra_row + 4 * j));
+                if (vb && f0 + 4 * j < K) v = __ldg(reinterpret_cast<const float4 *>(rb_row + 4 * j));
+                pa[4 * j] = u.x;
+                pa[4 * j + 1] = u.y;
+                pa[4 * j + 2] = u.z;
+                pa[4 * j + 3] = u.w;
+                pb[4 * j] = v.x;
+                pb[4 * j + 1] = v.y;
+                pb[4 * j + 2] = v.z;
+                pb[4 * j + 3] = v.w;
+            }
+            float da = 0.f, db = 0.f;
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                da = fmaf(x[f], pa[f], da);
+                db = fmaf(x[f], pb[f], db);
+            }
 #pragma unroll
             for (int o = G / 2; o >= 1; o >>= 1) {
                 da += __shfl_xor_sync(0xffffffffu, da, o);
@@ -160,80 +177,83 @@ __global__ void __launch_bounds__(256) adjoint_items_grouped_kernel(AdjointParam
             }
             // past the end of the item y = 0 and p = 0, so r = 0 adds nothing
             const float ra = ya - da, rb = yb - db;
-            acc.x = fmaf(ra, pa.x, acc.x);
-            acc.y = fmaf(ra, pa.y, acc.y);
-            acc.z = fmaf(ra, pa.z, acc.z);
-            acc.w = fmaf(ra, pa.w, acc.w);
-            acc.x = fmaf(rb, pb.x, acc.x);
-            acc.y = fmaf(rb, pb.y, acc.y);
-            acc.z = fmaf(rb, pb.z, acc.z);
-            acc.w = fmaf(rb, pb.w, acc.w);
-            r2 = fmaf(ra, ra, r2);
-            r2 = fmaf(rb, rb, r2);
+#pragma unroll
+            for (int f = 0; f < F; ++f) acc[f] = fmaf(rb, pb[f], fmaf(ra, pa[f], acc[f]));
+            r2 = fmaf(rb, rb, fmaf(ra, ra, r2));
         }
         // sum over the groups (every lane of a group holds the group's r^2)
 #pragma unroll
         for (int o = G; o < 32; o <<= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-            acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
-            acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+#pragma unroll
+            for (int f = 0; f < F; ++f) acc[f] += __shfl_xor_sync(0xffffffffu, acc[f], o);
             r2 += __shfl_xor_sync(0xffffffffu, r2, o);
         }
         if (g == 0) {
-            float *dst = a.part + it * (int64_t)LD;
-            *reinterpret_cast<float4 *>(dst + f0) = acc;
-            if (li == 0) dst[KT] = r2;
+            float *dst = a.part + it * (int64_t)LD + f0;
+#pragma unroll
+            for (int j = 0; j < PC; ++j)
+                *reinterpret_cast<float4 *>(dst + 4 * j) =
+                    make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
+            if (li == 0) a.part[it * (int64_t)LD + KT] = r2;
         }
     }
 }
 
 // Pass 2: one warp per local row of the self factor (kAdjRows rows per block, lanes over the
 // features).  The prior precision and Lambda mu of the hyperparameter slot of the block's first
-// row are staged as FP32 in shared memory (all rows of one side of a subset share it); a row
-// with another slot reads and converts its prior from global memory.
+// row are staged as FP32 in shared memory, zero-padded to KT columns (all rows of one side of a
+// subset share the slot); a row with another slot, or with its own propagated prior, reads and
+// converts its prior from global memory.
 constexpr int kAdjRows = 128;
-constexpr int kAdjWarps = 4;
+constexpr int kAdjWarps = 8;
 
+template <int KT>
 __global__ void __launch_bounds__(32 * kAdjWarps) adjoint_rows_kernel(AdjointParams a)
 {
-    extern __shared__ float adj_sm[];
-    const int K = a.K, KT = a.kt, LD = a.ldp, KP = K | 1;   // odd pitch: no bank conflicts
-    float *Lf = adj_sm, *bf = Lf + K * KP, *xs = bf + K;     // Lf [K][KP], bf [K], xs [warps][KT]
+    constexpr int KP = KT + 1;    // odd pitch: lanes reading one column hit distinct banks
+    __shared__ float Lf[KT * KP], bf[KT], xs[kAdjWarps][KT];
+    const int K = a.K, LD = a.ldp;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n0 = (int64_t)blockIdx.x * kAdjRows;
     const int64_t n1 = min(n0 + (int64_t)kAdjRows, a.n_rows);
     const int hb = a.row_hslot[a.self0 + n0];
     if (hb >= 0) {
         const double *hp = a.hyper + (int64_t)hb * hyper_slot_len(K);
-        for (int q = threadIdx.x; q < K * K; q += blockDim.x) {
-            const int i = q / K, k = q % K;
-            Lf[i * KP + k] = (float)hp[K + (i >= k ? tri(i, k) : tri(k, i))];
+        for (int q = threadIdx.x; q < KT * KT; q += blockDim.x) {
+            const int i = q / KT, k = q % KT;
+            Lf[i * KP + k] = (i < K && k < K) ? (float)hp[K + (i >= k ? tri(i, k) : tri(k, i))] : 0.f;
         }
-        for (int q = threadIdx.x; q < K; q += blockDim.x) bf[q] = (float)hp[K + ntri(K) + q];
+        for (int q = threadIdx.x; q < KT; q += blockDim.x) bf[q] = q < K ? (float)hp[K + ntri(K) + q] : 0.f;
     }
     __syncthreads();
-    float *xw = xs + warp * KT;
+    float *xw = xs[warp];
     double r2 = 0.0, quad = 0.0;
     for (int64_t n = n0 + warp; n < n1; n += kAdjWarps) {
         const int64_t row = a.self0 + n;
         const int64_t i0 = a.item_ptr[row], i1 = a.item_ptr[row + 1];
         const float *x = a.self + n * a.ld;
         float *g = a.grad + n * a.ld;
-        for (int k = lane; k < K; k += 32) xw[k] = x[k];
+        for (int k = lane; k < KT; k += 32) xw[k] = k < K ? x[k] : 0.f;
         __syncwarp();
         const int h = a.row_hslot[row];
-        const double *hp = h >= 0 ? a.hyper + (int64_t)h * hyper_slot_len(K) : nullptr;
         float qlane = 0.f;
         for (int i = lane; i < K; i += 32) {
             float s = 0.f;
             for (int64_t it = i0; it < i1; ++it) s += a.part[(it - a.item_base) * (int64_t)LD + i];
             // prior term L (x - mu) = L x - b, in FP32 like the data term
-            float lx = 0.f, b;
+            float lx, b;
             if (h == hb && h >= 0) {
-                for (int k = 0; k < K; ++k) lx = fmaf(Lf[i * KP + k], xw[k], lx);
+                float l0 = 0.f, l1 = 0.f;
+#pragma unroll
+                for (int k = 0; k < KT; k += 2) {
+                    l0 = fmaf(Lf[i * KP + k], xw[k], l0);
+                    l1 = fmaf(Lf[i * KP + k + 1], xw[k + 1], l1);
+                }
+                lx = l0 + l1;
                 b = bf[i];
             } else {
+                const double *hp = h >= 0 ? a.hyper + (int64_t)h * hyper_slot_len(K) : nullptr;
+                lx = 0.f;
                 for (int k = 0; k < K; ++k) {
                     const int e = i >= k ? tri(i, k) : tri(k, i);
                     const float l = (float)(hp ? hp[K + e] : a.prior_L[(int64_t)e * a.R + row]);
@@ -294,8 +314,15 @@ void launch_adjoint(const AdjointParams &a, int grid, cudaStream_t st)
         }
     }
     if (a.n_rows > 0) {
-        const size_t smem = ((size_t)a.K * (a.K | 1) + a.K + (size_t)kAdjWarps * a.kt) * sizeof(float);
-        adjoint_rows_kernel<<<(int)((a.n_rows + kAdjRows - 1) / kAdjRows), 32 * kAdjWarps, smem, st>>>(a);
+        const int blocks = (int)((a.n_rows + kAdjRows - 1) / kAdjRows);
+        switch (a.kt) {
+        case 4: adjoint_rows_kernel<4><<<blocks, 32 * kAdjWarps, 0, st>>>(a); break;
+        case 8: adjoint_rows_kernel<8><<<blocks, 32 * kAdjWarps, 0, st>>>(a); break;
+        case 12: adjoint_rows_kernel<12><<<blocks, 32 * kAdjWarps, 0, st>>>(a); break;
+        case 16: adjoint_rows_kernel<16><<<blocks, 32 * kAdjWarps, 0, st>>>(a); break;
+        case 32: adjoint_rows_kernel<32><<<blocks, 32 * kAdjWarps, 0, st>>>(a); break;
+        default: adjoint_rows_kernel<64><<<blocks, 32 * kAdjWarps, 0, st>>>(a); break;
+        }
     }
 }
 
