@@ -180,7 +180,6 @@ struct bmf_ctx {
 namespace {
 
 constexpr int kHyperJobsMax = 1 << 16;
-constexpr int kSweepMaxK = 64;
 constexpr int kNarrowMaxK = 16;   // CUDA-core Gram pass up to here, tensor cores beyond
 constexpr int kTeamMinK = 13;     // conditional: one thread per row below, a team per row from here
 
@@ -626,9 +625,6 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
 {
     if (c->failed) return fail(c, BMF_E_STATE, "context is in a failed state; call bmf_set_state");
     if (n_sweeps < 0) return fail(c, BMF_E_ARG, "n_sweeps < 0");
-    if (c->K > kSweepMaxK)
-        return fail(c, BMF_E_ARG, "Gibbs sweeps support K <= " + std::to_string(kSweepMaxK) +
-                                      " in this build (the adjoint supports K <= 64)");
     const int K = c->K;
     const SubsetGeom &g0 = geom_of_slot(c, sl0), &gl = geom_of_slot(c, sl1 - 1);
     const int64_t t_start = c->ss[g0.sid].t;

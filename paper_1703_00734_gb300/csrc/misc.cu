@@ -92,63 +92,41 @@ void launch_stats(int K, const StatChunk *chunks, int n_chunks, const double *X,
 // Block-level dense FP64 linear algebra on K x K row-major matrices in shared memory.
 // ------------------------------------------------------------------------------------------
 
-// In-place lower Cholesky (right-looking).  Returns false (uniformly) if a pivot is not > 0.
-__device__ bool block_chol(double *A, int K, int *flag)
+// In-place lower Cholesky (right-looking); rinv[k] = 1 / L_kk.  Returns false (uniformly) if a
+// pivot is not > 0.  Two barriers per column: the trailing update of column k uses the unscaled
+// column times 1 / d_k, and column k is scaled during the next pivot step.
+__device__ bool block_chol(double *A, int K, double *rinv, int *flag)
 {
     const int t = threadIdx.x, T = blockDim.x;
     for (int k = 0; k < K; ++k) {
         if (t == 0) {
             const double d = A[k * K + k];
-            if (!(d > 0.0))
+            if (!(d > 0.0)) {
                 *flag = 1;
-            else
-                A[k * K + k] = sqrt(d);
+            } else {
+                const double r = rsqrt(d);
+                A[k * K + k] = d * r;
+                rinv[k] = r;
+            }
+        } else if (k > 0) {
+            const double r = rinv[k - 1];
+            for (int i = k + t - 1; i < K; i += T - 1) A[i * K + k - 1] *= r;
         }
         __syncthreads();
         if (*flag) return false;
-        const double dk = A[k * K + k];
-        for (int i = k + 1 + t; i < K; i += T) A[i * K + k] /= dk;
-        __syncthreads();
+        const double r2 = rinv[k] * rinv[k];
         const int m = K - k - 1;
         for (int e = t; e < m * m; e += T) {
             const int i = k + 1 + e / m, j = k + 1 + e % m;
-            if (j <= i) A[i * K + j] = fma(-A[i * K + k], A[j * K + k], A[i * K + j]);
+            if (j <= i) A[i * K + j] = fma(-A[i * K + k] * A[j * K + k], r2, A[i * K + j]);
         }
         __syncthreads();
     }
-    // zero the strict upper triangle
+    // zero the strict upper triangle (column K - 1 has nothing below its pivot to scale)
     for (int e = t; e < K * K; e += T)
         if (e % K > e / K) A[e] = 0.0;
     __syncthreads();
     return true;
-}
-
-// Inverse of S = L L^T (L lower in Lm): column c solves L y = e_c, L^T x = y; then symmetrise.
-__device__ void block_spd_inverse_from_chol(const double *Lm, double *Out, double *Tmp, int K)
-{
-    const int t = threadIdx.x, T = blockDim.x;
-    for (int c = t; c < K; c += T) {
-        for (int i = 0; i < K; ++i) {
-            double s = (i == c) ? 1.0 : 0.0;
-            for (int k = 0; k < i; ++k) s = fma(-Lm[i * K + k], Tmp[k * K + c], s);
-            Tmp[i * K + c] = s / Lm[i * K + i];
-        }
-        for (int i = K - 1; i >= 0; --i) {
-            double s = Tmp[i * K + c];
-            for (int k = i + 1; k < K; ++k) s = fma(-Lm[k * K + i], Out[k * K + c], s);
-            Out[i * K + c] = s / Lm[i * K + i];
-        }
-    }
-    __syncthreads();
-    for (int e = t; e < K * K; e += T) {
-        const int i = e / K, j = e % K;
-        if (j < i) {
-            const double m = 0.5 * (Out[i * K + j] + Out[j * K + i]);
-            Out[i * K + j] = m;
-            Out[j * K + i] = m;
-        }
-    }
-    __syncthreads();
 }
 
 // ------------------------------------------------------------------------------------------
@@ -197,7 +175,8 @@ __global__ void __launch_bounds__(256) hyper_kernel(HyperParams a)
     extern __shared__ double s[];
     double *M = s, *C = M + KK, *L = C + KK, *B = L + KK;
     double *s1 = B + KK, *xbar = s1 + K, *mus = xbar + K, *v = mus + K, *mu = v + K;
-    double *red = mu + K;  // [T] stripe partial sums
+    double *rinv = mu + K;  // [K] reciprocal pivots
+    double *red = rinv + K;  // [T] stripe partial sums
     __shared__ int flag;
     if (t == 0) flag = 0;
     // 1. sum the chunk statistics: each entry is split over `ns` stripes of chunks, each
@@ -257,13 +236,27 @@ __global__ void __launch_bounds__(256) hyper_kernel(HyperParams a)
         C[e] = a.W0inv[e] + N * Sb + cw * (a.mu0[i] - xbar[i]) * (a.mu0[j] - xbar[j]);
     }
     __syncthreads();
-    // 3. W* = ([W*]^{-1})^{-1}
-    if (!block_chol(C, K, &flag)) goto fail;
-    block_spd_inverse_from_chol(C, M, B, K);     // M = W*
-    // 4. L = chol(W*)
-    for (int e = t; e < KK; e += T) L[e] = M[e];
+    // 3. the lower Cholesky factor of W* = ([W*]^{-1})^{-1} without forming W*: with P the
+    //    order reversal, P [W*]^{-1} P = R R^T (R lower) gives W* = (P R^{-T} P)(P R^{-T} P)^T,
+    //    and P R^{-T} P is lower with a positive diagonal, so it is that factor
+    for (int e = t; e < KK; e += T) L[e] = C[(KK - 1) - e];
     __syncthreads();
-    if (!block_chol(L, K, &flag)) goto fail;
+    if (!block_chol(L, K, rinv, &flag)) goto fail;
+    for (int c = t; c < K; c += T) {           // R^{-1} (lower) into M, a column per thread
+        for (int i = 0; i < c; ++i) M[i * K + c] = 0.0;
+        for (int i = c; i < K; ++i) {
+            double acc = i == c ? 1.0 : 0.0;
+            for (int k = c; k < i; ++k) acc = fma(-L[i * K + k], M[k * K + c], acc);
+            M[i * K + c] = acc * rinv[i];
+        }
+    }
+    __syncthreads();
+    // 4. L = P R^{-T} P: L_ij = (R^{-1})_{K-1-j, K-1-i}
+    for (int e = t; e < KK; e += T) {
+        const int i = e / K, j = e % K;
+        L[e] = j <= i ? M[(K - 1 - j) * K + (K - 1 - i)] : 0.0;
+    }
+    __syncthreads();
     // 5. Bartlett factor A (lower) in B
     {
         const double *dr = a.draws + jb.draw;
@@ -297,17 +290,23 @@ __global__ void __launch_bounds__(256) hyper_kernel(HyperParams a)
         M[e] = acc;
     }
     __syncthreads();
-    // 7. mu = mu* + chol(beta* Lambda)^{-T} z_mu
-    for (int e = t; e < KK; e += T) L[e] = bstar * M[e];
+    // 7. mu = mu* + chol(beta* Lambda)^{-T} z_mu, where chol(beta* Lambda) = sqrt(beta*) L A
+    //    (L A is lower with a positive diagonal and (L A)(L A)^T = Lambda)
+    for (int i = t; i < K; i += T) {
+        const double d = C[i * K + i];
+        if (!(d > 0.0)) flag = 1;
+        rinv[i] = 1.0 / d;
+    }
     __syncthreads();
-    if (!block_chol(L, K, &flag)) goto fail;
+    if (flag) goto fail;
     if (t == 0) {
+        const double sb = rsqrt(bstar);
         for (int i = K - 1; i >= 0; --i) {
             double acc = v[i];
-            for (int k = i + 1; k < K; ++k) acc = fma(-L[k * K + i], v[k], acc);
-            v[i] = acc / L[i * K + i];
+            for (int k = i + 1; k < K; ++k) acc = fma(-C[k * K + i], v[k], acc);
+            v[i] = acc * rinv[i];
         }
-        for (int i = 0; i < K; ++i) mu[i] = mus[i] + v[i];
+        for (int i = 0; i < K; ++i) mu[i] = fma(v[i], sb, mus[i]);
     }
     __syncthreads();
     // 8. write the slot: mu, Lambda (packed lower), b = Lambda mu
@@ -333,7 +332,7 @@ fail:
 void launch_hyper(const HyperParams &a, cudaStream_t st)
 {
     if (a.n_jobs <= 0) return;
-    const size_t smem = (size_t)(4 * a.K * a.K + 5 * a.K + 256) * sizeof(double);
+    const size_t smem = (size_t)(4 * a.K * a.K + 6 * a.K + 256) * sizeof(double);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(hyper_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     hyper_kernel<<<a.n_jobs, 256, smem, st>>>(a);
