@@ -94,7 +94,7 @@ struct bmf_ctx {
                 cudaStreamDestroy(x);
             }
         for (cudaEvent_t e : {ev_fork, ev_fac[0], ev_fac[1], ev_hyp[0], ev_hyp[1], ev_cdone, ev_tail,
-                              ev_tail2, ev_rmse, ev_gen[0], ev_gen[1], ev_copy})
+                              ev_tail2, ev_rmse, ev_gen[0], ev_gen[1], ev_copy, ev_copy_h})
             if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : ev_chunk)
             if (e) cudaEventDestroy(e);
@@ -118,6 +118,7 @@ struct bmf_ctx {
     cudaEvent_t ev_chunk[kMaxChunks] = {}, ev_cdone = nullptr;
     cudaEvent_t ev_tail = nullptr, ev_tail2 = nullptr, ev_rmse = nullptr, ev_gen[2] = {nullptr, nullptr};
     cudaEvent_t ev_copy = nullptr;   // host draw buffer on the device (copied on the generator stream)
+    cudaEvent_t ev_copy_h = nullptr; // its first part: the hyperparameter blocks of the first sweep
     struct Readback {
         DevError err;
         double rmse[2];
@@ -495,7 +496,7 @@ bmf_status setup_side(bmf_ctx *c, Side &s, int64_t R, const std::vector<int64_t>
 
 // Draw buffer of a call on the device.
 bmf_status stage_draws(bmf_ctx *c, const bmf_draws *d, int64_t need, const double **out,
-                       cudaStream_t copy_st)
+                       cudaStream_t copy_st, int64_t first = 0, cudaEvent_t first_ev = nullptr)
 {
     if (!d) {
         *out = nullptr;   // the device generator fills the sweep buffers
@@ -516,8 +517,18 @@ bmf_status stage_draws(bmf_ctx *c, const bmf_draws *d, int64_t need, const doubl
             return fail(c, BMF_E_OOM, "device allocation failed (draw buffer)");
         c->draws_cap = need;
     }
-    CUDA_TRY(c, cudaMemcpyAsync(c->draws_d, d->ptr, need * sizeof(double), cudaMemcpyHostToDevice,
-                                copy_st));
+    // a host buffer: the first `first` doubles are copied first and `first_ev` recorded after
+    // them, so that their readers need not wait for the whole buffer
+    int64_t done = 0;
+    if (first > 0 && first < need && first_ev) {
+        CUDA_TRY(c, cudaMemcpyAsync(c->draws_d, d->ptr, first * sizeof(double), cudaMemcpyHostToDevice,
+                                    copy_st));
+        CUDA_TRY(c, cudaEventRecord(first_ev, copy_st));
+        done = first;
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->draws_d + done, d->ptr + done, (need - done) * sizeof(double),
+                                cudaMemcpyHostToDevice, copy_st));
+    if (first > 0 && first_ev && done == 0) CUDA_TRY(c, cudaEventRecord(first_ev, copy_st));
     *out = c->draws_d;
     return BMF_OK;
 }
@@ -640,7 +651,10 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
     // host draw buffers are copied on the generator stream (idle with host draws), so that the
     // first Gram pass, which needs no draws, starts at once; the first readers wait for it
     const bool copy_async = draws && !draws->on_device && !use_graph && n_sweeps > 0;
-    bmf_status s = stage_draws(c, draws, per * n_sweeps, &dr, copy_async ? c->st5 : c->st);
+    // the call's first hyperparameter draws read only the first sweep's hyperparameter blocks
+    const int64_t first_hyper = 2 * (int64_t)(sl1 - sl0) * hyper_block_len(K);
+    bmf_status s = stage_draws(c, draws, per * n_sweeps, &dr, copy_async ? c->st5 : c->st,
+                               copy_async ? first_hyper : 0, c->ev_copy_h);
     if (s) return s;
     // the caller's host buffer is read until the copy completes: never return before that
     struct CopyWait {
@@ -756,7 +770,7 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
         // slots left them current (the conditional kernel keeps them current from then on)
         CUDA_TRY(c, cudaEventRecord(c->ev_fork, c->st));
         CUDA_TRY(c, cudaStreamWaitEvent(c->st2, c->ev_fork, 0));
-        if (copy_async) CUDA_TRY(c, cudaStreamWaitEvent(c->st2, c->ev_copy, 0));
+        if (copy_async) CUDA_TRY(c, cudaStreamWaitEvent(c->st2, c->ev_copy_h, 0));
         bool current = true;
         for (int sl = sl0; sl < sl1; ++sl) current = current && c->stats_ok[sl];
         for (int f = 0; f < 2; ++f) {
@@ -1274,7 +1288,7 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
         ok = ok && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) == cudaSuccess;
         for (cudaEvent_t *e : {&c->ev_fork, &c->ev_fac[0], &c->ev_fac[1], &c->ev_hyp[0], &c->ev_hyp[1],
                                &c->ev_cdone, &c->ev_tail, &c->ev_tail2, &c->ev_rmse, &c->ev_gen[0],
-                               &c->ev_gen[1], &c->ev_copy})
+                               &c->ev_gen[1], &c->ev_copy, &c->ev_copy_h})
             ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
         for (cudaEvent_t &e : c->ev_chunk)
             ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
