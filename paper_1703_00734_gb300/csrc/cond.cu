@@ -99,9 +99,9 @@ __global__ void __launch_bounds__(kCondBlock) cond_kernel(CondParams a)
                 ok = false;
                 break;
             }
+            // only 1 / L_jj is used from here on (the solves scale by it)
             const double rs = rsqrt(d);
             SM(RI + j) = rs;
-            SM(jj + j) = d * rs;
             for (int i = j + 1; i < K; ++i) {
                 const int ii = tri(i, 0);
                 double s = SM(ii + j);

@@ -546,10 +546,7 @@ __global__ void __launch_bounds__(32 * kWideWarps) cond_team_kernel(CondParams a
                     M[tri(i, k)] = l;
                     if constexpr (team_colcopy(T)) CK[i] = l;
                 }
-                if (tl == 0) {
-                    M[kk] = d * rs;
-                    RI[k] = rs;
-                }
+                if (tl == 0) RI[k] = rs;   // the solves scale by 1 / L_kk; L_kk itself is not kept
             }
             __syncwarp(mask);
             if (ok) {
