@@ -502,7 +502,6 @@ __global__ void __launch_bounds__(32 * kWideWarps) cond_team_kernel(CondParams a
     const unsigned mask = T == 32 ? 0xffffffffu : (((1u << T) - 1u) << ((threadIdx.x & 31) & ~(T - 1)));
     const int per_team = team_stride(K, T);
     double *M = smw + tm * per_team, *B = M + NT, *RI = B + K, *CK = RI + K;
-    double *XS = smw + NTEAM * per_team;     // [kCondBlock][K]: x of the block's rows
     const CondBlock blk = a.blocks[blockIdx.x];
     const int64_t R = a.R;
     const double tau = a.tau;
@@ -600,18 +599,15 @@ __global__ void __launch_bounds__(32 * kWideWarps) cond_team_kernel(CondParams a
             }
             __syncwarp(mask);
         }
-        // 6. state, gathered copy, moments, block copy for the statistics
+        // 6. state, gathered copy, moments
         if (active) {
             GT *g = static_cast<GT *>(a.Xg) + r * a.ldg;
             for (int i = tl; i < a.ldg; i += T) {
                 const double xi = (ok && i < K) ? B[i] : 0.0;
                 if (ok) g[i] = to_gather_w<GT>(xi);
-                if (i < K) {
-                    if (ok) {
-                        a.X[r * K + i] = xi;
-                        if (a.keep) a.S1[(int64_t)i * R + r] += xi;
-                    }
-                    XS[q * K + i] = xi;
+                if (i < K && ok) {
+                    a.X[r * K + i] = xi;
+                    if (a.keep) a.S1[(int64_t)i * R + r] += xi;
                 }
             }
             if (ok && a.keep && a.full)
@@ -623,19 +619,22 @@ __global__ void __launch_bounds__(32 * kWideWarps) cond_team_kernel(CondParams a
         }
         __syncwarp(mask);
     }
-    // 7. per-block statistics of the new state (unless computed on another stream)
+    // 7. per-block statistics of the new state (unless computed on another stream), read back
+    //    from the state rows this block has just written (visible to the block after the
+    //    barrier, and still in L1); no shared-memory copy, so more blocks fit on an SM
     if (a.stats == nullptr) return;
     __syncthreads();
     const int NS = K + NT;
+    const double *Xb = a.X + blk.row0 * K;
     double *out = a.stats + (a.blk0 + blockIdx.x) * (int64_t)NS;
     for (int e = threadIdx.x; e < NS; e += blockDim.x) {
         double s = 0.0;
         if (e < K) {
-            for (int q = 0; q < blk.n; ++q) s += XS[q * K + e];
+            for (int q = 0; q < blk.n; ++q) s += Xb[q * K + e];
         } else {
             int i, j;
             decode_packed(e - K, i, j);
-            for (int q = 0; q < blk.n; ++q) s = fma(XS[q * K + i], XS[q * K + j], s);
+            for (int q = 0; q < blk.n; ++q) s = fma(Xb[q * K + i], Xb[q * K + j], s);
         }
         out[e] = s;
     }
@@ -645,7 +644,7 @@ template <typename GT, typename AT, int T>
 static void launch_cond_team_t(const CondParams &a, int n_blocks, cudaStream_t st)
 {
     constexpr int NTEAM = 32 * kWideWarps / T;
-    const size_t smem = ((size_t)NTEAM * team_stride(a.K, T) + (size_t)kCondBlock * a.K) * sizeof(double);
+    const size_t smem = (size_t)NTEAM * team_stride(a.K, T) * sizeof(double);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(cond_team_kernel<GT, AT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cond_team_kernel<GT, AT, T><<<n_blocks, 32 * kWideWarps, smem, st>>>(a);
