@@ -11,8 +11,10 @@ are reported beside it.  `--impl reference` times the FP64 CPU oracle instead.
 Other workloads (--workload): a workload with an I x J grid (pp4x4-100000x20000-20M-k16) runs
 the three batched posterior-propagation stages, aggregation and prediction against the plain
 FP64 and reduced-precision samplers at the same sweep count; uniform-200000x50000-50M-k64 times
-the log-joint adjoint, Langevin moves and Gibbs sweeps at K = 64; any other named workload runs
-the plain-sweep benchmark above on it.
+the log-joint adjoint, Langevin moves and Gibbs sweeps at K = 64; sim-6040x3706-k5 and
+sim-6040x3706-k5-structured run PP on 1x1 ... 30x30 grids in both row/column orders and report
+test RMSE and time per partition (the paper's simulated-data experiment); any other named
+workload runs the plain-sweep benchmark above on it.
 
 Prints ONE JSON line (rank 0).  For --gpus N > 1 (torchrun) every rank runs an independent
 replica of the workload (one chain does not shard across GPUs) and value sums them.
@@ -547,7 +549,77 @@ def run_adjoint(args, rank, world, local_rank):
     }
 
 
-MODES = {"uniform-200000x50000-50M-k64": "adjoint"}
+MODES = {"uniform-200000x50000-50M-k64": "adjoint", "sim-6040x3706-k5": "partitions",
+         "sim-6040x3706-k5-structured": "partitions"}
+
+
+# ---------------------------------------------------------------------------------------
+# test RMSE and wall-clock time of PP against the partition (Section 5.3, simulated data)
+# ---------------------------------------------------------------------------------------
+PART_GRIDS = (1, 3, 5, 10, 30)
+PART_SWEEPS, PART_BURNIN, PART_THIN = 1200, 800, 2    # the paper's chains (200 samples kept)
+
+
+def run_partitions(args, rank, world, local_rank):
+    """One PP run per r x r grid and row/column order on the simulated data: three stages of
+    1200 sweeps (burn-in 800, thin 2; device generator), then aggregation (Eq. 14, Algorithm 2)
+    and the posterior-mean prediction of every held-out cell.  FP64 throughout, as in the
+    paper's runs.  Time per run: CUDA events around the stages plus the prediction call."""
+    import torch
+    from paper_1703_00734_gb300 import bmf
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    d = load_workload(args.workload, args.scale)
+    K, tau = d["K"], d["tau"]
+    T, B = PART_SWEEPS, PART_BURNIN
+    if args.scale < 1.0:                  # shrunk runs (tests, captures): shorter chains
+        T, B = 120, 80
+    runs, launches = [], 0
+    with ClockSampler(local_rank) as clk:
+        for order in ("decreasing", "none"):
+            for g in PART_GRIDS:
+                if g > min(d["N"], d["D"]):
+                    continue
+                m = bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], K, tau, "fp64",
+                            I=g, J=g, X0=d["X0"], W0=d["W0"], order=order, burnin=B,
+                            thin=PART_THIN, seed=rank, stream=stream.cuda_stream)
+                torch.cuda.synchronize()
+                n0 = m.launch_count()
+                stage_ms = []
+                t0 = time.perf_counter()
+                for stage in ((1,) if g == 1 else (1, 2, 3)):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    m.stage(stage, T, None)
+                    e1.record(stream)
+                    e1.synchronize()
+                    stage_ms.append(e0.elapsed_time(e1))
+                _, rmse = m.predict(d["test_row"], d["test_col"], d["test_val"])
+                secs = time.perf_counter() - t0
+                launches += m.launch_count() - n0
+                m.close()
+                runs.append({"grid": f"{g}x{g}", "order": order, "rmse": rmse,
+                             "seconds": secs, "stage_ms": stage_ms})
+                log(f"{order} {g}x{g}: rmse {rmse:.4f} in {secs:.2f} s")
+    if rank != 0:
+        return None
+    for r in runs:
+        base = next(q for q in runs if q["order"] == r["order"] and q["grid"] == "1x1")
+        r["wts"] = base["seconds"] / r["seconds"]
+    head = next((r for r in runs if r["grid"] == "10x10" and r["order"] == "decreasing"), runs[-1])
+    return {
+        "metric": "test RMSE of PP by partition (simulated data, Section 5.3)", "impl": "ours",
+        "value": head["rmse"], "unit": "RMSE", "n_gpus": world, "steps": T, "warmup": 0,
+        "ms_per_step": head["seconds"] * 1e3 / (3 * T), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "N": d["N"], "D": d["D"],
+                   "train_obs": len(d["row"]), "test_obs": len(d["test_row"]), "K": K,
+                   "tau": tau, "sweeps_per_stage": T, "burnin": B, "thin": PART_THIN,
+                   "value_run": f"{head['grid']} {head['order']}"},
+        "runs": runs, "gpu_launches": launches, "clocks": clk.summary(),
+    }
 
 
 def traffic_for(kernel, prec, workload):
@@ -654,6 +726,8 @@ def main():
             out = run_pp(args, rank, world, local_rank)
         elif MODES.get(args.workload) == "adjoint":
             out = run_adjoint(args, rank, world, local_rank)
+        elif MODES.get(args.workload) == "partitions":
+            out = run_partitions(args, rank, world, local_rank)
         else:
             out = run_ours(args, rank, world, local_rank)
         if world > 1:

@@ -14,6 +14,12 @@ and statistics of the rating matrices the paper uses, Section 5.3):
                     heaviest rows and columns saturate (fully observed), as in rating data.
   * ratings      -- y = clip(round(3.5 + x^T w + N(0, sigma^2)), 1, 5) with X, W entries of
                     variance K^{-1/2} (so x^T w has unit variance).
+  * ``dense``    -- every cell of Y = X W^T + E observed (X, W, E standard normal), then split
+                    by a missingness scenario (Section 5.3, simulated data): ``random``, a
+                    uniformly random fraction held out as the test set; ``structured``, cell
+                    (n, d) kept for training with probability w_n w_d, where w_n and w_d run in
+                    equal steps from 0.9 down to 0.005 over the rows and over the columns (about
+                    80% of the cells end up missing, i.e. in the test set).
 """
 from __future__ import annotations
 
@@ -162,6 +168,16 @@ def split(nnz: int, test_frac: float, rng):
     return m
 
 
+def structured_missing(N: int, D: int, rng) -> np.ndarray:
+    """Test (missing) mask over the N x D cells in row-major order for the structured
+    scenario: a cell is kept for training with probability w_n w_d, w_n and w_d equally
+    spaced from 0.9 down to 0.005 (Section 5.3)."""
+    wn = np.linspace(0.9, 0.005, N)
+    wd = np.linspace(0.9, 0.005, D)
+    keep = rng.random((N, D)) < wn[:, None] * wd[None, :]
+    return ~keep.reshape(-1)
+
+
 def init_state(n: int, K: int, sd: float, rng) -> np.ndarray:
     return rng.standard_normal((n, K)) * sd
 
@@ -186,6 +202,14 @@ WORKLOADS = {
     "uniform-200000x50000-50M-k64": dict(N=200_000, D=50_000, M=50_000_000,
                                          pattern="uniform", K=64, sigma=0.3, x_sd=1.0,
                                          w_sd=1.0, ratings=False, tau=1.0 / 0.09, seed=4),
+    # the paper's simulated data sets (Section 5.3): 6,040 x 3,706, K = 5, unit noise, 80% of
+    # the cells missing at random or in the structured pattern
+    "sim-6040x3706-k5": dict(N=6040, D=3706, pattern="dense", K=5, sigma=1.0, x_sd=1.0,
+                             w_sd=1.0, ratings=False, tau=1.0, seed=5, missing="random",
+                             test_frac=0.8),
+    "sim-6040x3706-k5-structured": dict(N=6040, D=3706, pattern="dense", K=5, sigma=1.0,
+                                        x_sd=1.0, w_sd=1.0, ratings=False, tau=1.0, seed=6,
+                                        missing="structured"),
 }
 
 
@@ -198,14 +222,18 @@ def make_workload(name: str = None, test_frac: float = 0.1, scale: float = 1.0, 
     cfg.update(over)
     N = sizes["N"] if "N" in sizes else max(2, int(round(cfg["N"] * scale)))
     D = sizes["D"] if "D" in sizes else max(2, int(round(cfg["D"] * scale)))
-    M = sizes["M"] if "M" in sizes else max(4, int(round(cfg["M"] * scale * scale)))
     K = cfg["K"]
     seed = cfg.get("seed", 0)
     rng = rng_for(seed, 1)
-    if cfg["pattern"] == "uniform":
-        row, col = uniform_pairs(N, D, M, rng)
+    if cfg["pattern"] == "dense":
+        keys = np.arange(N * D, dtype=np.int64)
+        row, col = (keys // D).astype(np.int32), (keys % D).astype(np.int32)
     else:
-        row, col = zipf_pairs(N, D, M, cfg["s_row"], cfg["s_col"], rng)
+        M = sizes["M"] if "M" in sizes else max(4, int(round(cfg["M"] * scale * scale)))
+        if cfg["pattern"] == "uniform":
+            row, col = uniform_pairs(N, D, M, rng)
+        else:
+            row, col = zipf_pairs(N, D, M, cfg["s_row"], cfg["s_col"], rng)
     if cfg.get("ratings"):
         sd = K ** (-0.25)
         y, Xt, Wt = planted_values(N, D, row, col, K, sd, sd, cfg["sigma"], rng_for(seed, 2),
@@ -213,7 +241,10 @@ def make_workload(name: str = None, test_frac: float = 0.1, scale: float = 1.0, 
     else:
         y, Xt, Wt = planted_values(N, D, row, col, K, cfg.get("x_sd", 1.0), cfg.get("w_sd", 1.0),
                                    cfg["sigma"], rng_for(seed, 2))
-    test = split(len(row), test_frac, rng_for(seed, 3))
+    if cfg.get("missing") == "structured":
+        test = structured_missing(N, D, rng_for(seed, 3))
+    else:
+        test = split(len(row), cfg.get("test_frac", test_frac), rng_for(seed, 3))
     tr = ~test
     X0 = init_state(N, K, 0.1, rng_for(seed, 4))
     W0 = init_state(D, K, 0.1, rng_for(seed, 5))
