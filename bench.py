@@ -333,6 +333,7 @@ def run_ours(args, rank, world, local_rank):
     }
     if world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         out["cpu_baseline"] = cpu_baseline(d, args.cpu_seconds)
+        out["cpu_all_cores"] = cpu_all_cores(d, args.cpu_seconds)
     return out
 
 
@@ -650,18 +651,19 @@ def oracle_sweeps(d, budget_s, max_sweeps, warmup=0):
     H = oracle.hyper_block_len(K)
 
     def one(t):
+        """One oracle sweep; returns its time (the draw buffer is made before the clock)."""
         dr = make_draws(d, K, prior.nu0, 1, seed=900 + t)
+        t0 = time.perf_counter()
         oracle.sweep_subset(s, st, K, d["tau"], prior, dr[0:H], dr[H:2 * H],
                             dr[lay[(0, "zx")]:lay[(0, "zx")] + s.n * K],
                             dr[lay[(0, "zw")]:lay[(0, "zw")] + s.d * K])
+        return time.perf_counter() - t0
 
     for t in range(warmup):
         one(t)
     done, busy = 0, 0.0
     while done < max_sweeps and (done == 0 or busy < budget_s):
-        t0 = time.perf_counter()
-        one(warmup + done)
-        busy += time.perf_counter() - t0
+        busy += one(warmup + done)
         done += 1
     return done, busy
 
@@ -671,6 +673,22 @@ def cpu_baseline(d, budget):
     return {"value": n / secs, "unit": "sweeps/s", "cores": 1, "kind": "oracle",
             "sample": f"{n} full FP64 oracle sweeps of the same workload, single thread "
                       f"({secs:.1f} s, draw generation excluded)"}
+
+
+def cpu_all_cores(d, budget):
+    """The oracle's OpenMP build (row conditionals over all host cores, same results)."""
+    import oracle
+    try:
+        threads = oracle.use_openmp(True)
+        n, secs = oracle_sweeps(d, budget, 1000)
+    except Exception as e:                       # no OpenMP runtime on this host
+        return {"unavailable": f"OpenMP build of the oracle failed: {e}"}
+    finally:
+        oracle.use_openmp(False)
+    return {"value": n / secs, "unit": "sweeps/s", "cores": threads,
+            "kind": "oracle, OpenMP over rows",
+            "sample": f"{n} full FP64 oracle sweeps of the same workload ({secs:.1f} s, draw "
+                      f"generation excluded; hyperparameter step and moments single-threaded)"}
 
 
 def run_reference(args, rank):

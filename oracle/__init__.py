@@ -9,7 +9,9 @@ the library never imports this package.
 Layout:
   * ``bmf_oracle.c``  -- FP64 numerical core (conditionals, Normal-Wishart draw, moment
     matching, Algorithm 2 aggregation, log-joint gradient), compiled with gcc into
-    ``oracle/_build/liborc.so``.
+    ``oracle/_build/liborc.so`` (single thread: the tests and the CPU baseline) and, on
+    request (``use_openmp``), into ``liborc_omp.so`` with the row conditionals split over
+    threads (same results; the all-core timing).
   * this module       -- ctypes bindings, the I x J grid planning (Section 3, Fig. 1), the
     per-subset CSR/CSC lists, and the stage orchestration of Algorithm 1 (Section 4.1) with
     the stage-wise hyperparameter rule of Section 5.1.
@@ -39,29 +41,45 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liborc.so")
+_SO_OMP = os.path.join(_BUILD, "liborc_omp.so")
 _SRC = os.path.join(_HERE, "bmf_oracle.c")
 _lib = None
+_openmp = False
 
 ORC_OK, ORC_NOT_PD = 0, 1
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, openmp: bool = False) -> str:
     """Compile the C core with gcc (FP contraction off so results do not depend on the
-    host's FMA support)."""
+    host's FMA support); ``openmp`` builds the variant whose row conditionals run on all
+    cores."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        tmp = _SO + ".tmp.%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _SO)
-    return _SO
+    so = _SO_OMP if openmp else _SO
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(_SRC):
+        tmp = so + ".tmp.%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared"]
+                              + (["-fopenmp"] if openmp else []) + ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, so)
+    return so
+
+
+def use_openmp(on: bool = True) -> int:
+    """Switch this process to the OpenMP build (or back); returns the thread count the row
+    conditionals use (1 for the serial build).  Results do not change."""
+    global _lib, _openmp
+    if on != _openmp:
+        _lib, _openmp = None, on
+    if not on:
+        return 1
+    build(openmp=True)
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
 def lib():
     global _lib
     if _lib is None:
-        build()
-        L = ctypes.CDLL(_SO)
+        so = build(openmp=_openmp)
+        L = ctypes.CDLL(so)
         P = ctypes.c_void_p
         i64, i32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_double
         L.orc_nw_posterior.argtypes = [i32, i64, P, P, f64, f64, P, P, P, P, P, P, P]
