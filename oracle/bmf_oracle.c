@@ -249,38 +249,6 @@ int orc_nw_draw(int K, const double *mu_star, double beta_star, const double *Ws
 /* Row conditionals (the Gibbs update of every x_n given W; Eqs. 2-4).                   */
 /* ------------------------------------------------------------------------------------- */
 
-/* One row of orc_update_rows with workspace w (2 K*K + 2 K doubles); 0, or 1 if Lambda_r is not
- * positive definite. */
-static int update_row(int K, int64_t r, const int64_t *ptr, const int32_t *idx, const double *val,
-                      const double *P, double tau, int per_row_prior, const double *mu_p,
-                      const double *Lam_p, const double *z, double *X_out, double *w)
-{
-    size_t KK = (size_t)K * K;
-    double *A = w, *L = w + KK, *b = w + 2 * KK;
-    const double *mu = per_row_prior ? mu_p + r * K : mu_p;
-    const double *Lam = per_row_prior ? Lam_p + r * (int64_t)KK : Lam_p;
-    for (size_t a = 0; a < KK; ++a) A[a] = Lam[a];
-    for (int i = 0; i < K; ++i) {
-        double s = 0.0;
-        for (int j = 0; j < K; ++j) s += Lam[i * K + j] * mu[j];
-        b[i] = s;
-    }
-    for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) {
-        const double *p = P + (int64_t)idx[e] * K;
-        double y = val[e];
-        for (int i = 0; i < K; ++i) {
-            for (int j = 0; j < K; ++j) A[i * K + j] += tau * p[i] * p[j];
-            b[i] += tau * y * p[i];
-        }
-    }
-    if (chol_lower(K, A, L)) return 1;
-    solve_lower(K, L, b);                       /* b <- L^{-1} b            */
-    for (int i = 0; i < K; ++i) b[i] += z[r * K + i]; /* + z                 */
-    solve_lower_t(K, L, b);                     /* x = L^{-T}(L^{-1} b + z) */
-    for (int i = 0; i < K; ++i) X_out[r * K + i] = b[i];
-    return 0;
-}
-
 /* For each row r of a CSR block (ptr/idx/val; idx indexes rows of the partner matrix P):
  *   Lambda_r = Lambda_p + tau sum_{d in Omega_r} p_d p_d^T,
  *   b_r      = Lambda_p mu_p + tau sum_{d in Omega_r} y_rd p_d,
@@ -288,46 +256,79 @@ static int update_row(int K, int64_t r, const int64_t *ptr, const int32_t *idx, 
  * The prior (mu_p, Lambda_p) is shared by all rows (per_row_prior = 0: mu_p[K],
  * Lam_p[K*K]) or given per row (per_row_prior = 1: mu_p[R*K], Lam_p[R*K*K]).
  * If some Lambda_r is not positive definite, *bad_row = the first such r and ORC_NOT_PD is
- * returned.  The rows are independent given P and the draws, so a build with OpenMP (the
- * all-core timing of the oracle) splits them over threads; every row's arithmetic is the same
- * as in the serial build. */
+ * returned (the serial build stops there).  The rows are independent given P and the draws, so
+ * a build with OpenMP (the all-core timing of the oracle) splits them over threads; every row's
+ * arithmetic is the same as in the serial build, whose loop compiles as if the OpenMP lines
+ * were absent. */
 int orc_update_rows(int K, int64_t R, const int64_t *ptr, const int32_t *idx, const double *val,
                     const double *P, double tau, int per_row_prior, const double *mu_p,
                     const double *Lam_p, const double *z, double *X_out, int64_t *bad_row)
 {
     size_t KK = (size_t)K * K;
+#ifdef _OPENMP
     int64_t first_bad = -1;
     int nomem = 0;
-#ifdef _OPENMP
 #pragma omp parallel
-#endif
     {
-        double *w = (double *)malloc(sizeof(double) * (2 * KK + 2 * K));
-        if (!w) {
-#ifdef _OPENMP
-#pragma omp atomic write
 #endif
-            nomem = 1;
-        }
+    double *w = (double *)malloc(sizeof(double) * (2 * KK + 2 * K));
+#ifdef _OPENMP
+    if (!w) {
+#pragma omp atomic write
+        nomem = 1;
+    }
+#else
+    if (!w) return ORC_NOMEM;
+#endif
+    double *A = w, *L = w + KK, *b = w + 2 * KK;
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 64)
 #endif
-        for (int64_t r = 0; r < R; ++r) {
-            if (!w) continue;
-            if (update_row(K, r, ptr, idx, val, P, tau, per_row_prior, mu_p, Lam_p, z, X_out, w)) {
+    for (int64_t r = 0; r < R; ++r) {
 #ifdef _OPENMP
-#pragma omp critical(orc_bad_row)
+        if (!w) continue;
 #endif
-                if (first_bad < 0 || r < first_bad) first_bad = r;
+        const double *mu = per_row_prior ? mu_p + r * K : mu_p;
+        const double *Lam = per_row_prior ? Lam_p + r * (int64_t)KK : Lam_p;
+        for (size_t a = 0; a < KK; ++a) A[a] = Lam[a];
+        for (int i = 0; i < K; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < K; ++j) s += Lam[i * K + j] * mu[j];
+            b[i] = s;
+        }
+        for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) {
+            const double *p = P + (int64_t)idx[e] * K;
+            double y = val[e];
+            for (int i = 0; i < K; ++i) {
+                for (int j = 0; j < K; ++j) A[i * K + j] += tau * p[i] * p[j];
+                b[i] += tau * y * p[i];
             }
         }
-        free(w);
+        if (chol_lower(K, A, L)) {
+#ifdef _OPENMP
+#pragma omp critical(orc_bad_row)
+            if (first_bad < 0 || r < first_bad) first_bad = r;
+            continue;
+#else
+            if (bad_row) *bad_row = r;
+            free(w);
+            return ORC_NOT_PD;
+#endif
+        }
+        solve_lower(K, L, b);                       /* b <- L^{-1} b            */
+        for (int i = 0; i < K; ++i) b[i] += z[r * K + i]; /* + z                 */
+        solve_lower_t(K, L, b);                     /* x = L^{-T}(L^{-1} b + z) */
+        for (int i = 0; i < K; ++i) X_out[r * K + i] = b[i];
+    }
+    free(w);
+#ifdef _OPENMP
     }
     if (nomem) return ORC_NOMEM;
     if (first_bad >= 0) {
         if (bad_row) *bad_row = first_bad;
         return ORC_NOT_PD;
     }
+#endif
     return ORC_OK;
 }
 
