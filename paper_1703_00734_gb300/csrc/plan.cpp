@@ -243,8 +243,17 @@ int build_plan(int64_t N, int64_t D, int64_t nnz, const int32_t *row, const int3
     P.tval.resize(n_test);
     {
         std::vector<int64_t> pos(tcount.begin(), tcount.end() - 1);
-        for (int64_t e = 0; e < n_test; ++e) {
-            int64_t k = pos[tsl[e]]++;
+        std::vector<int64_t> order(n_test);
+        for (int64_t e = 0; e < n_test; ++e) order[pos[tsl[e]]++] = e;
+        // within a slot, entries by (arena row, arena column): consecutive test entries then
+        // share their row of the gathered state copy, which the per-sweep RMSE pass reads
+        for (int sl = 0; sl < S; ++sl)
+            std::stable_sort(order.begin() + tcount[sl], order.begin() + tcount[sl + 1],
+                             [&](int64_t a, int64_t b) {
+                                 return tar[a] != tar[b] ? tar[a] < tar[b] : tac[a] < tac[b];
+                             });
+        for (int64_t k = 0; k < n_test; ++k) {
+            const int64_t e = order[k];
             P.trow[k] = tar[e];
             P.tcol[k] = tac[e];
             P.tval[k] = test_val[e] - P.offset;
