@@ -100,3 +100,35 @@ def test_wishart_and_mean_moments(orc):
     cov_mu = post["Wstar_inv"] / (bs * (nu - K - 1))
     assert np.all(np.abs(mus.mean(0) - post["mu_star"]) < 5 * np.sqrt(np.diag(cov_mu) / S))
     np.testing.assert_allclose(np.cov(mus.T), cov_mu, rtol=0.1, atol=0.05 * np.abs(cov_mu).max())
+
+
+def test_factor_identities_of_the_kernel_route(orc):
+    """The CUDA hyperparameter step reaches the oracle's factors by another route (equal up to
+    rounding): with P the order reversal and P [W*]^{-1} P = R R^T (R lower), the lower Cholesky
+    factor of W* = ([W*]^{-1})^{-1} is P R^{-T} P; and since L A is lower with a positive
+    diagonal, chol(beta* Lambda) = sqrt(beta*) L A.  Checked against the oracle's explicit
+    inverse-then-factor route and its draw of (mu, Lambda)."""
+    rng = np.random.default_rng(15)
+    for K, N in [(1, 7), (4, 30), (10, 200), (16, 500)]:
+        pr = _prior(orc, K, rng)
+        post = orc.nw_posterior(rng.standard_normal((N, K)) * 0.8 + 1.0, pr)
+        C = post["Wstar_inv"]
+        Pm = np.eye(K)[::-1]
+        R = np.linalg.cholesky(Pm @ C @ Pm)
+        L_route = Pm @ np.linalg.inv(R).T @ Pm
+        L_oracle = np.linalg.cholesky(np.linalg.inv(C))
+        assert np.allclose(np.triu(L_route, 1), 0.0)
+        np.testing.assert_allclose(L_route, L_oracle, rtol=1e-10, atol=1e-12 * np.abs(L_oracle).max())
+        h = synth.hyper_block(K, post["nu_star"], rng)
+        mu, Lam = orc.nw_draw(post, h, K)
+        A = np.zeros((K, K))
+        A[np.diag_indices(K)] = np.sqrt(h[:K])
+        A[np.tril_indices(K, -1)] = h[K:K + K * (K - 1) // 2]
+        LA = L_route @ A
+        np.testing.assert_allclose(LA @ LA.T, Lam, rtol=1e-9, atol=1e-12 * np.abs(Lam).max())
+        np.testing.assert_allclose(np.sqrt(post["beta_star"]) * LA,
+                                   np.linalg.cholesky(post["beta_star"] * Lam), rtol=1e-8,
+                                   atol=1e-10 * np.sqrt(post["beta_star"]) * np.abs(LA).max())
+        # mu = mu* + (L A)^{-T} z_mu / sqrt(beta*), the kernel's form
+        v = np.linalg.solve(LA.T, h[-K:]) / np.sqrt(post["beta_star"])
+        np.testing.assert_allclose(post["mu_star"] + v, mu, rtol=1e-8, atol=1e-10)
