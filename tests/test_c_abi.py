@@ -67,6 +67,19 @@ def test_c_client_builds_as_strict_c99(client):
     assert os.access(client, os.X_OK)
 
 
+def test_header_compiles_as_cxx(tmp_path):
+    """bmf.h is also usable from C++ (extern "C" linkage, no C-only constructs)."""
+    if shutil.which("g++") is None:
+        pytest.skip("no g++")
+    src = tmp_path / "use.cpp"
+    src.write_text('#include "bmf.h"\nint main() { bmf_config c{}; c.K = 4; '
+                   'return bmf_last_error(nullptr) == nullptr && c.K != 4; }\n')
+    r = subprocess.run(["g++", "-std=c++11", "-Wall", "-Wextra", "-Werror", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True,
+                       text=True)
+    assert r.returncode == 0, r.stderr
+
+
 @pytest.mark.gpu
 def test_c_client_matches_python_binding(client, tmp_path):
     from paper_1703_00734_gb300 import bmf
