@@ -101,6 +101,9 @@ def lib():
         L.orc_philox4x64.argtypes = [P, P, P]
         L.orc_philox4x64.restype = None
         L.orc_gen_subset.argtypes = [ctypes.c_uint64, i64, i32, i32, f64, i64, i64, P, P, P, P]
+        L.orc_lambda_means.argtypes = [i32, i32, P, f64, i32, P]
+        L.orc_fit_summaries.argtypes = [i32, i64, i32, P, i32, i32, f64, P, P, P, P, P, P]
+        L.orc_mix_choose.argtypes = [i32, i64, i32, P, P, P, P, P, P, P]
         _lib = L
     return _lib
 
@@ -448,6 +451,10 @@ class ChainState:
     S2W: np.ndarray = None
     n_kept: int = 0
     t: int = 0                   # sweeps done
+    samples_X: list = None       # retained samples (kept for the DM / GMM summaries only)
+    samples_W: list = None
+    mixX: dict = None            # propagated mixture prior (GMM summary): pi, mu, Lam per row
+    mixW: dict = None
 
 
 def new_chain(X0, W0, K):
@@ -490,6 +497,57 @@ def accumulate(st: ChainState):
     L.orc_moments_accumulate(K, st.X.shape[0], _p(st.X), _p(st.S1X), _p(st.S2X))
     L.orc_moments_accumulate(K, st.W.shape[0], _p(st.W), _p(st.S1W), _p(st.S2W))
     st.n_kept += 1
+    if st.samples_X is not None:
+        st.samples_X.append(st.X.copy())
+        st.samples_W.append(st.W.copy())
+
+
+# ---------------------------------------------------------------------------------------
+# Dominant-mode and mixture summaries (Section 4.1 "PP DM" / "PP GMM", Section 5.1)
+# ---------------------------------------------------------------------------------------
+SUMMARY_MODES = {"mm": 0, "dm": 1, "gmm": 2}
+
+
+def lambda_means(x, lam, max_iter=100):
+    """lambda-means clustering of the rows of x (S x K) with squared-distance penalty lam;
+    returns (cluster of each row, number of clusters)."""
+    x = _f64(x)
+    S, K = x.shape
+    assign = np.zeros(max(S, 1), np.int32)
+    n = lib().orc_lambda_means(K, S, _p(x), float(lam), int(max_iter), _p(assign))
+    if n < 0:
+        raise OracleError("lambda-means: out of memory")
+    return assign[:S], n
+
+
+def fit_summaries(samples, mode, lam=0.0, C=3):
+    """Per-row summaries of retained samples [S][R][K] (see orc_fit_summaries):
+    pi [R][C], mu [R][C][K], Lam [R][C][K][K], pooled_mu [R][K], pooled_Lam [R][K][K]."""
+    samples = _f64(samples)
+    S, R, K = samples.shape
+    C = 1 if mode in ("mm", "dm") else int(C)
+    out = dict(pi=np.zeros((R, C)), mu=np.zeros((R, C, K)), Lam=np.zeros((R, C, K, K)),
+               pooled_mu=np.zeros((R, K)), pooled_Lam=np.zeros((R, K, K)))
+    bad = ctypes.c_int64(-1)
+    st = lib().orc_fit_summaries(K, R, S, _p(samples), SUMMARY_MODES[mode], C, float(lam),
+                                 _p(out["pi"]), _p(out["mu"]), _p(out["Lam"]),
+                                 _p(out["pooled_mu"]), _p(out["pooled_Lam"]), ctypes.byref(bad))
+    _check(st, f"fit_summaries({mode}) row {bad.value}")
+    return out
+
+
+def mix_choose(mix, X):
+    """Component of each row's mixture prior with the largest responsibility at X; returns
+    (chosen, mu_rows [R][K], Lam_rows [R][K][K])."""
+    X = _f64(X)
+    R, K = X.shape
+    C = mix["pi"].shape[1]
+    chosen = np.zeros(max(R, 1), np.int32)
+    mu_out, Lam_out = np.zeros((R, K)), np.zeros((R, K, K))
+    st = lib().orc_mix_choose(K, R, C, _p(_f64(mix["pi"])), _p(_f64(mix["mu"])),
+                              _p(_f64(mix["Lam"])), _p(X), _p(chosen), _p(mu_out), _p(Lam_out))
+    _check(st, "mix_choose")
+    return chosen[:R], mu_out, Lam_out
 
 
 def run_stage(plan_: Plan, stage, chains: dict, K, tau, prior, draws_per_sweep, T, burnin=0,
@@ -504,6 +562,13 @@ def run_stage(plan_: Plan, stage, chains: dict, K, tau, prior, draws_per_sweep, 
         H = hyper_block_len(K)
         for s in subs:
             st = chains[s.sid]
+            # a propagated mixture prior: each row's component is chosen at its current value
+            # (X is unchanged until its own update, W likewise, so choosing both here is the
+            # same as choosing right before each factor's draws)
+            if st.mixX is not None:
+                _, st.muX_row, st.LamX_row = mix_choose(st.mixX, st.X)
+            if st.mixW is not None:
+                _, st.muW_row, st.LamW_row = mix_choose(st.mixW, st.W)
             sweep_subset(s, st, K, tau, prior,
                          dr[lay[(s.sid, "hx")]:lay[(s.sid, "hx")] + H],
                          dr[lay[(s.sid, "hw")]:lay[(s.sid, "hw")] + H],
@@ -513,14 +578,25 @@ def run_stage(plan_: Plan, stage, chains: dict, K, tau, prior, draws_per_sweep, 
                 accumulate(st)
 
 
-def finalize(st: ChainState):
-    """Moment-matched (mu, Lambda) per row of X and of W of one subset."""
-    mx, Lx = mm_finalize(st.S1X, st.S2X, st.n_kept)
-    mw, Lw = mm_finalize(st.S1W, st.S2W, st.n_kept)
-    return mx, Lx, mw, Lw
+def finalize(st: ChainState, summary="mm", lam=0.0, C=3):
+    """Per-row (mu, Lambda) of X and of W of one subset: moment matched (summary "mm"), of
+    the dominant lambda-means mode ("dm"), or the pooled moments of the fitted mixture ("gmm",
+    whose components are returned too, for propagation).  Returns (mx, Lx, mw, Lw) for "mm",
+    (mx, Lx, mw, Lw, mixX, mixW) otherwise (mix* None for "dm")."""
+    if summary == "mm":
+        mx, Lx = mm_finalize(st.S1X, st.S2X, st.n_kept)
+        mw, Lw = mm_finalize(st.S1W, st.S2W, st.n_kept)
+        return mx, Lx, mw, Lw
+    fx = fit_summaries(np.stack(st.samples_X), summary, lam, C)
+    fw = fit_summaries(np.stack(st.samples_W), summary, lam, C)
+    if summary == "dm":
+        return fx["mu"][:, 0], fx["Lam"][:, 0], fw["mu"][:, 0], fw["Lam"][:, 0], None, None
+    return (fx["pooled_mu"], fx["pooled_Lam"], fw["pooled_mu"], fw["pooled_Lam"],
+            dict(pi=fx["pi"], mu=fx["mu"], Lam=fx["Lam"]),
+            dict(pi=fw["pi"], mu=fw["mu"], Lam=fw["Lam"]))
 
 
-def setup_stage_chains(plan_: Plan, stage, X0, W0, K, finals: dict):
+def setup_stage_chains(plan_: Plan, stage, X0, W0, K, finals: dict, summary="mm"):
     """Chains of one stage.  X0/W0 are the caller's initial states in the reordered index
     space.  Propagated priors (Algorithm 1):
       stage 2, (i,0): W^(0) from subset (0,0);  (0,j): X^(0) from subset (0,0);
@@ -529,6 +605,8 @@ def setup_stage_chains(plan_: Plan, stage, X0, W0, K, finals: dict):
     chains = {}
     for s in plan_.stage_subsets(stage):
         st = new_chain(X0[s.r0:s.r1], W0[s.c0:s.c1], K)
+        if summary != "mm":
+            st.samples_X, st.samples_W = [], []
         src_x = src_w = None
         if stage == 2:
             if s.j == 0:
@@ -542,10 +620,14 @@ def setup_stage_chains(plan_: Plan, stage, X0, W0, K, finals: dict):
             mx, Lx = finals[src_x][0], finals[src_x][1]
             st.prior_x, st.muX_row, st.LamX_row = 1, mx.copy(), Lx.copy()
             st.X = mx.copy()
+            if summary == "gmm":
+                st.mixX = finals[src_x][4]        # chain starts at the mixture's mean
         if src_w is not None:
             mw, Lw = finals[src_w][2], finals[src_w][3]
             st.prior_w, st.muW_row, st.LamW_row = 1, mw.copy(), Lw.copy()
             st.W = mw.copy()
+            if summary == "gmm":
+                st.mixW = finals[src_w][5]
         chains[s.sid] = st
     return chains
 
@@ -576,21 +658,25 @@ def aggregate_plan(plan_: Plan, finals: dict, K, eps_rel=1e-6):
     return Xm, Wm, nc
 
 
-def pp_run(plan_: Plan, K, tau, prior, X0, W0, draws_fn, T, burnin, thin, eps_rel=1e-6):
-    """Algorithm 1 with the moment-matching approximation: stages I, II, III (each stage's
-    subsets in id order), then Algorithm 2.  ``draws_fn(stage, t)`` gives the stage's draw
-    buffer for sweep t.  X0/W0 are in the reordered index space.  Returns the aggregated
-    posterior means, the per-subset finals and the chains."""
+def pp_run(plan_: Plan, K, tau, prior, X0, W0, draws_fn, T, burnin, thin, eps_rel=1e-6,
+           summary="mm", lam=0.0, C=3):
+    """Algorithm 1: stages I, II, III (each stage's subsets in id order), then Algorithm 2.
+    ``draws_fn(stage, t)`` gives the stage's draw buffer for sweep t.  X0/W0 are in the
+    reordered index space.  ``summary``: the approximation propagated between stages and
+    aggregated -- "mm" moment matching, "dm" dominant mode, "gmm" mixture of the C largest
+    lambda-means modes (penalty ``lam``), propagated as a mixture prior whose component is
+    chosen by responsibility before each draw and aggregated through its pooled moments.
+    Returns the aggregated posterior means, the per-subset finals and the chains."""
     finals, all_chains = {}, {}
     for stage in (1, 2, 3):
         subs = plan_.stage_subsets(stage)
         if not subs:
             continue
-        chains = setup_stage_chains(plan_, stage, X0, W0, K, finals)
+        chains = setup_stage_chains(plan_, stage, X0, W0, K, finals, summary)
         run_stage(plan_, stage, chains, K, tau, prior, lambda t: draws_fn(stage, t), T,
                   burnin, thin)
         for sid, st in chains.items():
-            finals[sid] = finalize(st)
+            finals[sid] = finalize(st, summary, lam, C)
         all_chains.update(chains)
     Xm, Wm, nc = aggregate_plan(plan_, finals, K, eps_rel)
     return dict(Xm=Xm, Wm=Wm, finals=finals, chains=all_chains, n_corrected=nc)

@@ -698,3 +698,261 @@ int orc_gen_subset(uint64_t seed, int64_t t, int32_t sid, int K, double nu0, int
     }
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------------------- */
+/* Summaries beyond moment matching (Section 4.1 "PP DM" and "PP GMM", Section 5.1): the  */
+/* retained samples of each row are clustered by lambda-means; the dominant-mode          */
+/* approximation fits one Gaussian to the largest cluster, the mixture approximation one  */
+/* Gaussian to each of the C largest clusters.                                            */
+/* ------------------------------------------------------------------------------------- */
+
+/* lambda-means clustering of S points in R^K (rows of x) with penalty lambda on the squared
+ * distance: start from one cluster centred on the first point (the first retained sample; a
+ * start at the mean of all points, which lies between the modes of a multimodal posterior,
+ * opens spurious clusters on the far sides of the modes that the rounds never merge); then,
+ * until no assignment changes (at most max_iter rounds), visit the points in order and give
+ * each to the nearest centre (lowest index on ties), unless its squared distance to every
+ * centre exceeds lambda, in which case it opens a new cluster centred on itself; after each
+ * round move every centre to the mean of its points and drop empty clusters, renumbering the
+ * rest in order.
+ * assign[S] receives the cluster of each point; returns the number of clusters (>= 1 for
+ * S >= 1), or -1 if memory runs out. */
+int orc_lambda_means(int K, int S, const double *x, double lambda, int max_iter, int *assign)
+{
+    if (S <= 0) return 0;
+    /* at most S non-empty clusters enter a round, and a round opens at most one per point */
+    const size_t cap = 2 * (size_t)S + 1;
+    double *cen = (double *)malloc(sizeof(double) * cap * K);
+    int *cnt = (int *)malloc(sizeof(int) * cap);
+    int *prev = (int *)malloc(sizeof(int) * (size_t)S);
+    int *map = (int *)malloc(sizeof(int) * cap);
+    if (!cen || !cnt || !prev || !map) {
+        free(cen); free(cnt); free(prev); free(map);
+        return -1;
+    }
+    int n = 1;
+    for (int k = 0; k < K; ++k) cen[k] = x[k];
+    for (int i = 0; i < S; ++i) prev[i] = -1;
+    for (int it = 0; it < max_iter; ++it) {
+        int changed = 0;
+        for (int i = 0; i < S; ++i) {
+            const double *p = x + (size_t)i * K;
+            int best = 0;
+            double dbest = INFINITY;
+            for (int c = 0; c < n; ++c) {
+                double d = 0.0;
+                for (int k = 0; k < K; ++k) {
+                    const double e = p[k] - cen[(size_t)c * K + k];
+                    d += e * e;
+                }
+                if (d < dbest) {
+                    dbest = d;
+                    best = c;
+                }
+            }
+            if (dbest > lambda) {
+                best = n++;
+                for (int k = 0; k < K; ++k) cen[(size_t)best * K + k] = p[k];
+            }
+            assign[i] = best;
+        }
+        /* centres to the means of their points; empty clusters dropped */
+        for (int c = 0; c < n; ++c) cnt[c] = 0;
+        for (int i = 0; i < S; ++i) cnt[assign[i]]++;
+        int m = 0;
+        for (int c = 0; c < n; ++c) map[c] = cnt[c] > 0 ? m++ : -1;
+        for (int c = 0; c < n; ++c) {
+            if (map[c] < 0) continue;
+            double *dst = cen + (size_t)map[c] * K;
+            for (int k = 0; k < K; ++k) {
+                double s = 0.0;
+                for (int i = 0; i < S; ++i)
+                    if (assign[i] == c) s += x[(size_t)i * K + k];
+                dst[k] = s / cnt[c];
+            }
+        }
+        n = m;
+        for (int i = 0; i < S; ++i) {
+            assign[i] = map[assign[i]];
+            if (assign[i] != prev[i]) changed = 1;
+            prev[i] = assign[i];
+        }
+        if (!changed) break;
+    }
+    free(cen); free(cnt); free(prev); free(map);
+    return n;
+}
+
+/* Mean and precision (inverse of the 1/n covariance) of the points of x (S x K) with
+ * assign[i] == c (all points when c < 0); 0, ORC_NOT_PD (fewer than K + 1 points, or a singular
+ * covariance) or ORC_NOMEM. */
+static int fit_gaussian(int K, int S, const double *x, const int *assign, int c, double *mu,
+                        double *Lam)
+{
+    size_t KK = (size_t)K * K;
+    int n = 0;
+    for (int k = 0; k < K; ++k) mu[k] = 0.0;
+    for (int i = 0; i < S; ++i) {
+        if (c >= 0 && assign[i] != c) continue;
+        ++n;
+        for (int k = 0; k < K; ++k) mu[k] += x[(size_t)i * K + k];
+    }
+    if (n < K + 1) return ORC_NOT_PD;
+    for (int k = 0; k < K; ++k) mu[k] /= n;
+    double *w = (double *)malloc(sizeof(double) * (2 * KK + K));
+    if (!w) return ORC_NOMEM;
+    double *Sig = w, *work = w + KK;
+    for (size_t a = 0; a < KK; ++a) Sig[a] = 0.0;
+    for (int i = 0; i < S; ++i) {
+        if (c >= 0 && assign[i] != c) continue;
+        const double *p = x + (size_t)i * K;
+        for (int a = 0; a < K; ++a)
+            for (int b = 0; b < K; ++b) Sig[a * K + b] += (p[a] - mu[a]) * (p[b] - mu[b]);
+    }
+    for (size_t a = 0; a < KK; ++a) Sig[a] /= n;
+    const int st = spd_inverse(K, Sig, Lam, work);
+    free(w);
+    return st;
+}
+
+/* Per-row summaries of R rows from S retained samples (samples [S][R][K]).
+ *   mode 0, moment matching: one component fitted to all samples;
+ *   mode 1, dominant mode: one component fitted to the largest lambda-means cluster;
+ *   mode 2, mixture: one component for each of the C largest clusters (ties: lowest cluster
+ *           index) that has at least K + 1 samples, weights proportional to their sizes.
+ * A row whose clusters are all too small for a full-rank covariance falls back to moment
+ * matching.  Outputs: pi [R][C] (0 for unused components), mu [R][C][K], Lam [R][C][K][K];
+ * pooled_mu [R][K] and pooled_Lam [R][K][K], the mean of the fitted mixture and the inverse of
+ * its covariance sum_c pi_c (Lam_c^{-1} + (mu_c - m)(mu_c - m)^T), which the aggregation of
+ * Eq. 14 takes (Section 4.2, pooled mixture components). */
+int orc_fit_summaries(int K, int64_t R, int S, const double *samples, int mode, int C,
+                      double lambda, double *pi, double *mu, double *Lam, double *pooled_mu,
+                      double *pooled_Lam, int64_t *bad_row)
+{
+    size_t KK = (size_t)K * K;
+    double *x = (double *)malloc(sizeof(double) * (size_t)S * K);
+    int *assign = (int *)malloc(sizeof(int) * (size_t)(S > 0 ? S : 1));
+    int *size = (int *)malloc(sizeof(int) * (size_t)(S > 0 ? S : 1));
+    double *w = (double *)malloc(sizeof(double) * (3 * KK + K));
+    if (!x || !assign || !size || !w) {
+        free(x); free(assign); free(size); free(w);
+        return ORC_NOMEM;
+    }
+    double *Sig = w, *work = w + KK;   /* Sig [KK]; work [KK + K], or cov [KK] + work [KK + K] */
+    int status = ORC_OK;
+    for (int64_t r = 0; r < R && status == ORC_OK; ++r) {
+        for (int s = 0; s < S; ++s)
+            for (int k = 0; k < K; ++k) x[(size_t)s * K + k] = samples[((size_t)s * R + r) * K + k];
+        double *pir = pi + r * C, *mur = mu + r * (int64_t)C * K, *Lr = Lam + r * (int64_t)C * KK;
+        for (int c = 0; c < C; ++c) pir[c] = 0.0;
+        int used = 0;
+        if (mode != 0) {
+            const int n = orc_lambda_means(K, S, x, lambda, 100, assign);
+            if (n < 0) { status = ORC_NOMEM; break; }
+            for (int c = 0; c < n; ++c) size[c] = 0;
+            for (int s = 0; s < S; ++s) size[assign[s]]++;
+            const int want = mode == 1 ? 1 : C;
+            for (int t = 0; t < want; ++t) {
+                int best = -1;                       /* t-th largest, ties to the lowest index */
+                for (int c = 0; c < n; ++c)
+                    if (size[c] >= 0 && (best < 0 || size[c] > size[best])) best = c;
+                if (best < 0) break;
+                const int sz = size[best];
+                size[best] = -1;                     /* taken */
+                if (sz < K + 1) continue;
+                const int st = fit_gaussian(K, S, x, assign, best, mur + (size_t)used * K,
+                                            Lr + (size_t)used * KK);
+                if (st == ORC_NOMEM) { status = st; break; }
+                if (st) continue;
+                pir[used++] = sz;
+            }
+        }
+        if (status) break;
+        if (used == 0) {                              /* moment matching over all samples */
+            const int st = fit_gaussian(K, S, x, NULL, -1, mur, Lr);
+            if (st) {
+                if (bad_row) *bad_row = r;
+                status = st;
+                break;
+            }
+            pir[0] = 1.0;
+            used = 1;
+        }
+        double tot = 0.0;
+        for (int c = 0; c < used; ++c) tot += pir[c];
+        for (int c = 0; c < used; ++c) pir[c] /= tot;
+        /* pooled mean and covariance of the mixture */
+        double *pm = pooled_mu + r * K;
+        for (int k = 0; k < K; ++k) {
+            double s = 0.0;
+            for (int c = 0; c < used; ++c) s += pir[c] * mur[(size_t)c * K + k];
+            pm[k] = s;
+        }
+        for (size_t a = 0; a < KK; ++a) Sig[a] = 0.0;
+        for (int c = 0; c < used; ++c) {
+            double *cov = w + KK;                     /* Lam_c^{-1} */
+            if (spd_inverse(K, Lr + (size_t)c * KK, cov, w + 2 * KK)) {
+                if (bad_row) *bad_row = r;
+                status = ORC_NOT_PD;
+                break;
+            }
+            const double *mc = mur + (size_t)c * K;
+            for (int a = 0; a < K; ++a)
+                for (int b = 0; b < K; ++b)
+                    Sig[a * K + b] += pir[c] * (cov[a * K + b] + (mc[a] - pm[a]) * (mc[b] - pm[b]));
+        }
+        if (status) break;
+        if (spd_inverse(K, Sig, pooled_Lam + r * (int64_t)KK, work)) {
+            if (bad_row) *bad_row = r;
+            status = ORC_NOT_PD;
+        }
+    }
+    free(x); free(assign); free(size); free(w);
+    return status;
+}
+
+/* Component choice of a mixture prior (Section 5.1, GMM prior): for each row, the component
+ * with the largest responsibility pi_c N(x_r; mu_c, Lam_c^{-1}) at the row's current value x_r
+ * (log pi_c + (1/2) log det Lam_c - (1/2)(x_r - mu_c)^T Lam_c (x_r - mu_c); ties go to the
+ * lowest index; components with pi_c = 0 are skipped); its mean and precision are written to
+ * mu_out [R][K] and Lam_out [R][K][K], the per-row prior of the next draw of x_r.
+ * chosen [R] (nullable) receives the component. */
+int orc_mix_choose(int K, int64_t R, int C, const double *pi, const double *mu, const double *Lam,
+                   const double *X, int *chosen, double *mu_out, double *Lam_out)
+{
+    size_t KK = (size_t)K * K;
+    double *L = (double *)malloc(sizeof(double) * (KK + K));
+    if (!L) return ORC_NOMEM;
+    double *d = L + KK;
+    for (int64_t r = 0; r < R; ++r) {
+        int best = -1;
+        double sbest = -INFINITY;
+        for (int c = 0; c < C; ++c) {
+            const double p = pi[r * C + c];
+            if (!(p > 0.0)) continue;
+            const double *m = mu + (r * C + c) * (int64_t)K;
+            const double *A = Lam + (r * C + c) * (int64_t)KK;
+            if (chol_lower(K, A, L)) { free(L); return ORC_NOT_PD; }
+            double logdet = 0.0;
+            for (int k = 0; k < K; ++k) logdet += 2.0 * log(L[k * K + k]);
+            for (int k = 0; k < K; ++k) d[k] = X[r * K + k] - m[k];
+            double q = 0.0;                          /* (x - mu)^T A (x - mu) */
+            for (int a = 0; a < K; ++a) {
+                double s = 0.0;
+                for (int b = 0; b < K; ++b) s += A[a * K + b] * d[b];
+                q += d[a] * s;
+            }
+            const double score = log(p) + 0.5 * logdet - 0.5 * q;
+            if (best < 0 || score > sbest) {
+                best = c;
+                sbest = score;
+            }
+        }
+        if (best < 0) { free(L); return ORC_NOT_PD; }
+        if (chosen) chosen[r] = best;
+        memcpy(mu_out + r * K, mu + (r * C + best) * (int64_t)K, sizeof(double) * K);
+        memcpy(Lam_out + r * (int64_t)KK, Lam + (r * C + best) * (int64_t)KK, sizeof(double) * KK);
+    }
+    free(L);
+    return ORC_OK;
+}
