@@ -8,7 +8,8 @@ the library never imports this package.
 
 Layout:
   * ``bmf_oracle.c``  -- FP64 numerical core (conditionals, Normal-Wishart draw, moment
-    matching, Algorithm 2 aggregation, log-joint gradient), compiled with gcc into
+    matching and the dominant-mode / mixture summaries, Algorithm 2 aggregation, log-joint
+    gradient), compiled with gcc into
     ``oracle/_build/liborc.so`` (single thread: the tests and the CPU baseline) and, on
     request (``use_openmp``), into ``liborc_omp.so`` with the row conditionals split over
     threads (same results; the all-core timing).
