@@ -691,9 +691,76 @@ def cpu_all_cores(d, budget):
                       f"generation excluded; hyperparameter step and moments single-threaded)"}
 
 
+def _reference_line(metric, v, unit, n, secs, config, sample, warmup=0):
+    return {"impl": "reference", "metric": metric, "value": v, "unit": unit, "n_gpus": 1,
+            "steps": n, "warmup": warmup, "ms_per_step": secs * 1e3 / n,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config,
+            "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def reference_pp(args, d):
+    """The oracle on the PP workload's metric: one sweep of every subset of each stage (the
+    stage's batch), timed stage by stage; the propagated factors carry unit Gaussian priors (a
+    sweep's cost does not depend on their values).  Draw generation is outside the clock."""
+    import oracle
+    from paper_1703_00734_gb300 import synth
+    K, I, J = d["K"], d["I"], d["J"]
+    p = oracle.plan(d["N"], d["D"], d["row"], d["col"], d["val"], I, J)
+    prior = oracle.NWPrior(K)
+    finals = {s.sid: (np.zeros((s.n, K)), np.tile(np.eye(K), (s.n, 1, 1)),
+                      np.zeros((s.d, K)), np.tile(np.eye(K), (s.d, 1, 1))) for s in p.subsets}
+    X0, W0 = d["X0"][p.row_perm], d["W0"][p.col_perm]
+    secs = 0.0
+    for stage in (1, 2, 3):
+        subs = p.stage_subsets(stage)
+        chains = oracle.setup_stage_chains(p, stage, X0, W0, K, finals)
+        dr = synth.sweep_draws([(s.n, s.d) for s in subs], K, prior.nu0, synth.rng_for(901, stage))
+        t0 = time.perf_counter()
+        oracle.run_stage(p, stage, chains, K, d["tau"], prior, lambda t: dr, 1)
+        secs += time.perf_counter() - t0
+    return _reference_line("PP stage sweeps/s (all subsets of a stage batched)", 3 / secs,
+                           "stage sweeps/s", 3, secs,
+                           {"workload": args.workload, "K": K, "grid": f"{I}x{J}",
+                            "precision": "fp64"},
+                           "one sweep of each of the three stages' batches, single thread, "
+                           f"{secs:.1f} s")
+
+
+def reference_adjoint(args, d):
+    """The oracle's FP64 gradient of the masked log-joint at the initial state, time-bounded."""
+    import oracle
+    K = d["K"]
+    X, W = np.asarray(d["X0"], np.float64), np.asarray(d["W0"], np.float64)
+    mu, Lam = np.zeros(K), np.eye(K)
+    la = float(np.log(d["tau"]))
+    n, secs = 0, 0.0
+    while n == 0 or (secs < args.cpu_seconds and n < max(args.steps, 1)):
+        t0 = time.perf_counter()
+        oracle.logjoint_grad(d["row"], d["col"], d["val"], X, W, la, mu, Lam, mu, Lam)
+        secs += time.perf_counter() - t0
+        n += 1
+    return _reference_line("log-joint gradient evaluations/s (adjoint, K=64)", n / secs,
+                           "grad evals/s", n, secs,
+                           {"workload": args.workload, "N": d["N"], "D": d["D"],
+                            "train_obs": len(d["row"]), "K": K},
+                           f"{n} FP64 gradient evaluations of the whole data, single thread")
+
+
 def run_reference(args, rank):
     if rank != 0:
         return None
+    from paper_1703_00734_gb300 import synth as _synth
+    mode = MODES.get(args.workload)
+    if mode == "partitions":
+        return {"impl": "reference", "unavailable": "the metric is the test RMSE after 3 x 1200 "
+                "sweeps per grid, which the single-thread oracle does not reach in a bounded run"}
+    if _synth.WORKLOADS.get(args.workload, {}).get("I", 1) > 1:
+        return reference_pp(args, load_workload(args.workload, args.scale))
+    if mode == "adjoint":
+        return reference_adjoint(args, load_workload(args.workload, args.scale))
     d = load_workload(args.workload)
     n, secs = oracle_sweeps(d, args.cpu_seconds * 4, max(args.steps, 1),
                             warmup=min(args.warmup, 1))
