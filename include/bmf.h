@@ -169,6 +169,20 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
                     const int32_t *test_row, const int32_t *test_col, const double *test_val,
                     void *stream);
 
+/* Host-only preprocessing, exactly as bmf_init performs it, without a GPU or any device memory
+ * (to check a data set and its grid before creating a context): validates the COO training data
+ * (indices in range, no duplicate (row, col), finite values), orders rows and columns
+ * (order = BMF_ORDER_NONE or BMF_ORDER_DECREASING, Section 5.2) and cuts the I x J grid
+ * (row_bounds / col_bounds as for bmf_init, NULL for equal cuts).  Outputs, host, nullable:
+ *   row_perm [N], col_perm [D]: original index at each reordered position;
+ *   row_bounds_out [I+1], col_bounds_out [J+1]: the cuts in the reordered order;
+ *   subset_nnz [I*J]: training entries of subset s = i*J + j.
+ * Errors as bmf_init (BMF_E_ARG, BMF_E_SHAPE, BMF_E_NONFINITE), message via bmf_last_error(NULL). */
+bmf_status bmf_plan(int64_t N, int64_t D, int64_t nnz, const int32_t *row, const int32_t *col,
+                    const double *val, int32_t order, int32_t I, const int64_t *row_bounds,
+                    int32_t J, const int64_t *col_bounds, int64_t *row_perm, int64_t *col_perm,
+                    int64_t *row_bounds_out, int64_t *col_bounds_out, int64_t *subset_nnz);
+
 /* Number of doubles of one sweep's draw buffer for a batch: the subsets of `stage` (1..3)
  * when subset < 0, else the single subset `subset`. */
 int64_t bmf_draws_per_sweep(const bmf_ctx *ctx, int32_t stage, int32_t subset);
@@ -326,7 +340,7 @@ bmf_status bmf_aggregate_static(int32_t K, int64_t R, int32_t J, const double *m
                                 int64_t *n_corrected, void *stream);
 
 /* Message of the last failed call on ctx; with ctx NULL, of the last failed call of this thread
- * that takes no context (bmf_init, bmf_aggregate_static). */
+ * that takes no context (bmf_init, bmf_plan, bmf_aggregate_static). */
 const char *bmf_last_error(const bmf_ctx *ctx);
 
 #ifdef __cplusplus

@@ -125,6 +125,8 @@ def load(path: str = LIB_PATH):
     L.bmf_autotune.restype = st
     L.bmf_generate_draws.argtypes = [P, i32, i32, i64, i32, P, i32]
     L.bmf_generate_draws.restype = st
+    L.bmf_plan.argtypes = [i64, i64, i64, P, P, P, i32, i32, P, i32, P, P, P, P, P, P]
+    L.bmf_plan.restype = st
     L.bmf_destroy.argtypes = [P]
     L.bmf_destroy.restype = None
     L.bmf_last_error.argtypes = [P]
@@ -151,6 +153,24 @@ def aggregate_static(K, R, J, mu_ptr, lam_ptr, out_ptr, eps_rel=1e-6, stream=Non
     if st:
         raise BmfError(st, L.bmf_last_error(None).decode())
     return nc.value
+
+
+def plan(N, D, row, col, val, I=1, J=1, order="decreasing", row_bounds=None, col_bounds=None):
+    """The library's host-side preprocessing alone (bmf_plan: no GPU needed): row/column
+    order, grid cuts and training entries per subset."""
+    L = load()
+    row, col, val = _arr(row, np.int32), _arr(col, np.int32), _arr(val, np.float64)
+    rb = None if row_bounds is None else _arr(row_bounds, np.int64)
+    cb = None if col_bounds is None else _arr(col_bounds, np.int64)
+    out = dict(row_perm=np.zeros(N, np.int64), col_perm=np.zeros(D, np.int64),
+               row_bounds=np.zeros(I + 1, np.int64), col_bounds=np.zeros(J + 1, np.int64),
+               subset_nnz=np.zeros(I * J, np.int64))
+    s = L.bmf_plan(N, D, len(row), _ptr(row), _ptr(col), _ptr(val), ORDER[order], I, _ptr(rb), J,
+                   _ptr(cb), _ptr(out["row_perm"]), _ptr(out["col_perm"]),
+                   _ptr(out["row_bounds"]), _ptr(out["col_bounds"]), _ptr(out["subset_nnz"]))
+    if s:
+        raise BmfError(s, L.bmf_last_error(None).decode())
+    return out
 
 
 class BMF:

@@ -2132,6 +2132,34 @@ void bmf_destroy(bmf_ctx *c)
     delete c;
 }
 
+bmf_status bmf_plan(int64_t N, int64_t D, int64_t nnz, const int32_t *row, const int32_t *col,
+                    const double *val, int32_t order, int32_t I, const int64_t *row_bounds,
+                    int32_t J, const int64_t *col_bounds, int64_t *row_perm, int64_t *col_perm,
+                    int64_t *row_bounds_out, int64_t *col_bounds_out, int64_t *subset_nnz)
+{
+    g_init_error.clear();
+    g_noctx_msg = nullptr;
+    if (order != BMF_ORDER_NONE && order != BMF_ORDER_DECREASING) {
+        g_init_error = "unknown order";
+        return BMF_E_ARG;
+    }
+    HostPlan P;
+    std::string err;
+    const int st = build_plan(N, D, nnz, row, col, val, order, 0, I, row_bounds, J, col_bounds, 0,
+                              nullptr, nullptr, nullptr, P, err);
+    if (st) {
+        g_init_error = err;
+        return (bmf_status)st;
+    }
+    if (row_perm) std::copy(P.row_perm.begin(), P.row_perm.end(), row_perm);
+    if (col_perm) std::copy(P.col_perm.begin(), P.col_perm.end(), col_perm);
+    if (row_bounds_out) std::copy(P.row_bounds.begin(), P.row_bounds.end(), row_bounds_out);
+    if (col_bounds_out) std::copy(P.col_bounds.begin(), P.col_bounds.end(), col_bounds_out);
+    if (subset_nnz)
+        for (int s = 0; s < I * J; ++s) subset_nnz[s] = P.subs[s].nnz;
+    return BMF_OK;
+}
+
 const char *bmf_last_error(const bmf_ctx *c)
 {
     if (!c) return g_noctx_msg ? g_noctx_msg : g_init_error.c_str();
