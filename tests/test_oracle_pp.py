@@ -170,3 +170,46 @@ def test_theorem1_with_singular_differences_stays_close(orc):
                            np.tile(np.arange(D, dtype=np.int32), N), Y.ravel(), W, tau, mp, Lp,
                            z0)
     np.testing.assert_allclose(mstar, full, atol=1e-6)
+
+
+def test_stage_sources_and_hyperparameter_rule(orc):
+    """Algorithm 1's propagation sources and the stage-wise rule of Section 5.1: stage 2 (i,0)
+    takes W^(0) from (0,0), (0,j) takes X^(0) from (0,0); stage 3 (i,j) takes X from (i,0) and
+    W from (0,j); a propagated factor starts at the propagated mean and draws no
+    hyperparameters, a non-propagated one draws them (its mu, Lambda move off the start)."""
+    rng = np.random.default_rng(21)
+    K, I, J = 2, 3, 3
+    d = synth.make_workload(None, N=60, D=45, M=1500, pattern="uniform", K=K, sigma=0.5,
+                            tau=4.0, seed=22)
+    p = orc.plan(d["N"], d["D"], d["row"], d["col"], d["val"], I, J)
+    # recognisable per-subset summaries: subset s has mean 10 s + 1 (X) and -(10 s + 1) (W)
+    finals = {s.sid: (np.full((s.n, K), 10.0 * s.sid + 1), np.tile(np.eye(K), (s.n, 1, 1)),
+                      np.full((s.d, K), -(10.0 * s.sid + 1)), np.tile(np.eye(K), (s.d, 1, 1)))
+              for s in p.subsets}
+    X0, W0 = d["X0"][p.row_perm], d["W0"][p.col_perm]
+    prior = orc.NWPrior(K)
+    for stage in (2, 3):
+        chains = orc.setup_stage_chains(p, stage, X0, W0, K, finals)
+        for s in p.stage_subsets(stage):
+            st = chains[s.sid]
+            if stage == 2:
+                src_x = None if s.j == 0 else 0
+                src_w = 0 if s.j == 0 else None
+            else:
+                src_x, src_w = s.i * J, s.j
+            assert st.prior_x == (src_x is not None) and st.prior_w == (src_w is not None)
+            if src_x is not None:
+                np.testing.assert_array_equal(st.muX_row, finals[src_x][0])
+                np.testing.assert_array_equal(st.X, finals[src_x][0])
+            if src_w is not None:
+                np.testing.assert_array_equal(st.muW_row, finals[src_w][2])
+                np.testing.assert_array_equal(st.W, finals[src_w][2])
+        subs = p.stage_subsets(stage)
+        before = {sid: (st.muX.copy(), st.muW.copy()) for sid, st in chains.items()}
+        dr = synth.sweep_draws([(s.n, s.d) for s in subs], K, prior.nu0, rng)
+        orc.run_stage(p, stage, chains, K, d["tau"], prior, lambda t: dr, 1)
+        for s in subs:
+            st = chains[s.sid]
+            mx0, mw0 = before[s.sid]
+            assert np.array_equal(st.muX, mx0) == bool(st.prior_x)   # drawn iff not propagated
+            assert np.array_equal(st.muW, mw0) == bool(st.prior_w)
