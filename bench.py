@@ -1,20 +1,25 @@
 #!/usr/bin/env python
-"""Benchmark of the BPMF Gibbs sweep (Qin et al., arXiv 1703.00734, Section 5.1) on one GB300.
+"""Benchmark of the BPMF Gibbs sweep inside posterior propagation (Qin et al., arXiv 1703.00734,
+Algorithm 1, Eq. 14 / Algorithm 2, Section 5.1) on one GB300.
 
-A step is one full Gibbs sweep of the plain sampler on the 69,878 x 10,677 Zipf(1.2) rating
-matrix with 10M observations (9M train), K = 10: Normal-Wishart draws for both factors, the
-Gram-gather and FP64 conditional draw of every row and every column, and the test-RMSE pass.
-The headline `value` is sweeps/s of the reduced-precision path (FP32 gathers and Gram, FP64
-Cholesky/Wishart), inputs resident in HBM; the plain FP64 GPU sweep and the test RMSE of both
-are reported beside it.  `--impl reference` times the FP64 CPU oracle instead.
+Default workload pp4x4-100000x20000-20M-k16: a 100,000 x 20,000 Zipf(1.2) matrix with 20M
+observations (18M train), Gaussian values of a rank-16 truth plus noise, K = 16, on a 4 x 4 grid
+(stage sizes 1 / 6 / 9 subsets of uneven size).  A step is one whole PP run: the three stages of
+200 sweeps each (burn-in 100; all subsets of a stage batched into the same launches; FP32
+gathers and Gram, FP64 Cholesky/Wishart/moments), moment matching and propagation between
+stages, the eigenvalue-corrected aggregation and the prediction of the held-out entries.  The
+headline `value` is PP sweeps/s (a PP sweep sweeps every subset chain of the three stages once,
+visiting each training entry once per half-sweep, like a plain sweep of the whole matrix), with
+the plain FP64 and FP32 samplers on the whole matrix at the same sweep count and the test RMSE
+of all three beside it, plus the plain-sweep benchmark of the 69,878 x 10,677 Zipf matrix
+(`plain_sweep_zipf`).  `--impl reference` times the FP64 CPU oracle instead.
 
-Other workloads (--workload): a workload with an I x J grid (pp4x4-100000x20000-20M-k16) runs
-the three batched posterior-propagation stages, aggregation and prediction against the plain
-FP64 and reduced-precision samplers at the same sweep count; uniform-200000x50000-50M-k64 times
-the log-joint adjoint, Langevin moves and Gibbs sweeps at K = 64; sim-6040x3706-k5 and
-sim-6040x3706-k5-structured run PP on 1x1 ... 30x30 grids in both row/column orders and report
-test RMSE and time per partition (the paper's simulated-data experiment); any other named
-workload runs the plain-sweep benchmark above on it.
+Other workloads (--workload): zipf-69878x10677-10M-k10 and zipf-480189x17770-100M-k32 run the
+plain-sweep benchmark (a step is one Gibbs sweep of the 1 x 1 sampler);
+uniform-200000x50000-50M-k64 times the log-joint adjoint, Langevin moves and Gibbs sweeps at
+K = 64; sim-6040x3706-k5 and sim-6040x3706-k5-structured run PP on 1x1 ... 30x30 grids in both
+row/column orders and report test RMSE and time per partition (the paper's simulated-data
+experiment).
 
 Prints ONE JSON line (rank 0).  For --gpus N > 1 (torchrun) every rank runs an independent
 replica of the workload (one chain does not shard across GPUs) and value sums them.
@@ -35,7 +40,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "zipf-69878x10677-10M-k10"
+WORKLOAD = "pp4x4-100000x20000-20M-k16"
+PLAIN_WORKLOAD = "zipf-69878x10677-10M-k10"
 METRIC = "Gibbs sweeps/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 ALU peak: 152 SMs x 2 FP64 FMA/clock x 2 FLOP x 2.07 GHz (unit count and maximum clock
@@ -312,7 +318,7 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32+f64" if args.precision != "fp64" else "f64",
         "data": "synthetic (seeded Zipf(1.2) rating matrix standing in for a MovieLens-shaped "
                 "data set; no real data available)",
-        "config": {"workload": WORKLOAD if args.workload == WORKLOAD else args.workload,
+        "config": {"workload": args.workload,
                    "N": d["N"], "D": d["D"], "train_obs": M, "test_obs": len(d["test_row"]),
                    "K": K, "tau": tau, "precision": args.precision, "grid": "1x1",
                    "l2": "inputs larger than L2 (observation lists 144 MB > 129 MB L2)",
@@ -331,7 +337,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
-    if world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
+    if world == 1 and not args.no_cpu_baseline and args.workload == PLAIN_WORKLOAD:
         out["cpu_baseline"] = cpu_baseline(d, args.cpu_seconds)
         out["cpu_all_cores"] = cpu_all_cores(d, args.cpu_seconds)
     return out
@@ -340,110 +346,272 @@ def run_ours(args, rank, world, local_rank):
 # ---------------------------------------------------------------------------------------
 # posterior propagation on an I x J grid: three batched stages, then Algorithm 2
 # ---------------------------------------------------------------------------------------
-PP_CHUNK = 25
+PP_SWEEPS, PP_BURNIN = 200, 100      # per stage (100 retained samples, K + 1 <= 100)
+PP_CLASSES = ("gram_x", "cond_x", "gram_w", "cond_w")
+
+
+def stage_geometry(m, I, J):
+    """Per stage: X rows, W rows and training entries of its subsets (every training entry is
+    in exactly one subset, so the three stages together visit each once per half-sweep)."""
+    g = {1: [0, 0, 0], 2: [0, 0, 0], 3: [0, 0, 0]}
+    for sid in range(I * J):
+        info = m.subset_info(sid)
+        q = g[info["stage"]]
+        q[0] += info["row1"] - info["row0"]
+        q[1] += info["col1"] - info["col0"]
+        q[2] += info["nnz"]
+    return g
+
+
+def pp_algorithmic(geom, K, prec):
+    """Algorithmic work per launch of each kernel class in each stage (one launch per class and
+    sweep with one row chunk): Gram pass bytes = entries x (index + value + gathered partner
+    row); conditional FLOPs = rows x 2 x (assembly + Cholesky + two solves) FMAs."""
+    b = {"fp64": 8, "fp32": 4, "bf16": 2}[prec]
+    bval = 8 if prec == "fp64" else 4
+    per_obs = 4 + bval + K * b
+    fma_row = K * (K + 1) // 2 + K + (K ** 3 - K) // 6 + K * (K - 1)
+    out = {}
+    for st, (nx, nw, nnz) in geom.items():
+        out[(st, "gram_x")] = ("hbm", nnz * per_obs, "GB/s")
+        out[(st, "gram_w")] = ("hbm", nnz * per_obs, "GB/s")
+        out[(st, "cond_x")] = ("alu", 2.0 * fma_row * nx, "TFLOP/s")
+        out[(st, "cond_w")] = ("alu", 2.0 * fma_row * nw, "TFLOP/s")
+    return out
+
+
+def pp_kernel_table(prof_by_stage, algo, hbm):
+    """Per (stage, kernel class): launches, mean launch time and, for the Gram and conditional
+    classes, achieved work against the peak.  `stream_time_share` is the class's summed launch
+    time over the summed time of all classes: classes on side streams (hyperparameter draws,
+    test RMSE, generator) overlap the main stream, so it is not a critical-path share."""
+    rows = {}
+    total = sum(t for prof in prof_by_stage.values() for (_, t) in prof.values())
+    for st, prof in prof_by_stage.items():
+        for name, (n, t) in prof.items():
+            if n == 0:
+                continue
+            ent = {"stage": st, "kernel": name, "launches": n, "avg_us": t / n * 1e3,
+                   "stream_time_share": t / total if total else None}
+            if (st, name) in algo:
+                bound, work, unit = algo[(st, name)]
+                ach = work / (t / n / 1e3) / (1e9 if unit == "GB/s" else 1e12)
+                peak = hbm if unit == "GB/s" else FP64_PEAK_TFLOPS
+                ent.update(bound=bound, work_per_launch=work, achieved=ach, peak=peak,
+                           unit=unit, frac=ach / peak)
+            rows[f"s{st}.{name}"] = ent
+    return rows
 
 
 def run_pp(args, rank, world, local_rank):
+    """A step is one whole PP run (Algorithm 1, then Algorithm 2): the three stages of
+    PP_SWEEPS sweeps each (burn-in PP_BURNIN; every stage's subsets batched into the same
+    launches; device generator), moment matching and propagation between stages, the
+    eigenvalue-corrected aggregation and the posterior-mean prediction of the held-out entries.
+    The context restarts every chain before each step (bmf_restart, a new seed per step).
+    value = PP sweeps/s: one PP sweep is one sweep of every subset chain of the three stages,
+    which visits every training entry once per half-sweep, as a plain sweep of the whole matrix
+    does; the plain FP64 and reduced-precision samplers run the same number of sweeps on the
+    whole matrix beside it."""
     import torch
-    from paper_1703_00734_gb300 import bmf, synth
+    from paper_1703_00734_gb300 import bmf
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
     d = load_workload(args.workload, args.scale)
     K, tau, I, J = d["K"], d["tau"], d["I"], d["J"]
-    T, B = args.steps, max(1, args.steps // 2)
+    T, B = args.pp_sweeps, args.pp_burnin
+    if T - B < K + 1:
+        raise SystemExit(f"--pp-sweeps minus --pp-burnin must keep at least K + 1 = {K + 1} "
+                         "samples per chain for moment matching")
     test = (d["test_row"], d["test_col"], d["test_val"])
+    M, n_test = len(d["row"]), len(d["test_row"])
+    Wu, S = max(1, args.warmup), args.steps
+    seed0 = 1000 * (rank + 1)
+    t0 = time.perf_counter()
     m = bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], K, tau, args.precision, I=I, J=J,
-                X0=d["X0"], W0=d["W0"], burnin=B, seed=rank, stream=stream.cuda_stream)
-    stage_ms, launches, sizes_all, schedules = [], 0, {}, {}
-    with ClockSampler(local_rank) as clk:
+                X0=d["X0"], W0=d["W0"], test=test, burnin=B, seed=seed0,
+                stream=stream.cuda_stream)
+    init_ms = (time.perf_counter() - t0) * 1e3
+    # the per-sweep test-RMSE monitor is off: PP predicts once per run, from the aggregated
+    # posterior (bmf_test_rmse)
+    m.set_monitor(False)
+    geom = stage_geometry(m, I, J)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    # first (untimed) run: the schedule tuner on each stage's batch as it opens
+    schedules = {}
+    for stage in (1, 2, 3):
+        m.stage(stage, 0, None)                     # opens the stage (priors installed)
+        schedules[stage] = (m.autotune(stage, -1, 3) if not args.no_tune
+                            else m.get_schedule())
+        m.stage(stage, T, None)
+    m.test_rmse()
+
+    def pp_step(seed):
+        m.restart(seed)
         for stage in (1, 2, 3):
-            m.stage(stage, 0, None)                  # opens the stage (priors installed)
-            if not args.no_tune:
-                schedules[stage] = m.autotune(stage, -1, 3)
-            sizes = []
-            for sid in range(I * J):
-                info = m.subset_info(sid)
-                if info["stage"] == stage:
-                    sizes.append((info["row1"] - info["row0"], info["col1"] - info["col0"]))
-            sizes_all[stage] = sizes
-            ms = 0.0
-            for c0 in range(0, T, PP_CHUNK):    # draws in chunks of sweeps (host memory)
-                nc = min(PP_CHUNK, T - c0)
-                # per-kernel event tracing on the first chunk of each stage only (tracing turns
-                # the graph launch off)
-                m.profile(c0 == 0)
-                host = np.concatenate([synth.sweep_draws(sizes, K, float(K),
-                                                         synth.rng_for(300 + rank, stage, t))
-                                       for t in range(c0, c0 + nc)])
-                dr = torch.from_numpy(host).to(dev)
-                torch.cuda.synchronize()
-                n0 = m.launch_count()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                m.stage(stage, nc, dr)
-                e1.record(stream)
-                e1.synchronize()
-                ms += e0.elapsed_time(e1)
-                launches += m.launch_count() - n0
-                del dr
-            stage_ms.append(ms)
-        t0 = time.perf_counter()
-        yh, r_pp = m.predict(d["test_row"], d["test_col"], d["test_val"])
-        agg_ms = (time.perf_counter() - t0) * 1e3
-    prof = m.profile_read()
+            m.set_schedule(**schedules[stage])
+            m.stage(stage, T, None)
+        return m.test_rmse()
+
+    clk = ClockSampler(local_rank).__enter__()
+    clk.wait_first()
+    for w in range(1, Wu):
+        pp_step(seed0 + w)
+    torch.cuda.synchronize()
+    barrier(world)
+    n0 = m.launch_count()
+    rmses, run_ms = [], []
+    e0 = ev()
+    e0.record(stream)
+    for k in range(S):
+        a, b = ev(), ev()
+        a.record(stream)
+        rmses.append(pp_step(seed0 + 100 + k))
+        b.record(stream)
+        b.synchronize()
+        run_ms.append(a.elapsed_time(b))
+    e1 = ev()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = m.launch_count() - n0
+    clk.__exit__(None, None, None)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks(ms, world, dev)
+
+    # per-kernel timing: one more run, untimed, with the library's event tracing on and one
+    # launch per kernel class and half (no row chunks, no graph), stage by stage
+    m.restart(seed0 + 99)
+    prof_by_stage = {}
+    for stage in (1, 2, 3):
+        sc = dict(schedules[stage])
+        m.set_schedule(1, 1, sc["gram_blocks_per_sm"], 0.0, 0)
+        m.profile(True)
+        m.stage(stage, T, None)
+        prof_by_stage[stage] = m.profile_read()
+        m.profile(False)
+    m.test_rmse()
+
+    # e2e through the C ABI with host buffers: the initial state copied in from pinned host
+    # memory (bmf_restart), the three stages, and bmf_predict of the held-out entries given as
+    # pinned host arrays, the predictions copied back
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    hX0, hW0 = pin(d["X0"]), pin(d["W0"])
+    hr, hc, hv = pin(d["test_row"].astype(np.int32)), pin(d["test_col"].astype(np.int32)), \
+        pin(d["test_val"].astype(np.float64))
+    n_e2e = max(2, S // 4)
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    e2e_rmse = []
+    for k in range(n_e2e):
+        m.restart(seed0 + 200 + k, X0=hX0, W0=hW0)
+        for stage in (1, 2, 3):
+            m.set_schedule(**schedules[stage])
+            m.stage(stage, T, None)
+        yhat, r = m.predict(hr, hc, hv)
+        e2e_rmse.append(r)
+    e2e_s = time.perf_counter() - te
+    h2d = hX0.nbytes + hW0.nbytes + hr.nbytes + hc.nbytes + hv.nbytes
+    d2h = n_test * 8 + 8
     m.close()
-    # plain sampler on the whole matrix for the same number of sweeps
+
+    # the plain samplers on the whole matrix, same number of sweeps, device generator
     plain = {}
     for prec in ("fp64", args.precision):
         mp = bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], K, tau, prec, X0=d["X0"],
-                     W0=d["W0"], test=test, burnin=B, seed=rank, stream=stream.cuda_stream)
-        if not args.no_tune:
-            schedules["plain_" + prec] = mp.autotune(1, -1, 3)
-        ms = 0.0
-        for c0 in range(0, T, PP_CHUNK):
-            nc = min(PP_CHUNK, T - c0)
-            host = np.concatenate([synth.sweep_draws([(d["N"], d["D"])], K, float(K),
-                                                     synth.rng_for(400 + rank, t))
-                                   for t in range(c0, c0 + nc)])
-            dr = torch.from_numpy(host).to(dev)
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            mp.sweep(0, nc, dr)
-            b.record(stream)
-            b.synchronize()
-            ms += a.elapsed_time(b)
-            del dr
-        _, r_plain = mp.predict(d["test_row"], d["test_col"], d["test_val"])
-        plain[prec] = {"ms": ms, "sweeps_per_s": T / (ms / 1e3), "rmse": r_plain}
+                     W0=d["W0"], test=test, burnin=B, seed=seed0 + 7, stream=stream.cuda_stream)
+        mp.set_monitor(False)
+        sch = mp.autotune(1, -1, 3) if not args.no_tune else mp.get_schedule()
+        mp.sweep(0, 2, None)
+        mp.restart(seed0 + 7)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        mp.sweep(0, T, None)
+        r = mp.test_rmse()
+        b.record(stream)
+        b.synchronize()
+        pms = a.elapsed_time(b)
+        plain[prec] = {"sweeps_per_s": T / (pms / 1e3), "ms_per_run": pms, "sweeps": T,
+                       "burnin": B, "rmse": r, "schedule": sch}
         mp.close()
     if rank != 0:
         return None
-    M = len(d["row"])
-    total_ms = sum(stage_ms)
-    obs_sides = 2 * M   # every training entry is in exactly one subset, visited by both halves
-    kernels = {k: {"launches": n, "avg_us": t / n * 1e3} for k, (n, t) in prof.items() if n}
-    return {
-        "metric": "PP stage sweeps/s (all subsets of a stage batched)", "impl": "ours",
-        "value": 3 * T / (total_ms / 1e3), "unit": "stage sweeps/s", "n_gpus": world,
-        "steps": 3 * T, "warmup": 0, "ms_per_step": total_ms / (3 * T), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": args.workload, "N": d["N"], "D": d["D"], "train_obs": M, "K": K,
-                   "grid": f"{I}x{J}", "subsets_per_stage": [len(sizes_all[s]) for s in (1, 2, 3)],
-                   "sweeps_per_stage": T, "burnin": B, "precision": args.precision},
-        "stage_ms": stage_ms, "aggregate_predict_ms": agg_ms,
-        "obsK2_gflops_pp": obs_sides / 3 * 3 * T * 2 * K * K / (total_ms / 1e3) / 1e9,
-        "rmse": {"pp": r_pp, "plain_fp64": plain["fp64"]["rmse"],
+    sweeps_s = whole_job_rate(S * T, ms, world)
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    algo = pp_algorithmic(geom, K, args.precision)
+    kernels = pp_kernel_table(prof_by_stage, algo, hbm)
+    dom = max((k for k in kernels if "bound" in kernels[k]),
+              key=lambda k: kernels[k]["avg_us"] * kernels[k]["launches"])
+    kd = kernels[dom]
+    roof = {"kernel": dom, "bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
+            "unit": kd["unit"], "frac": kd["frac"],
+            "traffic": traffic_for(dom, args.precision, args.workload),
+            "work_per_launch": kd["work_per_launch"],
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if kd["unit"] == "GB/s"
+            else "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"}
+    rmse_pp = float(np.mean(rmses))
+    r64 = plain["fp64"]["rmse"]
+    out = {
+        "metric": METRIC, "value": sweeps_s, "unit": "sweeps/s", "n_gpus": world, "steps": S,
+        "warmup": Wu, "ms_per_step": ms / S, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.precision != "fp64" else "f64",
+        "data": "synthetic (seeded Zipf(1.2) pattern, Gaussian values of a rank-16 truth plus "
+                "N(0, 0.5^2) noise; no real data available)",
+        "config": {"workload": args.workload, "N": d["N"], "D": d["D"], "train_obs": M,
+                   "test_obs": n_test, "K": K, "tau": tau, "grid": f"{I}x{J}",
+                   "subsets_per_stage": [sum(1 for s in range(I * J)
+                                             if m_stage(s, I, J) == st) for st in (1, 2, 3)],
+                   "sweeps_per_stage": T, "burnin": B, "precision": args.precision,
+                   "step": "one whole PP run: 3 stages x sweeps_per_stage sweeps (all subsets of "
+                           "a stage batched), moment matching, Algorithm 2, held-out prediction",
+                   "unit_of_value": "PP sweep = one sweep of every subset chain of the three "
+                                    "stages (each training entry visited once per half-sweep)",
+                   "draws": "device generator (Philox4x64-10), new seed per step",
+                   "monitor": "per-sweep test-RMSE monitor off (PP and plain); the held-out "
+                              "RMSE is computed once per run from the posterior means",
+                   "l2": "inputs larger than L2 (observation lists 288 MB > 129 MB L2)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "obsK2_gflops": 2 * M * 2 * K * K * sweeps_s / 1e9,
+        "stage_sweeps_per_s": 3 * sweeps_s,
+        "run_ms": {"mean": float(np.mean(run_ms)), "min": float(np.min(run_ms)),
+                   "max": float(np.max(run_ms))},
+        "rmse": {"pp_mean_over_steps": rmse_pp, "pp_min": float(np.min(rmses)),
+                 "pp_max": float(np.max(rmses)), "plain_fp64": r64,
                  "plain_reduced": plain[args.precision]["rmse"],
-                 "abs_diff_vs_plain_fp64": abs(r_pp - plain["fp64"]["rmse"])},
+                 "abs_diff_pp_vs_plain_fp64": abs(rmse_pp - r64),
+                 "budget": 0.002, "within_budget": abs(rmse_pp - r64) <= 0.002},
         "plain": plain,
-        "pp_speedup_vs_plain_fp64_same_sweeps": plain["fp64"]["ms"] / total_ms,
-        "kernels": kernels, "gpu_launches": launches, "clocks": clk.summary(),
-        "schedule": schedules,
+        "speedup_vs_plain_fp64": sweeps_s / world / plain["fp64"]["sweeps_per_s"],
+        "speedup_note": "PP sweeps/s over plain FP64 sweeps/s at the same sweeps per chain "
+                        f"({T}, burn-in {B}); |RMSE difference| beside it",
+        "roofline": roof,
+        "kernels": kernels,
+        "schedule": {f"stage{k}": v for k, v in schedules.items()},
+        "e2e": {"value": world * n_e2e * T / e2e_s, "unit": "sweeps/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "rmse_mean": float(np.mean(e2e_rmse)),
+                "what": "bmf_restart from pinned host X0/W0, 3 x bmf_stage, bmf_predict of the "
+                        "held-out entries from pinned host arrays with the predictions read "
+                        "back; host wall clock"},
+        "init_ms": init_ms,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
     }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_pp(d, args.cpu_seconds, threads=1)
+        out["cpu_all_cores"] = cpu_baseline_pp(d, args.cpu_seconds, threads=0)
+    return out
+
+
+def m_stage(sid, I, J):
+    i, j = divmod(sid, J)
+    return 1 if i == 0 and j == 0 else (2 if i == 0 or j == 0 else 3)
 
 
 # ---------------------------------------------------------------------------------------
@@ -691,42 +859,101 @@ def cpu_all_cores(d, budget):
                       f"generation excluded; hyperparameter step and moments single-threaded)"}
 
 
-def _reference_line(metric, v, unit, n, secs, config, sample, warmup=0):
+def _reference_line(metric, v, unit, n, secs, config, sample, warmup=0, cores=1,
+                    kind="oracle"):
     return {"impl": "reference", "metric": metric, "value": v, "unit": unit, "n_gpus": 1,
             "steps": n, "warmup": warmup, "ms_per_step": secs * 1e3 / n,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config,
-            "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": unit, "cores": cores, "kind": kind,
                              "sample": sample},
             "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def reference_pp(args, d):
-    """The oracle on the PP workload's metric: one sweep of every subset of each stage (the
-    stage's batch), timed stage by stage; the propagated factors carry unit Gaussian priors (a
-    sweep's cost does not depend on their values).  Draw generation is outside the clock."""
+class OraclePP:
+    """The oracle's PP sweeps on a grid workload: one PP sweep is one sweep of every subset of
+    stage 1, then of stage 2, then of stage 3 (each stage's batch), chains continuing from one
+    PP sweep to the next; the propagated factors carry unit Gaussian priors (a sweep's cost does
+    not depend on their values).  Draw generation is outside the clock."""
+
+    def __init__(self, d):
+        import oracle
+        self.d, self.K = d, d["K"]
+        self.p = oracle.plan(d["N"], d["D"], d["row"], d["col"], d["val"], d["I"], d["J"])
+        self.prior = oracle.NWPrior(self.K)
+        K = self.K
+        finals = {s.sid: (np.zeros((s.n, K)), np.tile(np.eye(K), (s.n, 1, 1)),
+                          np.zeros((s.d, K)), np.tile(np.eye(K), (s.d, 1, 1)))
+                  for s in self.p.subsets}
+        X0, W0 = d["X0"][self.p.row_perm], d["W0"][self.p.col_perm]
+        self.chains = {st: oracle.setup_stage_chains(self.p, st, X0, W0, K, finals)
+                       for st in (1, 2, 3)}
+        self.t = 0
+
+    def sweep(self):
+        """One PP sweep; returns its time in seconds."""
+        import oracle
+        from paper_1703_00734_gb300 import synth
+        secs = 0.0
+        for st in (1, 2, 3):
+            subs = self.p.stage_subsets(st)
+            dr = synth.sweep_draws([(s.n, s.d) for s in subs], self.K, self.prior.nu0,
+                                   synth.rng_for(901, st, self.t))
+            t0 = time.perf_counter()
+            oracle.run_stage(self.p, st, self.chains[st], self.K, self.d["tau"], self.prior,
+                             lambda t: dr, 1)
+            secs += time.perf_counter() - t0
+        self.t += 1
+        return secs
+
+
+def cpu_baseline_pp(d, budget, threads=1):
+    """The oracle's PP sweeps/s on the bench workload, time-bounded: single thread (threads=1)
+    or its OpenMP build over all host cores (threads=0; bit-identical results)."""
     import oracle
-    from paper_1703_00734_gb300 import synth
-    K, I, J = d["K"], d["I"], d["J"]
-    p = oracle.plan(d["N"], d["D"], d["row"], d["col"], d["val"], I, J)
-    prior = oracle.NWPrior(K)
-    finals = {s.sid: (np.zeros((s.n, K)), np.tile(np.eye(K), (s.n, 1, 1)),
-                      np.zeros((s.d, K)), np.tile(np.eye(K), (s.d, 1, 1))) for s in p.subsets}
-    X0, W0 = d["X0"][p.row_perm], d["W0"][p.col_perm]
-    secs = 0.0
-    for stage in (1, 2, 3):
-        subs = p.stage_subsets(stage)
-        chains = oracle.setup_stage_chains(p, stage, X0, W0, K, finals)
-        dr = synth.sweep_draws([(s.n, s.d) for s in subs], K, prior.nu0, synth.rng_for(901, stage))
-        t0 = time.perf_counter()
-        oracle.run_stage(p, stage, chains, K, d["tau"], prior, lambda t: dr, 1)
-        secs += time.perf_counter() - t0
-    return _reference_line("PP stage sweeps/s (all subsets of a stage batched)", 3 / secs,
-                           "stage sweeps/s", 3, secs,
-                           {"workload": args.workload, "K": K, "grid": f"{I}x{J}",
-                            "precision": "fp64"},
-                           "one sweep of each of the three stages' batches, single thread, "
-                           f"{secs:.1f} s")
+    try:
+        used = oracle.use_openmp(threads != 1) if threads != 1 else 1
+        o = OraclePP(d)
+        n, secs = 0, 0.0
+        while n == 0 or secs < budget:
+            secs += o.sweep()
+            n += 1
+    except Exception as e:                       # no OpenMP runtime on this host
+        return {"unavailable": f"oracle run failed: {e}"}
+    finally:
+        if threads != 1:
+            oracle.use_openmp(False)
+    return {"value": n / secs, "unit": "sweeps/s", "cores": used,
+            "kind": "oracle" if threads == 1 else "oracle, OpenMP over rows",
+            "sample": f"{n} PP sweeps (one sweep of every subset of the three stages) of the "
+                      f"same workload, FP64, {secs:.1f} s, draw generation outside the clock"}
+
+
+def reference_pp(args, d):
+    """The reference arm on the PP workload: the oracle as it stands, its OpenMP build on all
+    host cores (row conditionals split over threads, results bit-identical to one thread), on
+    the metric of our arm (sweeps/s; each step one PP sweep, a bounded sample of the same
+    workload: a whole run of 3 x 200 sweeps would take hours), W untimed and K timed steps."""
+    import oracle
+    try:
+        cores, kind = oracle.use_openmp(True), "oracle, OpenMP over rows"
+    except Exception:                            # no OpenMP runtime on this host
+        cores, kind = 1, "oracle"
+    try:
+        o = OraclePP(d)
+        for _ in range(args.warmup):
+            o.sweep()
+        n = max(args.steps, 1)
+        secs = sum(o.sweep() for _ in range(n))
+    finally:
+        oracle.use_openmp(False)
+    return _reference_line(METRIC, n / secs, "sweeps/s", n, secs,
+                           {"workload": args.workload, "N": d["N"], "D": d["D"],
+                            "train_obs": len(d["row"]), "test_obs": len(d["test_row"]),
+                            "K": d["K"], "grid": f"{d['I']}x{d['J']}", "precision": "fp64"},
+                           f"{n} PP sweeps (one sweep of every subset of the three stages), "
+                           f"{cores} threads, {secs:.1f} s, draw generation outside the clock",
+                           warmup=args.warmup, cores=cores, kind=kind)
 
 
 def reference_adjoint(args, d):
@@ -779,18 +1006,23 @@ def run_reference(args, rank):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
     ap.add_argument("--burnin", type=int, default=2)
+    ap.add_argument("--pp-sweeps", type=int, default=PP_SWEEPS,
+                    help="sweeps per stage of a PP run (grid workloads)")
+    ap.add_argument("--pp-burnin", type=int, default=PP_BURNIN)
     ap.add_argument("--fp64-steps", type=int, default=20)
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-plain-zipf", action="store_true",
+                    help="skip the plain-sweep benchmark added to the default PP line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch schedule instead of running the schedule tuner")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload (rows and columns by s, observations by s^2); "
                          "for profiling captures only, not a bench configuration")
@@ -809,6 +1041,12 @@ def main():
             torch.distributed.init_process_group("nccl")
         if pp:
             out = run_pp(args, rank, world, local_rank)
+            if args.workload == WORKLOAD and not args.no_plain_zipf and args.scale == 1.0:
+                sub = argparse.Namespace(**vars(args))
+                sub.workload = PLAIN_WORKLOAD
+                plain = run_ours(sub, rank, world, local_rank)
+                if out is not None:
+                    out["plain_sweep_zipf"] = plain
         elif MODES.get(args.workload) == "adjoint":
             out = run_adjoint(args, rank, world, local_rank)
         elif MODES.get(args.workload) == "partitions":

@@ -215,6 +215,15 @@ typedef struct {
 bmf_status bmf_set_schedule(bmf_ctx *ctx, const bmf_schedule *sched);
 bmf_status bmf_get_schedule(const bmf_ctx *ctx, bmf_schedule *sched);
 
+/* Per-sweep test-RMSE monitor (no counterpart in the paper, whose PP evaluates the final
+ * aggregated prediction only): with on = 1 (the default) every sweep predicts the held-out
+ * entries of its batch with the current sample and with the running mean of the retained
+ * samples, and bmf_sweep / bmf_stage report both RMSEs in bmf_sweep_stats; with on = 0 that pass
+ * is skipped, the two RMSE fields are NaN, and the running mean stops accumulating (turn it off
+ * for a whole run).  The sampled values do not depend on it; bmf_test_rmse and bmf_predict do
+ * not use it. */
+bmf_status bmf_set_monitor(bmf_ctx *ctx, int32_t on);
+
 /* Schedule tuner: on the batch of `stage` (subset < 0) or of one subset, times candidate
  * schedules -- Gram grid 2/4/8 blocks per SM, then 1-4 row chunks for each half, then the split
  * weight, then the CUDA-graph launch -- with one untimed and sweeps_per_trial timed sweeps each
@@ -243,6 +252,23 @@ bmf_status bmf_stage(bmf_ctx *ctx, int32_t stage, int32_t n_sweeps, const bmf_dr
  * yhat: host [n] or NULL; y: host [n] or NULL; rmse: RMSE against y (needs y) or NULL. */
 bmf_status bmf_predict(bmf_ctx *ctx, int64_t n, const int32_t *row, const int32_t *col,
                        const double *y, double *yhat, double *rmse);
+
+/* Test RMSE of the posterior-mean prediction (Section 5.2) of the held-out entries given to
+ * bmf_init, computed on the device: finalises the moments of the open stage, aggregates (Eq. 14,
+ * Algorithm 2; for a 1 x 1 grid the means of the retained samples) and predicts every held-out
+ * entry; only the RMSE is read back.  NaN without held-out entries.  Needs every stage run
+ * (BMF_E_STATE otherwise). */
+bmf_status bmf_test_rmse(bmf_ctx *ctx, double *rmse);
+
+/* Start a new run of Algorithm 1 on the same data and grid (no counterpart in the paper: a
+ * context reuses its preprocessed observation lists across independent runs).  Every subset's
+ * chain returns to the initial state: X0 [N*K] and W0init [D*K], host, ORIGINAL order, each
+ * replacing the stored initial state, or NULL to reuse the stored one (the one given to bmf_init
+ * or to the last bmf_restart).  Moment sums, running test predictions, hyperparameter draws,
+ * propagated priors and sweep counters are cleared, stage 1 is open again, and the device
+ * generator takes `seed`.  The launch schedule is kept.  Errors: BMF_E_NONFINITE (non-finite
+ * initial state; nothing changed), BMF_E_CUDA. */
+bmf_status bmf_restart(bmf_ctx *ctx, const double *X0, const double *W0init, uint64_t seed);
 
 /* Aggregated posterior means (Eq. 14 / Algorithm 2) in the ORIGINAL order: Xm [N*K],
  * Wm [D*K] host; n_corrected (nullable) counts eigenvalue-corrected (row, submodel) pairs. */
@@ -316,24 +342,25 @@ int64_t bmf_launch_count(const bmf_ctx *ctx);
 void bmf_destroy(bmf_ctx *ctx);
 
 /* Aggregation without allocating (no counterpart in the paper: a deployment addition).
- * Some callers cannot let a library call cudaMalloc: code running while a CUDA graph is being
- * captured, or a runtime that owns all device memory through its own allocator.  This call
- * combines, for R rows, the per-row Gaussians of J submodels by Eq. 14 with the eigenvalue
- * correction of Algorithm 2 (the same operation bmf_posterior_means applies to a context's
- * moment-matched subset posteriors) and allocates nothing: its per-row working matrices live in
- * a static device array of BMF_AGGREGATE_STATIC_MAX_DOUBLES doubles (32 MiB) that every GPU
- * loading this library holds until the process exits.
+ * Some callers cannot let a library call cudaMalloc: a runtime that owns all device memory
+ * through its own pool allocator, or a service that must not grow its device footprint after
+ * start-up.  This call combines, for R rows, the per-row Gaussians of J submodels by Eq. 14 with
+ * the eigenvalue correction of Algorithm 2 (the same operation bmf_posterior_means applies to a
+ * context's moment-matched subset posteriors) and allocates nothing: its per-row working
+ * matrices live in a static device array of BMF_AGGREGATE_STATIC_MAX_DOUBLES doubles (32 MiB)
+ * that every GPU loading this library holds until the process exits.
  *   mu:  device [J][R][K], Lam: device [J][R][K][K] (full symmetric precisions); submodel 0 is
  *        the one whose posterior was propagated to the others;
  *   mu_star: device [R][K] output; n_corrected: host, nullable (corrected (row, j) pairs);
  *   eps_rel as in bmf_config (<= 0: 1e-6); stream: cudaStream_t or NULL.
  * Limits: 1 <= K <= 16, J >= 1, R * K * K <= BMF_AGGREGATE_STATIC_MAX_DOUBLES (else
  * BMF_E_SHAPE; split the rows over several calls).  Returns BMF_E_NOT_PD if an aggregated
- * precision is not positive definite.  The call waits for its stream before returning.
+ * precision is not positive definite.  The call reads two counters back and waits for its
+ * stream before returning.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  All calls share the
- * array (each call clears its counters first); calls that overlap on the GPU race on it.
- * Errors are reported by bmf_last_error(NULL). */
+ * that device current and keeps it; calls after a cudaDeviceReset of that device are not
+ * supported.  All calls share the array (each call clears its counters first); calls that
+ * overlap on the GPU race on it.  Errors are reported by bmf_last_error(NULL). */
 #define BMF_AGGREGATE_STATIC_MAX_DOUBLES 4194272
 bmf_status bmf_aggregate_static(int32_t K, int64_t R, int32_t J, const double *mu,
                                 const double *Lam, double eps_rel, double *mu_star,

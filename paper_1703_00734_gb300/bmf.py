@@ -87,6 +87,10 @@ def load(path: str = LIB_PATH):
     L.bmf_stage.restype = st
     L.bmf_predict.argtypes = [P, i64, P, P, P, P, P]
     L.bmf_predict.restype = st
+    L.bmf_test_rmse.argtypes = [P, ctypes.POINTER(f64)]
+    L.bmf_test_rmse.restype = st
+    L.bmf_restart.argtypes = [P, P, P, ctypes.c_uint64]
+    L.bmf_restart.restype = st
     L.bmf_posterior_means.argtypes = [P, P, P, ctypes.POINTER(i64)]
     L.bmf_posterior_means.restype = st
     L.bmf_get_state.argtypes = [P, i32, P, P, P]
@@ -117,6 +121,8 @@ def load(path: str = LIB_PATH):
     L.bmf_langevin.restype = st
     L.bmf_aggregate_static.argtypes = [i32, i64, i32, P, P, f64, P, ctypes.POINTER(i64), P]
     L.bmf_aggregate_static.restype = st
+    L.bmf_set_monitor.argtypes = [P, i32]
+    L.bmf_set_monitor.restype = st
     L.bmf_set_schedule.argtypes = [P, ctypes.POINTER(Schedule)]
     L.bmf_set_schedule.restype = st
     L.bmf_get_schedule.argtypes = [P, ctypes.POINTER(Schedule)]
@@ -246,6 +252,10 @@ class BMF:
                       row_weight=float(row_weight), graph=int(graph))
         self._check(self.L.bmf_set_schedule(self.h, ctypes.byref(sc)))
 
+    def set_monitor(self, on=True):
+        """Per-sweep test-RMSE monitor on or off (bmf_set_monitor); sampled values unchanged."""
+        self._check(self.L.bmf_set_monitor(self.h, int(bool(on))))
+
     def get_schedule(self):
         sc = Schedule()
         self._check(self.L.bmf_get_schedule(self.h, ctypes.byref(sc)))
@@ -303,6 +313,20 @@ class BMF:
         self._check(self.L.bmf_predict(self.h, len(row), _ptr(row), _ptr(col), _ptr(ya),
                                        _ptr(out), ctypes.byref(r) if ya is not None else None))
         return out, (r.value if ya is not None else None)
+
+    def test_rmse(self):
+        """RMSE of the posterior-mean prediction of the held-out entries given at construction
+        (aggregated on the device; bmf_test_rmse)."""
+        r = ctypes.c_double()
+        self._check(self.L.bmf_test_rmse(self.h, ctypes.byref(r)))
+        return r.value
+
+    def restart(self, seed, X0=None, W0=None):
+        """A new run of Algorithm 1 on the same data (bmf_restart): every chain back to the
+        initial state (X0 / W0 in the original order replace the stored one when given)."""
+        Xa = None if X0 is None else _arr(X0, np.float64)
+        Wa = None if W0 is None else _arr(W0, np.float64)
+        self._check(self.L.bmf_restart(self.h, _ptr(Xa), _ptr(Wa), int(seed)))
 
     def posterior_means(self):
         Xm, Wm = np.zeros((self.N, self.K)), np.zeros((self.D, self.K))

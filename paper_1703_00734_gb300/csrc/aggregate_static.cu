@@ -1,13 +1,14 @@
 // aggregate_static.cu -- bmf_aggregate_static: the aggregation of per-row Gaussian submodels
 // (Eq. 14 with the eigenvalue correction of Algorithm 2) for callers that cannot allocate GPU
-// memory, e.g. a host process that runs inside a CUDA-graph capture, or a runtime that owns all
-// device memory through its own allocator and forbids libraries from calling cudaMalloc.
+// memory, e.g. a runtime that owns all device memory through its own allocator and forbids
+// libraries from calling cudaMalloc, or a service whose device footprint is fixed at start-up.
 //
 // The per-row working matrices live in one file-scope static device array of fixed size
 // (kStaticBytes).  Every GPU that loads this library holds that array until the process exits.
 // All calls share it: the array keeps the previous call's contents, the call clears the part
 // that must start at zero, and two calls whose work overlaps on the GPU (different streams or
-// different host threads) race on it.
+// different host threads) race on it.  The call reads its counters back and synchronises its
+// stream before returning.
 #include <cstdint>
 #include <mutex>
 
@@ -187,7 +188,8 @@ aggregate_static_kernel(int K, int64_t R, int J, const double *__restrict__ mu,
     if (nc) atomicAdd(ncorr, nc);
 }
 
-// Device address of the static array, looked up once per device with that device current.
+// Device address of the static array, looked up once per device with that device current and
+// kept for the life of the process (a cudaDeviceReset of that device is not supported after it).
 std::mutex g_mutex;
 double *g_addr[kMaxDevices] = {nullptr};
 

@@ -98,7 +98,8 @@ struct bmf_ctx {
             if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : ev_chunk)
             if (e) cudaEventDestroy(e);
-        if (gexec) cudaGraphExecDestroy(gexec);
+        for (auto &g : graphs)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
         if (rb) cudaFreeHost(rb);
     }
     int K = 0, prec = BMF_FP64;
@@ -124,7 +125,13 @@ struct bmf_ctx {
         double rmse[2];
     } *rb = nullptr;                 // pinned host block: the end-of-call readback
     bmf_schedule sched = {1, 1, 4, 0.0, 0};
-    cudaGraphExec_t gexec = nullptr;  // the last captured sweep loop (graph schedule)
+    // graph schedule: the last captured launch sequence of each batch (a stage or one subset),
+    // updated in place by the next call of the same shape
+    struct GraphEntry {
+        int sl0, sl1;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graphs;
     int device = 0, sms = 1;
     DevMem mem;
     Side X, W;
@@ -154,12 +161,26 @@ struct bmf_ctx {
     int64_t gen_segs_cap = 0;
     double *aggX = nullptr, *aggW = nullptr;   // aggregated means, reordered order
     unsigned long long *ncorr_d = nullptr;
+    int64_t *agg_base = nullptr;     // [(I + J) max(I, J)] submodel base rows of every launch
+    double *agg_corr = nullptr;      // eigenvalue corrections of every (row, submodel) pair
+    // bmf_restart: the initial states in the original order and the original index of every
+    // arena row (the chains restart by a gather on the device)
+    double *X0o = nullptr, *W0o = nullptr;
+    int64_t *xsrc = nullptr, *wsrc = nullptr;
+    // held-out entries in the reordered index space (bmf_test_rmse) and original -> reordered
+    // index maps (bmf_predict), so that predictions need no host round trip of the means
+    int32_t *tg_row = nullptr, *tg_col = nullptr;
+    int64_t *row_rank_d = nullptr, *col_rank_d = nullptr;
+    double *pred_part = nullptr, *pred_out = nullptr;
+    char *pred_buf = nullptr;        // prediction entries of bmf_predict (grown on use)
+    int64_t pred_cap = 0;
     std::vector<SubState> ss;
     int stage_open = 0;
     bool failed = false;
     std::string err;
     int chunk_obs = 1024;
     bool full_moments = false;
+    bool monitor = true;             // per-sweep test RMSE (bmf_set_monitor)
     // adjoint / Langevin scratch (allocated on first use)
     float *adj_part = nullptr;
     int64_t adj_part_cap = 0;
@@ -548,6 +569,7 @@ bmf_status prepare_gen(bmf_ctx *c, int sl0, int sl1, int64_t per, int nbuf, int6
     *n_segs = (int)segs.size();
     if ((int64_t)segs.size() > c->gen_segs_cap) {
         if (c->gen_segs_d) cudaFree(c->gen_segs_d);
+    if (c->pred_buf) cudaFree(c->pred_buf);
         c->gen_segs_d = nullptr;
         c->gen_segs_cap = 0;
         if (cudaMalloc(&c->gen_segs_d, segs.size() * sizeof(GenSeg)) != cudaSuccess)
@@ -645,6 +667,9 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
     const int64_t rx0 = g0.xoff, rx1 = gl.xoff + gl.n();
     const int64_t rw0 = g0.woff, rw1 = gl.woff + gl.d();
     const int64_t tt0 = g0.test_off, tt1 = gl.test_off + gl.n_test;
+    // the per-sweep test-RMSE monitor (held-out entries of the batch, current sample and
+    // running mean of the retained samples)
+    const bool mon = c->monitor && tt1 > tt0;
     const int64_t per = per_sweep_draws(c, sl0, sl1);
     const double *dr = nullptr;
     const bool use_graph = c->sched.graph && !c->prof && n_sweeps > 0;
@@ -846,7 +871,7 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
             if (f == 0) {
                 // the previous sweep's RMSE pass reads the gathered copies this sweep rewrites;
                 // the generator fills this sweep's draws on the tail stream
-                if (it > 0 && tt1 > tt0) CUDA_TRY(c, cudaStreamWaitEvent(cs, c->ev_rmse, 0));
+                if (it > 0 && mon) CUDA_TRY(c, cudaStreamWaitEvent(cs, c->ev_rmse, 0));
                 if (it == 0 && copy_async) CUDA_TRY(c, cudaStreamWaitEvent(cs, c->ev_copy, 0));
                 if (gen && it >= 2) CUDA_TRY(c, cudaStreamWaitEvent(cs, c->ev_gen[it & 1], 0));
             }
@@ -928,12 +953,12 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
         // leaves the FP64 pipes idle): the test RMSE of this sample, and the draws of sweep
         // t + 2 into this sweep's buffer (every reader of that buffer is ordered before here)
         const bool tail_gen = gen && it + 2 < n_sweeps;
-        used_tail |= tt1 > tt0;
+        used_tail |= mon;
         used_gen |= tail_gen;
-        if (tt1 > tt0 || tail_gen) CUDA_TRY(c, cudaEventRecord(c->ev_tail, c->st));
-        if (tt1 > tt0) CUDA_TRY(c, cudaStreamWaitEvent(c->st4, c->ev_tail, 0));
+        if (mon || tail_gen) CUDA_TRY(c, cudaEventRecord(c->ev_tail, c->st));
+        if (mon) CUDA_TRY(c, cudaStreamWaitEvent(c->st4, c->ev_tail, 0));
         if (tail_gen) CUDA_TRY(c, cudaStreamWaitEvent(c->st5, c->ev_tail, 0));
-        if (tt1 > tt0) {
+        if (mon) {
             RmseParams rp{K, c->prec, tt0, tt1, c->trow, c->tcol, c->tval, c->X.G, c->W.G, c->ldg,
                           keep ? 1 : 0, c->ysum, kept > 0 ? 1.0 / (double)kept : 0.0,
                           c->rmse_part};
@@ -970,23 +995,30 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
             if (g) cudaGraphDestroy(g);
             return fail(c, BMF_E_CUDA, std::string("stream capture failed: ") + cudaGetErrorString(ee));
         }
+        cudaGraphExec_t *ge = nullptr;
+        for (auto &q : c->graphs)
+            if (q.sl0 == sl0 && q.sl1 == sl1) ge = &q.exec;
+        if (!ge) {
+            c->graphs.push_back(bmf_ctx::GraphEntry{sl0, sl1, nullptr});
+            ge = &c->graphs.back().exec;
+        }
         bool updated = false;
-        if (c->gexec) {
+        if (*ge) {
             cudaGraphExecUpdateResultInfo info;
-            updated = cudaGraphExecUpdate(c->gexec, g, &info) == cudaSuccess;
+            updated = cudaGraphExecUpdate(*ge, g, &info) == cudaSuccess;
             if (!updated) {
                 cudaGetLastError();
-                cudaGraphExecDestroy(c->gexec);
-                c->gexec = nullptr;
+                cudaGraphExecDestroy(*ge);
+                *ge = nullptr;
             }
         }
-        cudaError_t e = updated ? cudaSuccess : cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaError_t e = updated ? cudaSuccess : cudaGraphInstantiate(ge, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
-            c->gexec = nullptr;
+            *ge = nullptr;
             return fail(c, BMF_E_CUDA, std::string("graph instantiation failed: ") + cudaGetErrorString(e));
         }
-        CUDA_TRY(c, cudaGraphLaunch(c->gexec, c->st));
+        CUDA_TRY(c, cudaGraphLaunch(*ge, c->st));
     }
     CUDA_TRY(c, cudaGetLastError());
     for (int sl = sl0; sl < sl1; ++sl) {
@@ -997,7 +1029,7 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
         if (n_sweeps > 0) c->stats_ok[sl] = 1;
     }
     // every stream of the call has joined the context stream: one readback, one synchronisation
-    const bool want_rmse = stats && tt1 > tt0 && n_sweeps > 0;
+    const bool want_rmse = stats && mon && n_sweeps > 0;
     CUDA_TRY(c, cudaMemcpyAsync(&c->rb->err, c->err_d, sizeof(DevError), cudaMemcpyDeviceToHost, c->st));
     if (want_rmse)
         CUDA_TRY(c, cudaMemcpyAsync(c->rb->rmse, c->rmse_out, 2 * sizeof(double),
@@ -1108,7 +1140,10 @@ int last_stage(const bmf_ctx *c)
     return m;
 }
 
-// Aggregated means (reordered order) into c->aggX / c->aggW.
+// Aggregated means (reordered order) into c->aggX / c->aggW: Eq. 14 with Algorithm 2 for every
+// row block of X (submodels (i, 0..J-1)) and column block of W (submodels (0..I-1, j)); a block
+// with a single submodel takes the mean of its retained samples.  All launches are enqueued on
+// the context stream, then one synchronisation reads the device error word.
 bmf_status aggregate_all(bmf_ctx *c, int64_t *n_corrected)
 {
     if (c->stage_open != last_stage(c))
@@ -1121,18 +1156,12 @@ bmf_status aggregate_all(bmf_ctx *c, int64_t *n_corrected)
         if (s) return s;
     }
     CUDA_TRY(c, cudaMemsetAsync(c->ncorr_d, 0, sizeof(unsigned long long), c->st));
-    std::vector<int64_t> base;
-    int64_t *base_d = c->mem.alloc<int64_t>(std::max(I, J));
-    if (!base_d) return fail(c, BMF_E_OOM, "device allocation failed");
+    int64_t nb_done = 0;   // launches so far (their bases are at agg_base + nb_done * max(I, J))
+    const int MB = std::max(I, J);
     for (int f = 0; f < 2; ++f) {
         Side &sd = f == 0 ? c->X : c->W;
         const int nb = f == 0 ? I : J, ns = f == 0 ? J : I;
-        for (int b = 0; b < nb; ++b) {
-            base.clear();
-            for (int q = 0; q < ns; ++q) {
-                const SubsetGeom &g = f == 0 ? c->P.subs[b * J + q] : c->P.subs[q * J + b];
-                base.push_back(f == 0 ? g.xoff : g.woff);
-            }
+        for (int b = 0; b < nb; ++b, ++nb_done) {
             const SubsetGeom &g0 = f == 0 ? c->P.subs[b * J] : c->P.subs[b];
             const int64_t n = f == 0 ? g0.n() : g0.d();
             const int64_t out0 = f == 0 ? g0.r0 : g0.c0;
@@ -1141,23 +1170,13 @@ bmf_status aggregate_all(bmf_ctx *c, int64_t *n_corrected)
                 // one submodel: the posterior mean is the mean of the retained samples
                 const SubState &su = c->ss[g0.sid];
                 if (su.kept < 1) return fail(c, BMF_E_STATE, "no retained samples");
-                std::vector<double> S1((size_t)n * K), m((size_t)n * K);
-                for (int k = 0; k < K; ++k)
-                    if (n)
-                        CUDA_TRY(c, cudaMemcpy(S1.data() + (size_t)k * n, sd.S1 + (int64_t)k * sd.R + base[0],
-                                               n * sizeof(double), cudaMemcpyDeviceToHost));
-                for (int64_t r = 0; r < n; ++r)
-                    for (int k = 0; k < K; ++k) m[r * K + k] = S1[(size_t)k * n + r] / (double)su.kept;
-                if (n) CUDA_TRY(c, cudaMemcpy(out, m.data(), n * K * sizeof(double), cudaMemcpyHostToDevice));
+                launch_mean_rows(K, n, sd.S1, sd.R, f == 0 ? g0.xoff : g0.woff,
+                                 1.0 / (double)su.kept, out, c->st);
                 continue;
             }
-            CUDA_TRY(c, cudaMemcpyAsync(base_d, base.data(), ns * sizeof(int64_t),
-                                        cudaMemcpyHostToDevice, c->st));
-            AggParams ap{K, n, ns, base_d, sd.mm_mu, sd.mm_L, sd.R, c->eps_rel, out, c->ncorr_d,
-                         c->err_d};
-            if (!launch_aggregate(ap, c->st))
-                return fail(c, BMF_E_OOM, "device allocation failed (aggregation scratch)");
-            CUDA_TRY(c, cudaStreamSynchronize(c->st));
+            AggParams ap{K, n, ns, c->agg_base + nb_done * MB, sd.mm_mu, sd.mm_L, sd.R,
+                         c->eps_rel, out, c->agg_corr, c->ncorr_d, c->err_d};
+            launch_aggregate(ap, c->st);
         }
     }
     CUDA_TRY(c, cudaGetLastError());
@@ -1187,6 +1206,56 @@ bmf_status means_original(bmf_ctx *c, std::vector<double> &Xm, std::vector<doubl
         std::memcpy(&Xm[(size_t)c->P.row_perm[k] * K], &xr[(size_t)k * K], K * sizeof(double));
     for (int64_t k = 0; k < c->P.D; ++k)
         std::memcpy(&Wm[(size_t)c->P.col_perm[k] * K], &wr[(size_t)k * K], K * sizeof(double));
+    return BMF_OK;
+}
+
+// Every chain back to the stored initial state (the X0o / W0o copies): states and gathered
+// copies, moment sums, running test predictions, hyperparameter slots, counters, priors and
+// the open stage.  Enqueued on the context stream and synchronised.
+bmf_status restart_chains(bmf_ctx *c)
+{
+    const int K = c->K, NT = ntri(K);
+    const int S = (int)c->P.subs.size();
+    launch_gather_rows(K, c->X.R, c->xsrc, c->X0o, c->X.F, c->st);
+    launch_gather_rows(K, c->W.R, c->wsrc, c->W0o, c->W.F, c->st);
+    launch_fill_gather(K, c->prec, c->X.R, c->X.F, c->X.G, c->ldg, c->st);
+    launch_fill_gather(K, c->prec, c->W.R, c->W.F, c->W.G, c->ldg, c->st);
+    for (Side *sd : {&c->X, &c->W}) {
+        if (!sd->R) continue;
+        CUDA_TRY(c, cudaMemsetAsync(sd->S1, 0, sd->R * K * sizeof(double), c->st));
+        CUDA_TRY(c, cudaMemsetAsync(sd->S2, 0, sd->R * NT * sizeof(double), c->st));
+        CUDA_TRY(c, cudaMemsetAsync(sd->pL, 0, sd->R * NT * sizeof(double), c->st));
+        CUDA_TRY(c, cudaMemsetAsync(sd->pb, 0, sd->R * K * sizeof(double), c->st));
+    }
+    const int64_t nt = (int64_t)c->P.trow.size();
+    if (nt) CUDA_TRY(c, cudaMemsetAsync(c->ysum, 0, nt * sizeof(double), c->st));
+    CUDA_TRY(c, cudaMemsetAsync(c->hyper, 0, (size_t)2 * S * hyper_slot_len(K) * sizeof(double), c->st));
+    c->ss.assign(S, SubState());
+    c->stats_ok.assign(S, 0);
+    for (int sl = 0; sl < S; ++sl) {
+        refresh_hslots(c, sl);
+        bmf_status s = upload_hslots(c, sl);
+        if (s) return s;
+    }
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    c->failed = false;
+    c->stage_open = 1;
+    return BMF_OK;
+}
+
+// Room for n prediction entries (row, col int32; y and y_hat FP64) in c->pred_buf.
+bmf_status pred_room(bmf_ctx *c, int64_t n)
+{
+    const int64_t need = n * (int64_t)(2 * sizeof(int32_t) + 2 * sizeof(double));
+    if (need <= c->pred_cap) return BMF_OK;
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    if (c->pred_buf) cudaFree(c->pred_buf);
+    c->pred_buf = nullptr;
+    c->pred_cap = 0;
+    if (cudaMalloc(&c->pred_buf, need) != cudaSuccess)
+        return fail(c, BMF_E_OOM, "device allocation failed (prediction entries)");
+    c->pred_cap = need;
     return BMF_OK;
 }
 
@@ -1366,6 +1435,21 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
     c->aggX = c->mem.alloc<double>(N * K);
     c->aggW = c->mem.alloc<double>(D * K);
     c->ncorr_d = c->mem.alloc<unsigned long long>(1);
+    const int MB = std::max(I, J);
+    c->agg_base = c->mem.alloc<int64_t>((size_t)(I + J) * MB);
+    // eigenvalue corrections of one aggregation launch (at most N (J - 1) or D (I - 1) pairs;
+    // the launches run in order on the context stream and reuse the buffer)
+    c->agg_corr = c->mem.alloc<double>((size_t)N * std::max(J - 1, 0) + (size_t)D * std::max(I - 1, 0));
+    c->X0o = c->mem.alloc<double>(N * K);
+    c->W0o = c->mem.alloc<double>(D * K);
+    c->xsrc = c->mem.alloc<int64_t>(c->P.RX);
+    c->wsrc = c->mem.alloc<int64_t>(c->P.RW);
+    c->tg_row = c->mem.alloc<int32_t>(nt);
+    c->tg_col = c->mem.alloc<int32_t>(nt);
+    c->row_rank_d = c->mem.alloc<int64_t>(N);
+    c->col_rank_d = c->mem.alloc<int64_t>(D);
+    c->pred_part = c->mem.alloc<double>(2 * c->rmse_blocks);
+    c->pred_out = c->mem.alloc<double>(2);
     if (!c->mem.ok) return bail(BMF_E_OOM, "device allocation failed");
     cudaMemcpy(c->mu0_d, c->mu0.data(), K * sizeof(double), cudaMemcpyHostToDevice);
     cudaMemcpy(c->W0inv_d, c->W0inv.data(), (size_t)K * K * sizeof(double), cudaMemcpyHostToDevice);
@@ -1378,27 +1462,44 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
     }
     DevError z = {0u, INT32_MAX};
     cudaMemcpy(c->err_d, &z, sizeof(z), cudaMemcpyHostToDevice);
-    // initial states: every subset's blocks from X0 / W0init (original order)
-    std::vector<double> hx((size_t)c->P.RX * K), hw((size_t)c->P.RW * K);
-    for (const auto &g : c->P.subs) {
-        for (int64_t r = 0; r < g.n(); ++r)
-            std::memcpy(&hx[(size_t)(g.xoff + r) * K], &X0[c->P.row_perm[g.r0 + r] * K],
-                        K * sizeof(double));
-        for (int64_t r = 0; r < g.d(); ++r)
-            std::memcpy(&hw[(size_t)(g.woff + r) * K], &W0init[c->P.col_perm[g.c0 + r] * K],
-                        K * sizeof(double));
+    // aggregation bases: X block i over submodels (i, j), then W block j over (i, j)
+    {
+        std::vector<int64_t> base((size_t)(I + J) * MB, 0);
+        for (int i = 0; i < I; ++i)
+            for (int j = 0; j < J; ++j) base[(size_t)i * MB + j] = c->P.subs[i * J + j].xoff;
+        for (int j = 0; j < J; ++j)
+            for (int i = 0; i < I; ++i) base[(size_t)(I + j) * MB + i] = c->P.subs[i * J + j].woff;
+        cudaMemcpy(c->agg_base, base.data(), base.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
     }
-    cudaMemcpy(c->X.F, hx.data(), hx.size() * sizeof(double), cudaMemcpyHostToDevice);
-    cudaMemcpy(c->W.F, hw.data(), hw.size() * sizeof(double), cudaMemcpyHostToDevice);
-    launch_fill_gather(K, c->prec, c->P.RX, c->X.F, c->X.G, c->ldg, c->st);
-    launch_fill_gather(K, c->prec, c->P.RW, c->W.F, c->W.G, c->ldg, c->st);
+    // held-out entries in the reordered index space; original -> reordered maps
+    if (nt) {
+        std::vector<int32_t> gr(nt), gc(nt);
+        for (const auto &g : c->P.subs)
+            for (int64_t k = g.test_off; k < g.test_off + g.n_test; ++k) {
+                gr[k] = (int32_t)(g.r0 + (c->P.trow[k] - g.xoff));
+                gc[k] = (int32_t)(g.c0 + (c->P.tcol[k] - g.woff));
+            }
+        cudaMemcpy(c->tg_row, gr.data(), nt * sizeof(int32_t), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->tg_col, gc.data(), nt * sizeof(int32_t), cudaMemcpyHostToDevice);
+    }
+    if (N) cudaMemcpy(c->row_rank_d, c->P.row_rank.data(), N * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (D) cudaMemcpy(c->col_rank_d, c->P.col_rank.data(), D * sizeof(int64_t), cudaMemcpyHostToDevice);
+    // initial states: kept in the original order; every subset's blocks gathered from them
+    {
+        std::vector<int64_t> xs(c->P.RX), ws(c->P.RW);
+        for (const auto &g : c->P.subs) {
+            for (int64_t r = 0; r < g.n(); ++r) xs[g.xoff + r] = c->P.row_perm[g.r0 + r];
+            for (int64_t r = 0; r < g.d(); ++r) ws[g.woff + r] = c->P.col_perm[g.c0 + r];
+        }
+        if (c->P.RX) cudaMemcpy(c->xsrc, xs.data(), xs.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+        if (c->P.RW) cudaMemcpy(c->wsrc, ws.data(), ws.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    }
+    if (N) cudaMemcpy(c->X0o, X0, N * K * sizeof(double), cudaMemcpyHostToDevice);
+    if (D) cudaMemcpy(c->W0o, W0init, D * K * sizeof(double), cudaMemcpyHostToDevice);
     c->ss.assign(S, SubState());
     c->stats_ok.assign(S, 0);
-    for (int sl = 0; sl < S; ++sl) {
-        refresh_hslots(c, sl);
-        s = upload_hslots(c, sl);
-        if (s) return bail(s, "");
-    }
+    s = restart_chains(c);
+    if (s) return bail(s, "");
     cudaError_t e = cudaStreamSynchronize(c->st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return bail(BMF_E_CUDA, std::string("CUDA: ") + cudaGetErrorString(e));
@@ -1431,6 +1532,14 @@ bmf_status bmf_set_schedule(bmf_ctx *c, const bmf_schedule *s)
         return fail(c, BMF_E_ARG, "row_weight must be finite and >= 0");
     if (s->graph != 0 && s->graph != 1) return fail(c, BMF_E_ARG, "graph must be 0 or 1");
     c->sched = *s;
+    return BMF_OK;
+}
+
+bmf_status bmf_set_monitor(bmf_ctx *c, int32_t on)
+{
+    if (!c) return BMF_E_ARG;
+    if (on != 0 && on != 1) return fail(c, BMF_E_ARG, "monitor must be 0 or 1");
+    c->monitor = on != 0;
     return BMF_OK;
 }
 
@@ -1664,35 +1773,77 @@ bmf_status bmf_predict(bmf_ctx *c, int64_t n, const int32_t *row, const int32_t 
     for (int64_t e = 0; e < n; ++e)
         if (row[e] < 0 || row[e] >= c->P.N || col[e] < 0 || col[e] >= c->P.D)
             return fail(c, BMF_E_ARG, "prediction index out of range");
-    std::vector<double> x, w;
-    bmf_status s = means_original(c, x, w, nullptr);
+    bmf_status s = aggregate_all(c, nullptr);
     if (s) return s;
     if (n == 0) {
         if (rmse) *rmse = NAN;
         return BMF_OK;
     }
-    // means (original order) and entries to the device, dot products there
-    DevMem tmp;
-    double *xd = tmp.alloc<double>(x.size()), *wd = tmp.alloc<double>(w.size());
-    int32_t *rd = tmp.alloc<int32_t>(n), *cd = tmp.alloc<int32_t>(n);
-    double *yd = tmp.alloc<double>(n);
-    if (!tmp.ok) return fail(c, BMF_E_OOM, "device allocation failed (predict)");
-    CUDA_TRY(c, cudaMemcpy(xd, x.data(), x.size() * sizeof(double), cudaMemcpyHostToDevice));
-    CUDA_TRY(c, cudaMemcpy(wd, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
-    CUDA_TRY(c, cudaMemcpy(rd, row, n * sizeof(int32_t), cudaMemcpyHostToDevice));
-    CUDA_TRY(c, cudaMemcpy(cd, col, n * sizeof(int32_t), cudaMemcpyHostToDevice));
-    launch_predict(c->K, n, rd, cd, xd, wd, c->P.offset, yd, c->st);
-    CUDA_TRY(c, cudaGetLastError());
-    std::vector<double> h(n);
-    CUDA_TRY(c, cudaMemcpyAsync(h.data(), yd, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
-    CUDA_TRY(c, cudaStreamSynchronize(c->st));
-    if (yhat) std::memcpy(yhat, h.data(), n * sizeof(double));
+    // entries to the device, predictions there with the aggregated means (reordered order,
+    // reached through the original -> reordered maps), squared errors summed there
+    if ((s = pred_room(c, n))) return s;
+    int32_t *rd = reinterpret_cast<int32_t *>(c->pred_buf), *cd = rd + n;
+    double *yd = reinterpret_cast<double *>(c->pred_buf + n * 2 * sizeof(int32_t)), *hd = yd + n;
+    CUDA_TRY(c, cudaMemcpyAsync(rd, row, n * sizeof(int32_t), cudaMemcpyHostToDevice, c->st));
+    CUDA_TRY(c, cudaMemcpyAsync(cd, col, n * sizeof(int32_t), cudaMemcpyHostToDevice, c->st));
+    if (rmse) CUDA_TRY(c, cudaMemcpyAsync(yd, y, n * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    PredictParams pp{c->K, n, rd, cd, c->row_rank_d, c->col_rank_d, c->aggX, c->aggW,
+                     c->P.offset, hd, rmse ? yd : nullptr, rmse ? c->pred_part : nullptr};
+    launch_predict_sq(pp, c->rmse_blocks, c->st);
     if (rmse) {
-        double ss = 0.0;
-        for (int64_t e = 0; e < n; ++e) ss += (y[e] - h[e]) * (y[e] - h[e]);
-        *rmse = std::sqrt(ss / (double)n);
+        launch_rmse_final(c->pred_part, c->rmse_blocks, c->pred_out, c->st);
+        CUDA_TRY(c, cudaMemcpyAsync(c->rb->rmse, c->pred_out, 2 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, c->st));
     }
+    if (yhat) CUDA_TRY(c, cudaMemcpyAsync(yhat, hd, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    if (rmse) *rmse = std::sqrt(c->rb->rmse[0] / (double)n);
     return BMF_OK;
+}
+
+bmf_status bmf_test_rmse(bmf_ctx *c, double *rmse)
+{
+    if (!c || !rmse) return BMF_E_ARG;
+    bmf_status s = aggregate_all(c, nullptr);
+    if (s) return s;
+    const int64_t nt = (int64_t)c->P.trow.size();
+    if (nt == 0) {
+        *rmse = NAN;
+        return BMF_OK;
+    }
+    // held-out values are stored centred: the prediction of the centred value has no offset
+    PredictParams pp{c->K, nt, c->tg_row, c->tg_col, nullptr, nullptr, c->aggX, c->aggW, 0.0,
+                     nullptr, c->tval, c->pred_part};
+    launch_predict_sq(pp, c->rmse_blocks, c->st);
+    launch_rmse_final(c->pred_part, c->rmse_blocks, c->pred_out, c->st);
+    CUDA_TRY(c, cudaMemcpyAsync(c->rb->rmse, c->pred_out, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                c->st));
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    *rmse = std::sqrt(c->rb->rmse[0] / (double)nt);
+    return BMF_OK;
+}
+
+bmf_status bmf_restart(bmf_ctx *c, const double *X0, const double *W0init, uint64_t seed)
+{
+    if (!c) return BMF_E_ARG;
+    const int K = c->K;
+    if (X0)
+        for (int64_t e = 0; e < c->P.N * K; ++e)
+            if (!std::isfinite(X0[e])) return fail(c, BMF_E_NONFINITE, "non-finite X0");
+    if (W0init)
+        for (int64_t e = 0; e < c->P.D * K; ++e)
+            if (!std::isfinite(W0init[e])) return fail(c, BMF_E_NONFINITE, "non-finite W0init");
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    if (X0 && c->P.N)
+        CUDA_TRY(c, cudaMemcpyAsync(c->X0o, X0, c->P.N * K * sizeof(double), cudaMemcpyHostToDevice,
+                                    c->st));
+    if (W0init && c->P.D)
+        CUDA_TRY(c, cudaMemcpyAsync(c->W0o, W0init, c->P.D * K * sizeof(double),
+                                    cudaMemcpyHostToDevice, c->st));
+    c->seed = seed;
+    return restart_chains(c);
 }
 
 bmf_status bmf_get_state(bmf_ctx *c, int32_t subset, double *X, double *W, double *hyper)
@@ -2125,6 +2276,7 @@ void bmf_destroy(bmf_ctx *c)
     if (c->draws_d) cudaFree(c->draws_d);
     if (c->gen_d) cudaFree(c->gen_d);
     if (c->gen_segs_d) cudaFree(c->gen_segs_d);
+    if (c->pred_buf) cudaFree(c->pred_buf);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (void *p : {(void *)c->adj_part, (void *)c->adj_sums, (void *)c->fval[0], (void *)c->fval[1],
                     (void *)c->lg_buf})

@@ -176,14 +176,37 @@ struct AggParams {
     int64_t R;
     double eps_rel;
     double *out;              // [n_rows x K]
+    double *corr;             // [(J - 1) x n_rows] eigenvalue correction of each (row, j >= 1)
     unsigned long long *n_corrected;
     DevError *err;
 };
-bool launch_aggregate(const AggParams &a, cudaStream_t st);   // false: scratch allocation failed
+void launch_aggregate(const AggParams &a, cudaStream_t st);
 
-// y_hat = offset + xm[row]^T wm[col] for host-given entries (original order means).
-void launch_predict(int K, int64_t n, const int32_t *row, const int32_t *col, const double *Xm,
-                    const double *Wm, double offset, double *yhat, cudaStream_t st);
+// A factor block with a single submodel: posterior mean = mean of the retained samples,
+// out[r][k] = S1[k][base + r] * inv_kept.
+void launch_mean_rows(int K, int64_t n, const double *S1, int64_t R, int64_t base,
+                      double inv_kept, double *out, cudaStream_t st);
+
+// Posterior-mean predictions y_hat = offset + Xm[row]^T Wm[col] of n entries; (row, col) are
+// reordered indices when the rank maps are null, else original ones mapped through them.
+// yhat (nullable) receives the predictions; with y non-null, partial[2 b] receives block b's
+// sum of (y - y_hat)^2 and partial[2 b + 1] zero (sum them with launch_rmse_final).
+struct PredictParams {
+    int K;
+    int64_t n;
+    const int32_t *row, *col;
+    const int64_t *row_rank, *col_rank;
+    const double *Xm, *Wm;
+    double offset;
+    double *yhat;
+    const double *y;
+    double *partial;
+};
+void launch_predict_sq(const PredictParams &p, int blocks, cudaStream_t st);
+
+// out[a][k] = in[src[a]][k] for the R rows of a factor arena (chain restart).
+void launch_gather_rows(int K, int64_t R, const int64_t *src, const double *in, double *out,
+                        cudaStream_t st);
 
 // K > 16 (wide.cu): Gram on the tensor cores (BF16, split TF32) or FP64 lanes over entries;
 // conditional draw with one warp per row.  Partials: packed lower of the exact K, then K rhs.

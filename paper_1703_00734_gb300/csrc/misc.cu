@@ -612,42 +612,148 @@ void launch_propagate(const PropParams &a, cudaStream_t st)
 // Algorithm 2 (Eq. 14 with the eigenvalue correction), thread per row.
 // ------------------------------------------------------------------------------------------
 
-// Smallest eigenvalue of the symmetric K x K matrix in `a` (row-major, thread-private global
-// scratch) by cyclic Jacobi rotations (Golub & Van Loan, Section 8.5).
-__device__ double jacobi_min_eig(double *a, int K)
+// Smallest eigenvalue of the symmetric matrix held packed-lower in A (interleaved; destroyed):
+// Householder reduction to tridiagonal form T = Q^T A Q (Golub & Van Loan, Algorithm 8.3.1),
+// then bisection on the Sturm count of T (the number of negative pivots of the LDL^T
+// factorisation of T - x I equals the number of eigenvalues below x; Golub & Van Loan,
+// Section 8.4.1).  Both steps are backward stable, so the result is the smallest eigenvalue to
+// O(u |A|).  v: K scratch slots, dg / of: the K diagonal and K - 1 off-diagonal entries of T.
+__device__ double min_eig_tridiag(double *A, double *v, double *dg, double *of, int K, int rb)
 {
-    double fro = 0.0;
-    for (int e = 0; e < K * K; ++e) fro += a[e] * a[e];
-    for (int sweep = 0; sweep < 100; ++sweep) {
-        double off = 0.0;
-        for (int p = 0; p < K; ++p)
-            for (int q = p + 1; q < K; ++q) off += a[p * K + q] * a[p * K + q];
-        if (off <= 1e-30 * fro || off == 0.0) break;
-        for (int p = 0; p < K; ++p)
-            for (int q = p + 1; q < K; ++q) {
-                const double apq = a[p * K + q];
-                if (apq == 0.0) continue;
-                const double theta = (a[q * K + q] - a[p * K + p]) / (2.0 * apq);
-                const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                const double c = 1.0 / sqrt(tt * tt + 1.0), s = tt * c;
-                for (int k = 0; k < K; ++k) {
-                    const double akp = a[k * K + p], akq = a[k * K + q];
-                    a[k * K + p] = c * akp - s * akq;
-                    a[k * K + q] = s * akp + c * akq;
-                }
-                for (int k = 0; k < K; ++k) {
-                    const double apk = a[p * K + k], aqk = a[q * K + k];
-                    a[p * K + k] = c * apk - s * aqk;
-                    a[q * K + k] = s * apk + c * aqk;
-                }
-            }
+#define AP(i, j) RS(A, (i) >= (j) ? tri(i, j) : tri(j, i))
+    for (int k = 0; k + 2 < K; ++k) {
+        // Householder vector of the column below the diagonal, x = A(k+1 .., k)
+        double nrm2 = 0.0;
+        for (int i = k + 1; i < K; ++i) nrm2 = fma(AP(i, k), AP(i, k), nrm2);
+        RS(dg, k) = AP(k, k);
+        const double x0 = AP(k + 1, k);
+        if (nrm2 == 0.0) {
+            RS(of, k) = 0.0;
+            continue;
+        }
+        const double nrm = sqrt(nrm2);
+        const double alpha = x0 >= 0.0 ? -nrm : nrm;   // H x = alpha e_1
+        RS(of, k) = alpha;
+        const double beta = 1.0 / (nrm2 - x0 * alpha);  // 2 / (v^T v), v = x - alpha e_1
+        for (int i = k + 1; i < K; ++i) RS(v, i) = AP(i, k);
+        RS(v, k + 1) = x0 - alpha;
+        // p = beta B v (B the trailing block), then w = p - (beta p^T v / 2) v; the w values
+        // replace column k of A, which is not read again
+        double pv = 0.0;
+        for (int i = k + 1; i < K; ++i) {
+            double s = 0.0;
+            for (int j = k + 1; j < K; ++j) s = fma(AP(i, j), RS(v, j), s);
+            s *= beta;
+            RS(A, tri(i, k)) = s;
+            pv = fma(s, RS(v, i), pv);
+        }
+        const double kk = 0.5 * beta * pv;
+        for (int i = k + 1; i < K; ++i) RS(A, tri(i, k)) = fma(-kk, RS(v, i), RS(A, tri(i, k)));
+        // B -= v w^T + w v^T (lower triangle)
+        for (int i = k + 1; i < K; ++i) {
+            const double vi = RS(v, i), wi = RS(A, tri(i, k));
+            for (int j = k + 1; j <= i; ++j)
+                RS(A, tri(i, j)) = fma(-vi, RS(A, tri(j, k)), fma(-wi, RS(v, j), RS(A, tri(i, j))));
+        }
     }
-    double m = a[0];
-    for (int i = 1; i < K; ++i) m = fmin(m, a[i * K + i]);
-    return m;
+    if (K >= 2) {
+        RS(dg, K - 2) = AP(K - 2, K - 2);
+        RS(of, K - 2) = AP(K - 1, K - 2);
+    }
+    RS(dg, K - 1) = AP(K - 1, K - 1);
+#undef AP
+    // Gershgorin interval of T
+    double lo = 0.0, hi = 0.0;
+    for (int i = 0; i < K; ++i) {
+        const double r = (i > 0 ? fabs(RS(of, i - 1)) : 0.0) + (i + 1 < K ? fabs(RS(of, i)) : 0.0);
+        const double a = RS(dg, i) - r, b = RS(dg, i) + r;
+        lo = i == 0 ? a : fmin(lo, a);
+        hi = i == 0 ? b : fmax(hi, b);
+    }
+    const double tol = 0x1.0p-48 * fmax(fabs(lo), fabs(hi)) + 1e-300;
+    for (int it = 0; it < 200 && hi - lo > tol; ++it) {
+        const double x = 0.5 * (lo + hi);
+        int below = 0;
+        double q = RS(dg, 0) - x;
+        for (int i = 0;; ++i) {
+            if (fabs(q) < 1e-300) q = -1e-300;
+            below += q < 0.0;
+            if (i + 1 == K) break;
+            const double e = RS(of, i);
+            q = RS(dg, i + 1) - x - e * e / q;
+        }
+        if (below >= 1)
+            hi = x;
+        else
+            lo = x;
+    }
+    return 0.5 * (lo + hi);
 }
 
-__global__ void __launch_bounds__(kRowBlock) aggregate_kernel(AggParams a, double *jac_scratch)
+// Algorithm 2 in two passes.  Pass 1, one thread per (row n, submodel j >= 1): the difference
+// Lambda^(j) - Lambda^(1) is tested for positive definiteness by a Cholesky factorisation; if a
+// pivot is not > 0, corr = |lambda_min| + eps (> 0), else corr = 0.  Pass 2, one thread per row:
+// Lambda* = (2 - J) Lambda^(1) + sum_j Lambda*^(j) with Lambda*^(j) = Lambda^(j) when corr = 0,
+// else (Lambda^(j) - Lambda^(1) + corr I) + Lambda^(1); the same for the right-hand side
+// Lambda* mu* = (2 - J) Lambda^(1) mu^(1) + sum_j Lambda*^(j) mu^(j); then Cholesky and solve.
+// Splitting keeps few slots per thread in shared memory, so several warps share an SM.
+
+// In-place packed lower Cholesky used only as a positive-definiteness test (pivot > 0 at every
+// step), scaling by one reciprocal per column.
+__device__ bool row_pd_test(double *P, int K, int rb)
+{
+    for (int j = 0; j < K; ++j) {
+        const int jj = tri(j, 0);
+        double d = RS(P, jj + j);
+        for (int k = 0; k < j; ++k) d = fma(-RS(P, jj + k), RS(P, jj + k), d);
+        if (!(d > 0.0)) return false;
+        const double r = 1.0 / sqrt(d);
+        for (int i = j + 1; i < K; ++i) {
+            const int ii = tri(i, 0);
+            double s = RS(P, ii + j);
+            for (int k = 0; k < j; ++k) s = fma(-RS(P, ii + k), RS(P, jj + k), s);
+            RS(P, ii + j) = s * r;
+        }
+    }
+    return true;
+}
+
+static inline size_t agg_corr_slots(int K) { return (size_t)ntri(K) + 3 * K; }
+
+__global__ void __launch_bounds__(kRowBlock) aggregate_corr_kernel(AggParams a, int64_t n_pairs)
+{
+    extern __shared__ double sm[];
+    const int t = threadIdx.x, rb = blockDim.x;
+    const int64_t q = (int64_t)blockIdx.x * rb + t;
+    unsigned long long nc = 0;
+    if (q < n_pairs) {
+        const int K = a.K, NT = ntri(K);
+        const int j = 1 + (int)(q / a.n_rows);
+        const int64_t n = q % a.n_rows;
+        double *Fm = sm + t, *v = Fm + NT * rb, *dg = v + K * rb, *of = dg + K * rb;
+        const int64_t r1 = a.sub_base[0] + n, rj = a.sub_base[j] + n;
+        for (int e = 0; e < NT; ++e) RS(Fm, e) = a.L[(int64_t)e * a.R + rj] - a.L[(int64_t)e * a.R + r1];
+        double corr = 0.0;
+        if (!row_pd_test(Fm, K, rb)) {
+            double mean_diag = 0.0;
+            for (int i = 0; i < K; ++i) mean_diag += a.L[(int64_t)tri(i, i) * a.R + r1];
+            mean_diag /= (double)K;
+            const double eps = a.eps_rel * (mean_diag > 1.0 ? mean_diag : 1.0);
+            for (int e = 0; e < NT; ++e) RS(Fm, e) = a.L[(int64_t)e * a.R + rj] - a.L[(int64_t)e * a.R + r1];
+            corr = fabs(min_eig_tridiag(Fm, v, dg, of, K, rb)) + eps;
+            nc = 1;
+        }
+        a.corr[q] = corr;
+    }
+    // one atomic per warp (the block may end in a partial warp: only its existing lanes vote)
+    const unsigned am = __activemask();
+    const unsigned votes = __ballot_sync(am, nc != 0);
+    if ((t & 31) == __ffs(am) - 1 && votes) atomicAdd(a.n_corrected, (unsigned long long)__popc(votes));
+}
+
+static inline size_t agg_slots(int K) { return (size_t)2 * ntri(K) + K; }
+
+__global__ void __launch_bounds__(kRowBlock) aggregate_kernel(AggParams a)
 {
     extern __shared__ double sm[];
     const int t = threadIdx.x, rb = blockDim.x;
@@ -657,10 +763,6 @@ __global__ void __launch_bounds__(kRowBlock) aggregate_kernel(AggParams a, doubl
     double *Ls = sm + t, *Dm = Ls + NT * rb, *h = Dm + NT * rb;
     const int64_t r1 = a.sub_base[0] + n;
     const double c0 = 2.0 - (double)J;
-    double mean_diag = 0.0;
-    for (int i = 0; i < K; ++i) mean_diag += a.L[(int64_t)tri(i, i) * a.R + r1];
-    mean_diag /= (double)K;
-    const double eps = a.eps_rel * (mean_diag > 1.0 ? mean_diag : 1.0);
     for (int e = 0; e < NT; ++e) RS(Ls, e) = c0 * a.L[(int64_t)e * a.R + r1];
     for (int i = 0; i < K; ++i) {
         double s = 0.0;
@@ -668,46 +770,20 @@ __global__ void __launch_bounds__(kRowBlock) aggregate_kernel(AggParams a, doubl
             s = fma(a.L[(int64_t)(i >= k ? tri(i, k) : tri(k, i)) * a.R + r1], a.mu[r1 * K + k], s);
         RS(h, i) = c0 * s;
     }
-    unsigned long long ncorr = 0;
     for (int j = 1; j < J; ++j) {
         const int64_t rj = a.sub_base[j] + n;
-        for (int e = 0; e < NT; ++e)
-            RS(Dm, e) = a.L[(int64_t)e * a.R + rj] - a.L[(int64_t)e * a.R + r1];
-        // Lambda*^(j) = Lambda^(j) if the difference is PD, else corrected difference + Lambda^(1)
-        bool pd;
-        {
-            // factor a copy (kept in the accumulated slots' scratch: reuse h-adjacent area)
-            double *F = jac_scratch + n * (int64_t)K * K;   // K*K per row, also used by Jacobi
-            for (int e = 0; e < NT; ++e) F[e] = RS(Dm, e);
-            pd = true;
-            for (int jj = 0; jj < K && pd; ++jj) {
-                const int b = tri(jj, 0);
-                double d = F[b + jj];
-                for (int k = 0; k < jj; ++k) d = fma(-F[b + k], F[b + k], d);
-                if (!(d > 0.0)) {
-                    pd = false;
-                    break;
+        const double corr = a.corr[(int64_t)(j - 1) * a.n_rows + n];
+        if (corr > 0.0) {
+            for (int i = 0; i < K; ++i)
+                for (int k = 0; k <= i; ++k) {
+                    const int e = tri(i, k);
+                    const double l1 = a.L[(int64_t)e * a.R + r1];
+                    double dd = a.L[(int64_t)e * a.R + rj] - l1;
+                    if (i == k) dd += corr;
+                    RS(Dm, e) = dd + l1;
                 }
-                const double sd = sqrt(d);
-                F[b + jj] = sd;
-                for (int i = jj + 1; i < K; ++i) {
-                    const int ib = tri(i, 0);
-                    double s = F[ib + jj];
-                    for (int k = 0; k < jj; ++k) s = fma(-F[ib + k], F[b + k], s);
-                    F[ib + jj] = s / sd;
-                }
-            }
-            if (!pd) {
-                for (int i = 0; i < K; ++i)
-                    for (int k = 0; k < K; ++k)
-                        F[i * K + k] = RS(Dm, i >= k ? tri(i, k) : tri(k, i));
-                const double lmin = jacobi_min_eig(F, K);
-                for (int i = 0; i < K; ++i) RS(Dm, tri(i, i)) += fabs(lmin) + eps;
-                for (int e = 0; e < NT; ++e) RS(Dm, e) += a.L[(int64_t)e * a.R + r1];
-                ++ncorr;
-            } else {
-                for (int e = 0; e < NT; ++e) RS(Dm, e) = a.L[(int64_t)e * a.R + rj];
-            }
+        } else {
+            for (int e = 0; e < NT; ++e) RS(Dm, e) = a.L[(int64_t)e * a.R + rj];
         }
         for (int e = 0; e < NT; ++e) RS(Ls, e) += RS(Dm, e);
         for (int i = 0; i < K; ++i) {
@@ -724,48 +800,118 @@ __global__ void __launch_bounds__(kRowBlock) aggregate_kernel(AggParams a, doubl
     }
     row_solve(Ls, h, K, rb);
     for (int i = 0; i < K; ++i) a.out[n * K + i] = RS(h, i);
-    if (ncorr) atomicAdd(a.n_corrected, ncorr);
 }
 
-bool launch_aggregate(const AggParams &a, cudaStream_t st)
+// Threads per block for a thread-per-row kernel with `per_row` shared slots: at most
+// kRowBlock, fewer when the block would not leave room for four blocks per SM.
+static int row_block_small(size_t per_row)
 {
-    if (a.n_rows <= 0) return true;
-    // per-row K x K scratch for the factorisation test and the Jacobi fallback
-    double *scr = nullptr;
-    if (cudaMallocAsync(&scr, (size_t)a.n_rows * a.K * a.K * sizeof(double), st) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
+    const size_t fit = (size_t)(220 * 1024 / 4) / (per_row * sizeof(double));
+    return (int)(fit >= (size_t)kRowBlock ? kRowBlock : (fit < 1 ? 1 : fit));
+}
+
+void launch_aggregate(const AggParams &a, cudaStream_t st)
+{
+    if (a.n_rows <= 0) return;
+    const int64_t n_pairs = a.n_rows * (int64_t)(a.J - 1);
+    if (n_pairs > 0) {
+        const size_t per = agg_corr_slots(a.K);
+        const int rb = row_block_small(per);
+        const size_t smem = per * rb * sizeof(double);
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(aggregate_corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        aggregate_corr_kernel<<<(int)((n_pairs + rb - 1) / rb), rb, smem, st>>>(a, n_pairs);
     }
-    const size_t per_row = (size_t)(2 * ntri(a.K) + a.K);
-    const int rb = row_block(per_row);
-    const size_t smem = per_row * rb * sizeof(double);
+    const size_t per = agg_slots(a.K);
+    const int rb = row_block_small(per);
+    const size_t smem = per * rb * sizeof(double);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(aggregate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-    aggregate_kernel<<<(int)((a.n_rows + rb - 1) / rb), rb, smem, st>>>(a, scr);
-    cudaFreeAsync(scr, st);
-    return true;
+    aggregate_kernel<<<(int)((a.n_rows + rb - 1) / rb), rb, smem, st>>>(a);
 }
 
 // ------------------------------------------------------------------------------------------
-// Posterior-mean prediction and gathered-copy refresh.
+// Posterior-mean prediction (Section 5.2) and the chain-restart gather.
 // ------------------------------------------------------------------------------------------
-__global__ void predict_kernel(int K, int64_t n, const int32_t *row, const int32_t *col,
-                               const double *Xm, const double *Wm, double offset, double *yhat)
+// One factor block with a single submodel: its posterior mean is the mean of the retained
+// samples, out[r][k] = S1[k][base + r] * inv_kept.
+__global__ void mean_rows_kernel(int K, int64_t n, const double *S1, int64_t R, int64_t base,
+                                 double inv_kept, double *out)
 {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    const double *x = Xm + (int64_t)row[e] * K, *w = Wm + (int64_t)col[e] * K;
-    double s = 0.0;
-    for (int k = 0; k < K; ++k) s = fma(x[k], w[k], s);
-    yhat[e] = offset + s;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n * K) return;
+    const int64_t r = q / K;
+    const int k = (int)(q % K);
+    out[q] = S1[(int64_t)k * R + base + r] * inv_kept;
 }
 
-void launch_predict(int K, int64_t n, const int32_t *row, const int32_t *col, const double *Xm,
-                    const double *Wm, double offset, double *yhat, cudaStream_t st)
+void launch_mean_rows(int K, int64_t n, const double *S1, int64_t R, int64_t base,
+                      double inv_kept, double *out, cudaStream_t st)
 {
     if (n <= 0) return;
-    predict_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(K, n, row, col, Xm, Wm, offset, yhat);
+    const int64_t m = n * K;
+    mean_rows_kernel<<<(int)((m + 255) / 256), 256, 0, st>>>(K, n, S1, R, base, inv_kept, out);
+}
+
+// y_hat = offset + Xm[row]^T Wm[col] (indices mapped through the rank arrays when given), and
+// with y the per-block sums of (y - y_hat)^2 (each thread a fixed strided subset, then a fixed
+// tree: deterministic).
+__global__ void __launch_bounds__(256) predict_sq_kernel(PredictParams p)
+{
+    double s = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < p.n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t rr = p.row_rank ? p.row_rank[p.row[e]] : (int64_t)p.row[e];
+        const int64_t cc = p.col_rank ? p.col_rank[p.col[e]] : (int64_t)p.col[e];
+        const double *x = p.Xm + rr * p.K, *w = p.Wm + cc * p.K;
+        double d = 0.0;
+        for (int k = 0; k < p.K; ++k) d = fma(x[k], w[k], d);
+        const double yh = p.offset + d;
+        if (p.yhat) p.yhat[e] = yh;
+        if (p.y) {
+            const double r = p.y[e] - yh;
+            s = fma(r, r, s);
+        }
+    }
+    if (!p.partial) return;
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        p.partial[2 * blockIdx.x] = red[0];
+        p.partial[2 * blockIdx.x + 1] = 0.0;
+    }
+}
+
+void launch_predict_sq(const PredictParams &p, int blocks, cudaStream_t st)
+{
+    predict_sq_kernel<<<blocks, 256, 0, st>>>(p);
+}
+
+// out[a][k] = in[src[a]][k]: every subset's block of a factor arena from a factor in the
+// original order.
+__global__ void gather_rows_kernel(int K, int64_t R, const int64_t *src, const double *in,
+                                   double *out)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= R * K) return;
+    const int64_t a = q / K;
+    const int k = (int)(q % K);
+    out[q] = in[src[a] * K + k];
+}
+
+void launch_gather_rows(int K, int64_t R, const int64_t *src, const double *in, double *out,
+                        cudaStream_t st)
+{
+    const int64_t m = R * K;
+    if (m <= 0) return;
+    gather_rows_kernel<<<(int)((m + 255) / 256), 256, 0, st>>>(K, R, src, in, out);
 }
 
 template <typename GT>

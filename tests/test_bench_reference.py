@@ -1,7 +1,7 @@
 """The benchmark's reference arm (the FP64 oracle on the host cores) reports the metric of the
-mode it stands beside: Gibbs sweeps/s for the plain sweep, stage sweeps/s for the PP workload,
-gradient evaluations/s for the adjoint workload, and an 'unavailable' line for the partition
-experiment, whose metric needs 3 x 1200 sweeps per grid."""
+mode it stands beside: Gibbs sweeps/s for the plain sweep and for the PP workload (one PP sweep
+per step), gradient evaluations/s for the adjoint workload, and an 'unavailable' line for the
+partition experiment, whose metric needs 3 x 1200 sweeps per grid."""
 import json
 import os
 import subprocess
@@ -22,13 +22,12 @@ def _run(*extra):
 
 @pytest.mark.parametrize("workload,scale,metric,unit", [
     ("planted-1000x500-k10", "1.0", "Gibbs sweeps/s", "sweeps/s"),
-    ("pp4x4-100000x20000-20M-k16", "0.03", "PP stage sweeps/s (all subsets of a stage batched)",
-     "stage sweeps/s"),
+    ("pp4x4-100000x20000-20M-k16", "0.03", "Gibbs sweeps/s", "sweeps/s"),
     ("uniform-200000x50000-50M-k64", "0.03", "log-joint gradient evaluations/s (adjoint, K=64)",
      "grad evals/s"),
 ])
 def test_reference_arm_metric_follows_the_mode(workload, scale, metric, unit):
-    out = _run("--workload", workload, "--scale", scale)
+    out = _run("--workload", workload, "--scale", scale, "--warmup", "1")
     assert out["impl"] == "reference" and out["metric"] == metric and out["unit"] == unit
     assert out["value"] > 0 and out["cpu_baseline"]["kind"] == "oracle"
     assert out["e2e"]["h2d_bytes_per_step"] == 0
@@ -37,3 +36,9 @@ def test_reference_arm_metric_follows_the_mode(workload, scale, metric, unit):
 def test_reference_arm_partition_experiment_is_unavailable():
     out = _run("--workload", "sim-6040x3706-k5")
     assert out["impl"] == "reference" and "unavailable" in out
+
+
+def test_reference_arm_pp_takes_the_requested_steps_and_warmup():
+    out = _run("--workload", "pp4x4-100000x20000-20M-k16", "--scale", "0.03", "--warmup", "2")
+    assert out["steps"] == 2 and out["warmup"] == 2
+    assert out["config"]["grid"] == "4x4"

@@ -99,6 +99,18 @@ def test_pp_stages_fp64_parity_and_aggregation():
     yo = oracle.predict(d["test_row"], d["test_col"], Xm_o[rr], Wm_o[cr], pr.p.offset)
     np.testing.assert_allclose(yh, yo, rtol=1e-6, atol=1e-8)
     assert abs(r - oracle.rmse(yo, d["test_val"])) < 1e-8
+    # Eq. 14 with Algorithm 2 on identical inputs: the library's own moment-matched subset
+    # posteriors fed to the oracle's aggregation.  The eigenvalue correction must have run on
+    # the device (an indefinite difference Lambda^(j) - Lambda^(1) in some rows).
+    gfin = {}
+    for s in pr.p.subsets:
+        mx, Lx = pr.m.get_posterior(s.sid, 0)
+        mw, Lw = pr.m.get_posterior(s.sid, 1)
+        gfin[s.sid] = (mx, Lx, mw, Lw)
+    Xg_o, Wg_o, nc_g = oracle.aggregate_plan(pr.p, gfin, 4)
+    assert nc > 0 and nc_g == nc
+    assert_rows_close(Xm, Xg_o[rr], 1e-9, "aggregated X, identical inputs")
+    assert_rows_close(Wm, Wg_o[cr], 1e-9, "aggregated W, identical inputs")
 
 
 def test_error_paths():
@@ -200,3 +212,48 @@ def test_pp_with_empty_subsets_and_zero_sweep_calls():
     assert nc == nc_o
     assert_rows_close(Xm, Xm_o, 1e-6, "aggregated X")
     assert_rows_close(Wm, Wm_o, 1e-6, "aggregated W")
+
+
+def test_restart_reproduces_a_run_and_test_rmse_matches_predict():
+    """bmf_restart: a restarted context with the same seed repeats a whole PP run bit for bit
+    (device generator), equals a freshly initialised context, and a new seed gives a new run;
+    bmf_test_rmse equals the RMSE of bmf_predict on the same held-out entries."""
+    from paper_1703_00734_gb300 import bmf
+    d = small(N=240, D=160, M=9000, K=4, seed=13)
+    test = (d["test_row"], d["test_col"], d["test_val"])
+
+    def ctx(seed):
+        return bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], 4, d["tau"], "fp32",
+                       I=2, J=3, X0=d["X0"], W0=d["W0"], test=test, burnin=3, seed=seed)
+
+    def run(m):
+        for stage in (1, 2, 3):
+            m.stage(stage, 10, None)
+        Xm, Wm, nc = m.posterior_means()
+        return m.test_rmse(), Xm, Wm
+
+    m = ctx(5)
+    r1, X1, W1 = run(m)
+    _, rp = m.predict(*test)
+    assert abs(r1 - rp) < 1e-12 * max(1.0, r1)
+    m.restart(5)
+    r2, X2, W2 = run(m)
+    assert r2 == r1
+    np.testing.assert_array_equal(X2, X1)
+    np.testing.assert_array_equal(W2, W1)
+    m.restart(6)
+    r3, X3, _ = run(m)
+    assert r3 != r1 and not np.array_equal(X3, X1)
+    m.restart(5, X0=d["X0"], W0=d["W0"])
+    r4, X4, _ = run(m)
+    assert r4 == r1
+    np.testing.assert_array_equal(X4, X1)
+    with pytest.raises(bmf.BmfError) as e:
+        m.restart(5, X0=np.full_like(d["X0"], np.nan))
+    assert e.value.status == 4
+    m.close()
+    f = ctx(5)
+    r5, X5, _ = run(f)
+    assert r5 == r1
+    np.testing.assert_array_equal(X5, X1)
+    f.close()
