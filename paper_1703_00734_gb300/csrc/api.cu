@@ -124,7 +124,7 @@ struct bmf_ctx {
         DevError err;
         double rmse[2];
     } *rb = nullptr;                 // pinned host block: the end-of-call readback
-    bmf_schedule sched = {1, 1, 4, 0.0, 0};
+    bmf_schedule sched = {1, 1, 4, 0.0, 0, 0};
     // graph schedule: the last captured launch sequence of each batch (a stage or one subset),
     // updated in place by the next call of the same shape
     struct GraphEntry {
@@ -920,7 +920,9 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
             cp.stats = c->stats;
             cp.err = c->err_d;
             // lanes per row of the conditional: one thread per row below K = 13, a team above
-            const int team = K >= kTeamMinK ? cond_team_size(K) : 1;
+            const int team = K >= kTeamMinK
+                                 ? (c->sched.cond_lanes > 0 ? c->sched.cond_lanes : cond_team_size(K))
+                                 : 1;
             auto cond_chunk = [&](int64_t ba, int64_t bb, cudaStream_t sx) {
                 if (bb <= ba) return;
                 CondParams q = cp;
@@ -1531,6 +1533,9 @@ bmf_status bmf_set_schedule(bmf_ctx *c, const bmf_schedule *s)
     if (!(s->row_weight >= 0.0) || !std::isfinite(s->row_weight))
         return fail(c, BMF_E_ARG, "row_weight must be finite and >= 0");
     if (s->graph != 0 && s->graph != 1) return fail(c, BMF_E_ARG, "graph must be 0 or 1");
+    if (s->cond_lanes != 0 && s->cond_lanes != 2 && s->cond_lanes != 4 && s->cond_lanes != 8 &&
+        s->cond_lanes != 16 && s->cond_lanes != 32)
+        return fail(c, BMF_E_ARG, "cond_lanes must be 0, 2, 4, 8, 16 or 32");
     c->sched = *s;
     return BMF_OK;
 }
@@ -1662,9 +1667,9 @@ bmf_status bmf_autotune(bmf_ctx *c, int32_t stage, int32_t subset, int32_t sweep
         }
         return BMF_OK;
     };
-    bmf_schedule b0{1, 1, 4, 0.0, 0};
+    bmf_schedule b0{1, 1, 4, 0.0, 0, 0};
     cands = {b0};
-    for (int g : {2, 8}) cands.push_back(bmf_schedule{1, 1, g, 0.0, 0});
+    for (int g : {2, 8}) cands.push_back(bmf_schedule{1, 1, g, 0.0, 0, 0});
     s = run_all(cands);
     for (int f = 0; f < 2 && !s; ++f) {
         cands.clear();
@@ -1683,6 +1688,17 @@ bmf_status bmf_autotune(bmf_ctx *c, int32_t stage, int32_t subset, int32_t sweep
             sc.row_weight = w0 * m;
             cands.push_back(sc);
         }
+        s = run_all(cands);
+    }
+    if (!s && K >= kTeamMinK) {
+        // lanes per row of the conditional (every choice gives bit-identical values)
+        cands.clear();
+        for (int lanes : {2, 4, 8})
+            if (lanes != cond_team_size(K)) {
+                bmf_schedule sc = best;
+                sc.cond_lanes = lanes;
+                cands.push_back(sc);
+            }
         s = run_all(cands);
     }
     if (!s) {

@@ -69,4 +69,32 @@ __device__ __forceinline__ double widen(float f)
 }
 __device__ __forceinline__ double widen(double d) { return d; }
 
+// 1 / sqrt(d) for a positive pivot of the FP64 Cholesky in the reduced-precision modes (FP32 or
+// BF16 Gram entries, relative error ~1e-7 already): a float copy of d from its top bits (integer
+// pipe), the FP32 hardware reciprocal square root (relative error below 2^-21 with the
+// truncation), widened on the integer pipe, then one Newton step in FP64,
+// y <- y + (y / 2)(1 - d y^2): relative error below 1e-12, with four FP64 operations instead of
+// the full-precision sequence.  Pivots outside the normal float range take rsqrt().
+__device__ __forceinline__ double rsqrt_refined(double d)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((u >> 52) & 0x7ffull) - 1023;
+    if (e < -125 || e > 126) return rsqrt(d);
+    const uint32_t fb = ((uint32_t)(e + 127) << 23) | (uint32_t)((u >> 29) & 0x7fffffull);
+    const double y = widen(rsqrtf(__uint_as_float(fb)));
+    const double r = fma(-(d * y), y, 1.0);
+    return fma(0.5 * y, r, y);
+}
+
+// Pivot reciprocal square root of the conditional draw: full FP64 in the FP64 mode (gathered
+// type double), refined FP32 otherwise.
+template <typename GT>
+__device__ __forceinline__ double pivot_rsqrt(double d)
+{
+    if constexpr (sizeof(GT) == 8)
+        return rsqrt(d);
+    else
+        return rsqrt_refined(d);
+}
+
 }  // namespace bmf

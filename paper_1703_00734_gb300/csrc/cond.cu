@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kCondBlock) cond_kernel(CondParams a)
                 break;
             }
             // only 1 / L_jj is used from here on (the solves scale by it)
-            const double rs = rsqrt(d);
+            const double rs = pivot_rsqrt<GT>(d);
             SM(RI + j) = rs;
             for (int i = j + 1; i < K; ++i) {
                 const int ii = tri(i, 0);
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(kCondBlock) cond_kernel_k(CondParams a)
 #pragma unroll
             for (int k = 0; k < j; ++k) d = fma(-M[tri(j, k)], M[tri(j, k)], d);
             if (!(d > 0.0)) ok = false;
-            const double rs = rsqrt(d);
+            const double rs = pivot_rsqrt<GT>(d);
             RI[j] = rs;
             M[tri(j, j)] = d * rs;
 #pragma unroll

@@ -481,15 +481,16 @@ __device__ __forceinline__ void decode_packed(int e, int &i, int &j)
 int cond_team_size(int K) { return K <= 16 ? 4 : (K <= 48 ? 16 : 32); }
 
 // Doubles per team in shared memory: the packed matrix, right-hand side, pivots and (teams of 8
-// or more lanes) a contiguous copy of the current column, padded so that the teams of one
-// half-warp start in different banks (stride = T mod 16 doubles past a multiple of 16: the
-// 16 / T teams of a half-warp cover the 32 banks once).  The column copy removes the strided
-// reads of the trailing update; for 4-lane teams (K <= 16) the extra shared memory would cost
-// a resident block per SM, which measured slower.
+// or more lanes) a contiguous copy of the current column, rounded up to a multiple of 8 doubles
+// and offset by T mod 16 doubles (4 for teams of 16 or 32 lanes), so that consecutive teams of
+// a warp start in different banks.  Rounding to 8 rather than 16 doubles lets five blocks of
+// 4-lane teams share an SM at K = 16 (44 KB each).  The column copy removes the strided reads of
+// the trailing update; for 4-lane teams (K <= 16) the extra shared memory would cost a resident
+// block per SM, which measured slower.
 __host__ __device__ constexpr bool team_colcopy(int T) { return T >= 8; }
 __host__ __device__ constexpr int team_stride(int K, int T)
 {
-    return (ntri(K) + (team_colcopy(T) ? 3 : 2) * K + 15) / 16 * 16 + T % 16;
+    return (ntri(K) + (team_colcopy(T) ? 3 : 2) * K + 7) / 8 * 8 + (T % 16 == 0 ? 4 : T % 16);
 }
 
 template <typename GT, typename AT, int T>
@@ -536,7 +537,7 @@ __global__ void __launch_bounds__(32 * kWideWarps) cond_team_kernel(CondParams a
             const int kk = tri(k, k);
             const double d = ok ? M[kk] : 1.0;
             if (!(d > 0.0)) ok = false;
-            const double rs = ok ? rsqrt(d) : 0.0;
+            const double rs = ok ? pivot_rsqrt<GT>(d) : 0.0;
             __syncwarp(mask);
             if (ok) {
                 // the scaled column also goes to CK[i], contiguous, for the trailing update
@@ -654,6 +655,7 @@ template <typename GT, typename AT>
 static void launch_cond_team_p(const CondParams &a, int n_blocks, int team, cudaStream_t st)
 {
     switch (team) {
+    case 2: launch_cond_team_t<GT, AT, 2>(a, n_blocks, st); break;
     case 4: launch_cond_team_t<GT, AT, 4>(a, n_blocks, st); break;
     case 8: launch_cond_team_t<GT, AT, 8>(a, n_blocks, st); break;
     case 16: launch_cond_team_t<GT, AT, 16>(a, n_blocks, st); break;

@@ -29,7 +29,7 @@ def _run(*extra):
 def test_reference_arm_metric_follows_the_mode(workload, scale, metric, unit):
     out = _run("--workload", workload, "--scale", scale, "--warmup", "1")
     assert out["impl"] == "reference" and out["metric"] == metric and out["unit"] == unit
-    assert out["value"] > 0 and out["cpu_baseline"]["kind"] == "oracle"
+    assert out["value"] > 0 and out["cpu_baseline"]["kind"].startswith("oracle")
     assert out["e2e"]["h2d_bytes_per_step"] == 0
 
 
