@@ -212,9 +212,10 @@ typedef struct {
                           once (kept and updated in place across calls of the same shape); 0: launch
                           directly.  Ignored while profiling is on. */
     int32_t cond_lanes; /* K >= 13: lanes that factor one row in the FP64 conditional draw (2, 4,
-                          8, 16 or 32; every choice gives bit-identical values); 0: a default
-                          from K (4 up to K = 16, 16 up to 48, 32 above).  Ignored for K <= 12
-                          (one thread per row). */
+                          8, 16 or 32; every choice gives bit-identical values; 2 at K <= 16
+                          keeps the row's matrix in registers); 0: a default from K (2 up to
+                          K = 16, 16 up to 48, 32 above).  Ignored for K <= 12 (one thread per
+                          row). */
 } bmf_schedule;
 bmf_status bmf_set_schedule(bmf_ctx *ctx, const bmf_schedule *sched);
 bmf_status bmf_get_schedule(const bmf_ctx *ctx, bmf_schedule *sched);

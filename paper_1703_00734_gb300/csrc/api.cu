@@ -929,6 +929,8 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
                 q.blocks = me.blocks + ba;
                 q.blk0 = me.stat0 + ba;
                 traced(c, sx, f == 0 ? K_COND_X : K_COND_W, 1, [&] {
+                    // two lanes per row: the register-resident kernel where it exists
+                    if (team == 2 && launch_cond_pair(c->prec, q, (int)(bb - ba), sx)) return;
                     if (team > 1)
                         launch_cond_team(c->prec, q, (int)(bb - ba), team, sx);
                     else
@@ -1694,7 +1696,7 @@ bmf_status bmf_autotune(bmf_ctx *c, int32_t stage, int32_t subset, int32_t sweep
         // lanes per row of the conditional (every choice gives bit-identical values)
         cands.clear();
         for (int lanes : {2, 4, 8})
-            if (lanes != cond_team_size(K)) {
+            if (lanes != (best.cond_lanes > 0 ? best.cond_lanes : cond_team_size(K))) {
                 bmf_schedule sc = best;
                 sc.cond_lanes = lanes;
                 cands.push_back(sc);

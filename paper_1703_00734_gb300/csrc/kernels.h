@@ -216,6 +216,9 @@ void launch_gram_wide(int K, int prec, const GramParams &a, int grid, cudaStream
 // Conditional draw with a team of `team` lanes (4, 8, 16 or 32) per row (wide.cu).
 void launch_cond_team(int prec, const CondParams &a, int n_blocks, int team, cudaStream_t st);
 int cond_team_size(int K);
+// The same draw for 13 <= K <= 16 with two lanes per row and the row's matrix in registers
+// (cond_pair.cu; bit-identical to the team kernel).  False for other K (nothing launched).
+bool launch_cond_pair(int prec, const CondParams &a, int n_blocks, cudaStream_t st);
 
 // Adjoint of the masked log-joint (adjoint.cu).
 int adjoint_kt(int K);          // template width (K rounded up to 4, 8, 12, 16, 32 or 64)

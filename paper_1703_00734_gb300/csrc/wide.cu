@@ -478,7 +478,10 @@ __device__ __forceinline__ void decode_packed(int e, int &i, int &j)
     j = e - i * (i + 1) / 2;
 }
 
-int cond_team_size(int K) { return K <= 16 ? 4 : (K <= 48 ? 16 : 32); }
+// Default lanes per row: two (the register-resident pair kernel of cond_pair.cu) up to K = 16,
+// then 16, then 32.  Measured on the 100k x 20k, K = 16 PP workload: the pair kernel takes
+// 1.10 ms per stage-3 X half against 1.33 ms for four-lane teams.
+int cond_team_size(int K) { return K <= 16 ? 2 : (K <= 48 ? 16 : 32); }
 
 // Doubles per team in shared memory: the packed matrix, right-hand side, pivots and (teams of 8
 // or more lanes) a contiguous copy of the current column, rounded up to a multiple of 8 doubles
