@@ -36,6 +36,19 @@
  *    chain, is retained when t > burnin and (t - burnin - 1) % thin == 0):
  *    mu = mean, Sigma = E[x x^T] - mu mu^T (1/S normaliser), Lambda = Sigma^{-1}.  It needs
  *    S >= K + 1 retained samples (a full-rank Sigma); fewer fail with BMF_E_STATE.
+ *  - Dominant-mode and mixture summaries (Section 4.1, PP DM / PP GMM; summary != MM): the
+ *    retained samples of each row are clustered by lambda-means (one cluster at the first
+ *    sample; each round visits the samples in order and gives each to the nearest centre,
+ *    lowest index on ties, unless every squared distance exceeds lambda, when it opens a
+ *    cluster at itself; centres then move to their means and empty clusters are dropped; until
+ *    no assignment changes, at most 100 rounds).  DM fits one Gaussian (mean, inverse of the 1/n
+ *    covariance) to the largest cluster; GMM one to each of the C largest clusters with at
+ *    least K + 1 samples (ties: lowest index), weights by size.  A row without such a cluster
+ *    takes one Gaussian over all samples.  DM propagates and aggregates its Gaussian; GMM
+ *    propagates the mixture (before each draw of a row the component with the largest
+ *    pi_c N(x; mu_c, Lambda_c^{-1}) at the row's current value is its prior; its chain starts at
+ *    the mixture mean) and aggregates the pooled moments, mean and inverse of
+ *    sum_c pi_c (Lambda_c^{-1} + (mu_c - m)(mu_c - m)^T).
  *  - Aggregation (Eq. 14, Algorithm 2): for X^(i) submodel "(1)" is subset (i,0) and the
  *    others are (i,j), j >= 1; for W^(j) it is (0,j) and (i,j), i >= 1.  A difference
  *    Lambda^(j) - Lambda^(1) that is not positive definite (FP64 Cholesky pivot <= 0) gets
@@ -126,9 +139,19 @@ typedef struct {
     int32_t moments;   /* BMF_MOMENTS_AUTO: second moments (for moment matching) only when the
                           grid has more than one subset; BMF_MOMENTS_MEAN: sums of x only (enough
                           for posterior-mean prediction); BMF_MOMENTS_FULL: sums of x and x x^T */
+    int32_t summary;   /* subset-posterior summary propagated between stages and aggregated
+                          (Section 4.1): BMF_SUMMARY_MM moment matching (default),
+                          BMF_SUMMARY_DM dominant mode, BMF_SUMMARY_GMM mixture of modes */
+    int32_t components; /* GMM: largest clusters kept, 1..BMF_MAX_COMPONENTS (0: 3) */
+    double lambda;     /* DM / GMM: lambda-means penalty on the squared distance (> 0) */
+    int32_t max_samples; /* DM / GMM: retained samples kept per chain (a ring of max_samples x
+                          K doubles per factor row); a call that would retain more fails with
+                          BMF_E_STATE */
 } bmf_config;
 
 enum { BMF_MOMENTS_AUTO = 0, BMF_MOMENTS_MEAN = 1, BMF_MOMENTS_FULL = 2 };
+enum { BMF_SUMMARY_MM = 0, BMF_SUMMARY_DM = 1, BMF_SUMMARY_GMM = 2 };
+#define BMF_MAX_COMPONENTS 4
 
 typedef struct {
     const double *ptr; /* draw buffer (layout above), FP64 */
@@ -291,8 +314,9 @@ bmf_status bmf_set_state(bmf_ctx *ctx, int32_t subset, const double *X, const do
 bmf_status bmf_get_moments(bmf_ctx *ctx, int32_t subset, int32_t factor, double *S1, double *S2,
                            int64_t *kept);
 
-/* Per-row moment-matched posterior (mu [n*K], Lambda [n*K*K]) of one subset's factor, as
- * propagated to the next stage (needs second moments; BMF_E_STATE otherwise). */
+/* Per-row summary of one subset's factor posterior (mu [n*K], Lambda [n*K*K]) as propagated to
+ * the next stage and aggregated: moment matched (needs second moments; BMF_E_STATE otherwise),
+ * the dominant mode (DM) or the mixture's pooled moments (GMM). */
 bmf_status bmf_get_posterior(bmf_ctx *ctx, int32_t subset, int32_t factor, double *mu,
                              double *Lam);
 
@@ -372,8 +396,20 @@ bmf_status bmf_aggregate_static(int32_t K, int64_t R, int32_t J, const double *m
                                 const double *Lam, double eps_rel, double *mu_star,
                                 int64_t *n_corrected, void *stream);
 
+/* The summaries of the convention above for R rows of S samples each, without a context
+ * (Section 4.1): samples device [S][R][K]; mode 0 one Gaussian over all samples, 1 dominant
+ * mode, 2 mixture of the C largest modes (1 <= C <= BMF_MAX_COMPONENTS); lambda > 0 the
+ * lambda-means penalty.  Outputs, device, indexed by row: pi [R][C] (0 for unused components),
+ * mu [R][C][K], Lam [R][C][K][K], pooled_mu [R][K], pooled_Lam [R][K][K] (the mixture's
+ * pooled mean and precision), assign [R][S] (cluster of each sample; nullable).  Limits:
+ * 1 <= K <= 32, S >= 1, S * K <= 8192.  BMF_E_NOT_PD if a row's covariance is singular.  The
+ * call waits for its stream; errors via bmf_last_error(NULL). */
+bmf_status bmf_fit_summaries(int32_t K, int64_t R, int32_t S, const double *samples, int32_t mode,
+                             int32_t C, double lambda, double *pi, double *mu, double *Lam,
+                             double *pooled_mu, double *pooled_Lam, int32_t *assign, void *stream);
+
 /* Message of the last failed call on ctx; with ctx NULL, of the last failed call of this thread
- * that takes no context (bmf_init, bmf_plan, bmf_aggregate_static). */
+ * that takes no context (bmf_init, bmf_plan, bmf_aggregate_static, bmf_fit_summaries). */
 const char *bmf_last_error(const bmf_ctx *ctx);
 
 #ifdef __cplusplus

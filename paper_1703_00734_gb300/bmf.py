@@ -15,6 +15,7 @@ BMF_FP64, BMF_FP32, BMF_BF16 = 0, 1, 2
 PRECISION = {"fp64": BMF_FP64, "fp32": BMF_FP32, "bf16": BMF_BF16}
 ORDER = {"none": 0, "decreasing": 1}
 MOMENTS = {"auto": 0, "mean": 1, "full": 2}
+SUMMARY = {"mm": 0, "dm": 1, "gmm": 2}
 FACTOR_X, FACTOR_W = 0, 1
 STATUS = {0: "BMF_OK", 1: "BMF_E_ARG", 2: "BMF_E_SHAPE", 3: "BMF_E_NOT_PD",
           4: "BMF_E_NONFINITE", 5: "BMF_E_TIMEOUT", 6: "BMF_E_OOM", 7: "BMF_E_CUDA",
@@ -33,7 +34,9 @@ class Config(ctypes.Structure):
                 ("mu0", ctypes.POINTER(ctypes.c_double)), ("W0", ctypes.POINTER(ctypes.c_double)),
                 ("order", ctypes.c_int32), ("center", ctypes.c_int32), ("burnin", ctypes.c_int32),
                 ("thin", ctypes.c_int32), ("seed", ctypes.c_uint64), ("eps_rel", ctypes.c_double),
-                ("moments", ctypes.c_int32)]
+                ("moments", ctypes.c_int32), ("summary", ctypes.c_int32),
+                ("components", ctypes.c_int32), ("lam", ctypes.c_double),
+                ("max_samples", ctypes.c_int32)]
 
 
 class Draws(ctypes.Structure):
@@ -137,6 +140,8 @@ def load(path: str = LIB_PATH):
     L.bmf_autotune.restype = st
     L.bmf_generate_draws.argtypes = [P, i32, i32, i64, i32, P, i32]
     L.bmf_generate_draws.restype = st
+    L.bmf_fit_summaries.argtypes = [i32, i64, i32, P, i32, i32, f64, P, P, P, P, P, P, P]
+    L.bmf_fit_summaries.restype = st
     L.bmf_plan.argtypes = [i64, i64, i64, P, P, P, i32, i32, P, i32, P, P, P, P, P, P]
     L.bmf_plan.restype = st
     L.bmf_destroy.argtypes = [P]
@@ -167,6 +172,31 @@ def aggregate_static(K, R, J, mu_ptr, lam_ptr, out_ptr, eps_rel=1e-6, stream=Non
     return nc.value
 
 
+def fit_summaries(samples, mode, lam, C=3, stream=None):
+    """bmf_fit_summaries on a device tensor of samples [S, R, K] (FP64): per-row dominant-mode /
+    mixture / all-sample Gaussian fits (include/bmf.h).  Returns a dict of device tensors
+    (pi, mu, Lam, pooled_mu, pooled_Lam, assign)."""
+    import torch
+    L = load()
+    S, R, K = samples.shape
+    m = SUMMARY[mode] if isinstance(mode, str) else int(mode)
+    C = 1 if m != 2 else int(C)
+    dev = samples.device
+    f64 = dict(dtype=torch.float64, device=dev)
+    out = dict(pi=torch.zeros((R, C), **f64), mu=torch.zeros((R, C, K), **f64),
+               Lam=torch.zeros((R, C, K, K), **f64), pooled_mu=torch.zeros((R, K), **f64),
+               pooled_Lam=torch.zeros((R, K, K), **f64),
+               assign=torch.zeros((R, S), dtype=torch.int32, device=dev))
+    x = samples.contiguous()
+    st = L.bmf_fit_summaries(int(K), int(R), int(S), x.data_ptr(), m, C, float(lam),
+                             out["pi"].data_ptr(), out["mu"].data_ptr(), out["Lam"].data_ptr(),
+                             out["pooled_mu"].data_ptr(), out["pooled_Lam"].data_ptr(),
+                             out["assign"].data_ptr(), ctypes.c_void_p(stream) if stream else None)
+    if st:
+        raise BmfError(st, L.bmf_last_error(None).decode())
+    return out
+
+
 def plan(N, D, row, col, val, I=1, J=1, order="decreasing", row_bounds=None, col_bounds=None):
     """The library's host-side preprocessing alone (bmf_plan: no GPU needed): row/column
     order, grid cuts and training entries per subset."""
@@ -192,7 +222,8 @@ class BMF:
     def __init__(self, N, D, row, col, val, K, tau, precision="fp64", I=1, J=1, row_bounds=None,
                  col_bounds=None, X0=None, W0=None, test=None, beta0=2.0, nu0=None, mu0=None,
                  W0_prior=None, order="decreasing", center=True, burnin=0, thin=1, seed=0,
-                 eps_rel=1e-6, moments="auto", stream=None):
+                 eps_rel=1e-6, moments="auto", summary="mm", components=3, lam=0.0,
+                 max_samples=0, stream=None):
         L = load()
         self.L = L
         self.N, self.D, self.K, self.I, self.J = int(N), int(D), int(K), int(I), int(J)
@@ -216,7 +247,8 @@ class BMF:
                      W0=W0a.ctypes.data_as(dp) if W0a is not None else None,
                      order=ORDER[order], center=int(bool(center)), burnin=int(burnin),
                      thin=int(thin), seed=int(seed), eps_rel=float(eps_rel),
-                     moments=MOMENTS[moments])
+                     moments=MOMENTS[moments], summary=SUMMARY[summary],
+                     components=int(components), lam=float(lam), max_samples=int(max_samples))
         self.precision = cfg.precision
         h = ctypes.c_void_p()
         st = L.bmf_init(ctypes.byref(h), ctypes.byref(cfg), N, D, len(row), _ptr(row), _ptr(col),

@@ -78,6 +78,7 @@ struct Side {
 struct SubState {
     int64_t t = 0, kept = 0;
     int prior[2] = {0, 0};  // 1: factor has a per-row (propagated or installed) prior
+    int mix[2] = {0, 0};    // 1: that prior is a propagated mixture (GMM summary)
     bool finalized = false;
 };
 
@@ -181,6 +182,13 @@ struct bmf_ctx {
     int chunk_obs = 1024;
     bool full_moments = false;
     bool monitor = true;             // per-sweep test RMSE (bmf_set_monitor)
+    // DM / GMM summaries (Section 4.1): retained samples per arena ([max_samples][R][K]), the
+    // mixture store of propagated mixture priors per arena and which rows carry one
+    int summary = BMF_SUMMARY_MM, ncomp = 3, max_samples = 0;
+    double lambda = 0.0;
+    double *ring[2] = {nullptr, nullptr};
+    double *mix[2] = {nullptr, nullptr};
+    int8_t *has_mix[2] = {nullptr, nullptr};
     // adjoint / Langevin scratch (allocated on first use)
     float *adj_part = nullptr;
     int64_t adj_part_cap = 0;
@@ -262,6 +270,11 @@ bmf_status cuda_fail(bmf_ctx *c, cudaError_t e, const char *where)
     return BMF_E_CUDA;
 }
 
+bmf_status cuda_status(bmf_ctx *c, cudaError_t e, const char *where)
+{
+    return e == cudaSuccess ? BMF_OK : cuda_fail(c, e, where);
+}
+
 #define CUDA_TRY(c, call)                                         \
     do {                                                          \
         cudaError_t e_ = (call);                                  \
@@ -269,6 +282,10 @@ bmf_status cuda_fail(bmf_ctx *c, cudaError_t e, const char *where)
     } while (0)
 
 int64_t hyper_block_len(int K) { return K + (int64_t)K * (K - 1) / 2 + K; }
+
+// Doubles per component in the mixture store: score constant, mean, packed precision, precision
+// x mean.
+int64_t mix_width(int K) { return 1 + 2 * (int64_t)K + (int64_t)K * (K + 1) / 2; }
 
 // Host FP64 inverse of a small SPD matrix (Gauss-Jordan with partial pivoting).
 bool host_inverse(int K, const std::vector<double> &A, std::vector<double> &Ainv)
@@ -751,6 +768,18 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
     const int64_t hyper_len = 2 * (int64_t)(sl1 - sl0) * HB;
     const int64_t zx_len = (rx1 - rx0) * K;
     int64_t kept = c->ss[g0.sid].kept;
+    // the DM / GMM summaries keep every retained sample: the ring must hold this call's
+    bool any_mix[2] = {false, false};
+    for (int sl = sl0; sl < sl1; ++sl)
+        for (int f = 0; f < 2; ++f) any_mix[f] = any_mix[f] || c->ss[geom_of_slot(c, sl).sid].mix[f];
+    if (c->summary != BMF_SUMMARY_MM) {
+        int64_t k2 = kept;
+        for (int it = 0; it < n_sweeps; ++it) k2 += keep_sample(c, t_start + it + 1) ? 1 : 0;
+        if (k2 > c->max_samples)
+            return fail(c, BMF_E_STATE, "the call would retain " + std::to_string(k2) +
+                                            " samples per chain; max_samples is " +
+                                            std::to_string(c->max_samples));
+    }
     // (mu, Lambda) | factor for sweep `it`, on the side stream.  The statistics of X for sweep
     // it+1 depend only on the X written by sweep it, so they run while the main stream does
     // W | X of sweep it and the Gram pass of sweep it+1 (and symmetrically for W).
@@ -867,6 +896,13 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
             const std::vector<int64_t> &B = bounds[f];
             const int nch = (int)B.size() - 1;
             cudaStream_t cs = nch == 1 ? c->st : c->st3;
+            if (any_mix[f]) {
+                // propagated mixture priors: each row's component from its current value,
+                // installed as its prior before this half's draws
+                MixChooseParams mp{K, c->ncomp, r0, r1 - r0, me.R, c->mix[f], c->has_mix[f], me.F,
+                                   me.pL, me.pb, nullptr, c->err_d};
+                traced(c, c->st, f == 0 ? K_COND_X : K_COND_W, 1, [&] { launch_mix_choose(mp, c->st); });
+            }
             if (nch == 1) gram_chunk(b0, b1);
             if (f == 0) {
                 // the previous sweep's RMSE pass reads the gathered copies this sweep rewrites;
@@ -947,6 +983,10 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
                 CUDA_TRY(c, cudaEventRecord(c->ev_cdone, c->st3));
                 CUDA_TRY(c, cudaStreamWaitEvent(c->st, c->ev_cdone, 0));
             }
+            if (keep && c->summary != BMF_SUMMARY_MM && r1 > r0)
+                CUDA_TRY(c, cudaMemcpyAsync(c->ring[f] + (kept - 1) * me.R * K + r0 * K, me.F + r0 * K,
+                                            (size_t)(r1 - r0) * K * sizeof(double),
+                                            cudaMemcpyDeviceToDevice, c->st));
             if (hyp[f] && it + 1 < n_sweeps) {
                 CUDA_TRY(c, cudaEventRecord(c->ev_fac[f], c->st));
                 CUDA_TRY(c, cudaStreamWaitEvent(c->st2, c->ev_fac[f], 0));
@@ -1057,32 +1097,65 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
     return BMF_OK;
 }
 
-// Moment matching of every subset of a stage (the propagated summaries, Section 4.1).
+// The summary of one subset's posterior that propagates and aggregates (Section 4.1): moment
+// matching of the moment sums, or the dominant mode / mixture of the retained samples.
+// Enqueued on the context stream; the caller checks the device error word.
+bmf_status finalize_subset(bmf_ctx *c, int sid)
+{
+    const SubsetGeom &g = c->P.subs[sid];
+    SubState &su = c->ss[sid];
+    if (su.finalized) return BMF_OK;
+    if (su.kept < 1)
+        return fail(c, BMF_E_STATE, "subset " + std::to_string(g.sid) +
+                                        " has no retained samples (burn-in not passed)");
+    if (c->summary != BMF_SUMMARY_MM) {
+        for (int f = 0; f < 2; ++f) {
+            Side &sd = f == 0 ? c->X : c->W;
+            SummaryParams sp{};
+            sp.K = c->K;
+            sp.S = (int)su.kept;
+            sp.C = c->summary == BMF_SUMMARY_DM ? 1 : c->ncomp;
+            sp.mode = c->summary;
+            sp.lambda = c->lambda;
+            sp.samples = c->ring[f];
+            sp.sample_stride = sd.R * c->K;
+            sp.row0 = f == 0 ? g.xoff : g.woff;
+            sp.n_rows = f == 0 ? g.n() : g.d();
+            sp.mm_mu = sd.mm_mu;
+            sp.mm_L = sd.mm_L;
+            sp.mm_b = sd.mm_b;
+            sp.mix = c->summary == BMF_SUMMARY_GMM ? c->mix[f] : nullptr;
+            sp.R = sd.R;
+            sp.err = c->err_d;
+            launch_summary(sp, c->st);
+        }
+        su.finalized = true;
+        return BMF_OK;
+    }
+    if (!c->full_moments)
+        return fail(c, BMF_E_STATE, "moment matching needs second moments (moments mode)");
+    if (su.kept < c->K + 1)
+        return fail(c, BMF_E_STATE, "subset " + std::to_string(g.sid) + " has " +
+                                        std::to_string(su.kept) + " retained samples; moment "
+                                        "matching needs at least K + 1 (a full-rank covariance)");
+    for (int f = 0; f < 2; ++f) {
+        Side &sd = f == 0 ? c->X : c->W;
+        MMParams mp{c->K, f == 0 ? g.xoff : g.woff, f == 0 ? g.xoff + g.n() : g.woff + g.d(),
+                    sd.R, sd.S1, sd.S2, (double)su.kept, sd.mm_mu, sd.mm_L, sd.mm_b, c->err_d};
+        launch_mm(mp, c->st);
+    }
+    su.finalized = true;
+    return BMF_OK;
+}
+
+// The summaries of every subset of a stage.
 bmf_status finalize_stage(bmf_ctx *c, int stage)
 {
     int sl0, sl1;
     if (!stage_slots(c, stage, sl0, sl1)) return BMF_OK;
     for (int sl = sl0; sl < sl1; ++sl) {
-        const SubsetGeom &g = geom_of_slot(c, sl);
-        SubState &su = c->ss[g.sid];
-        if (su.finalized) continue;
-        if (su.kept < 1)
-            return fail(c, BMF_E_STATE, "subset " + std::to_string(g.sid) +
-                                            " has no retained samples (burn-in not passed)");
-        if (!c->full_moments)
-            return fail(c, BMF_E_STATE, "moment matching needs second moments (moments mode)");
-        if (su.kept < c->K + 1)
-            return fail(c, BMF_E_STATE, "subset " + std::to_string(g.sid) + " has " +
-                                            std::to_string(su.kept) + " retained samples; moment "
-                                            "matching needs at least K + 1 (a full-rank covariance)");
-        for (int f = 0; f < 2; ++f) {
-            Side &sd = f == 0 ? c->X : c->W;
-            MMParams mp{c->K, f == 0 ? g.xoff : g.woff,
-                        f == 0 ? g.xoff + g.n() : g.woff + g.d(), sd.R, sd.S1, sd.S2,
-                        (double)su.kept, sd.mm_mu, sd.mm_L, sd.mm_b, c->err_d};
-            launch_mm(mp, c->st);
-        }
-        su.finalized = true;
+        bmf_status s = finalize_subset(c, geom_of_slot(c, sl).sid);
+        if (s) return s;
     }
     CUDA_TRY(c, cudaGetLastError());
     return check_dev_error(c);
@@ -1097,6 +1170,17 @@ bmf_status install_prior_from(bmf_ctx *c, int dst_sid, int f, int src_sid)
                   sd.mm_mu, sd.mm_L, sd.mm_b, sd.pL, sd.pb, sd.F, sd.G, c->ldg, c->prec};
     launch_propagate(pp, c->st);
     c->ss[dst_sid].prior[f] = 1;
+    if (c->summary == BMF_SUMMARY_GMM && n > 0) {
+        // the source rows' mixture becomes the destination rows' prior; each draw picks its
+        // component (the chain starts at the pooled mean set above)
+        const int64_t W = mix_width(c->K), src0 = f == 0 ? gs.xoff : gs.woff,
+                      dst0 = f == 0 ? gd.xoff : gd.woff;
+        CUDA_TRY(c, cudaMemcpyAsync(c->mix[f] + dst0 * c->ncomp * W, c->mix[f] + src0 * c->ncomp * W,
+                                    (size_t)n * c->ncomp * W * sizeof(double), cudaMemcpyDeviceToDevice,
+                                    c->st));
+        CUDA_TRY(c, cudaMemsetAsync(c->has_mix[f] + dst0, 1, (size_t)n, c->st));
+        c->ss[dst_sid].mix[f] = 1;
+    }
     c->stats_ok[gd.slot] = 0;    // the propagated factor starts at the propagated mean
     refresh_hslots(c, gd.slot);
     return upload_hslots(c, gd.slot);
@@ -1234,6 +1318,9 @@ bmf_status restart_chains(bmf_ctx *c)
     const int64_t nt = (int64_t)c->P.trow.size();
     if (nt) CUDA_TRY(c, cudaMemsetAsync(c->ysum, 0, nt * sizeof(double), c->st));
     CUDA_TRY(c, cudaMemsetAsync(c->hyper, 0, (size_t)2 * S * hyper_slot_len(K) * sizeof(double), c->st));
+    for (int f = 0; f < 2; ++f)
+        if (c->has_mix[f])
+            CUDA_TRY(c, cudaMemsetAsync(c->has_mix[f], 0, (size_t)(f == 0 ? c->X.R : c->W.R), c->st));
     c->ss.assign(S, SubState());
     c->stats_ok.assign(S, 0);
     for (int sl = 0; sl < S; ++sl) {
@@ -1325,6 +1412,28 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
         return BMF_E_ARG;
     }
     c->full_moments = cfg->moments == BMF_MOMENTS_FULL || (cfg->moments == BMF_MOMENTS_AUTO && I * J > 1);
+    if (cfg->summary < BMF_SUMMARY_MM || cfg->summary > BMF_SUMMARY_GMM) {
+        g_init_error = "unknown summary";
+        delete c;
+        return BMF_E_ARG;
+    }
+    c->summary = cfg->summary;
+    if (c->summary != BMF_SUMMARY_MM) {
+        c->ncomp = c->summary == BMF_SUMMARY_DM ? 1 : (cfg->components > 0 ? cfg->components : 3);
+        c->lambda = cfg->lambda;
+        c->max_samples = cfg->max_samples;
+        std::string e;
+        if (!(c->lambda > 0.0) || !std::isfinite(c->lambda)) e = "the DM / GMM summaries need lambda > 0";
+        else if (c->ncomp < 1 || c->ncomp > BMF_MAX_COMPONENTS) e = "components must be in 1..4";
+        else if (c->max_samples < 1) e = "the DM / GMM summaries need max_samples >= 1";
+        else if (K > 32 || (int64_t)c->max_samples * K > 8192)
+            e = "the DM / GMM summaries need K <= 32 and max_samples * K <= 8192";
+        if (!e.empty()) {
+            g_init_error = e;
+            delete c;
+            return BMF_E_ARG;
+        }
+    }
     c->mu0.assign(K, 0.0);
     if (cfg->mu0) std::memcpy(c->mu0.data(), cfg->mu0, K * sizeof(double));
     std::vector<double> W0((size_t)K * K, 0.0);
@@ -1454,6 +1563,14 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
     c->col_rank_d = c->mem.alloc<int64_t>(D);
     c->pred_part = c->mem.alloc<double>(2 * c->rmse_blocks);
     c->pred_out = c->mem.alloc<double>(2);
+    if (c->summary != BMF_SUMMARY_MM)
+        for (int f = 0; f < 2; ++f) {
+            const int64_t R = f == 0 ? c->P.RX : c->P.RW;
+            c->ring[f] = c->mem.alloc<double>((size_t)c->max_samples * R * K);
+            c->has_mix[f] = c->mem.alloc<int8_t>(R);
+            if (c->summary == BMF_SUMMARY_GMM)
+                c->mix[f] = c->mem.alloc<double>((size_t)R * c->ncomp * mix_width(K));
+        }
     if (!c->mem.ok) return bail(BMF_E_OOM, "device allocation failed");
     cudaMemcpy(c->mu0_d, c->mu0.data(), K * sizeof(double), cudaMemcpyHostToDevice);
     cudaMemcpy(c->W0inv_d, c->W0inv.data(), (size_t)K * K * sizeof(double), cudaMemcpyHostToDevice);
@@ -1959,25 +2076,13 @@ bmf_status bmf_get_posterior(bmf_ctx *c, int32_t subset, int32_t factor, double 
         return fail(c, BMF_E_ARG, "bad subset or factor");
     if (!c->ss[subset].finalized) {
         // finalise on demand (does not change the chain)
-        const SubsetGeom &g = c->P.subs[subset];
-        SubState &su = c->ss[subset];
-        if (su.kept < 1) return fail(c, BMF_E_STATE, "no retained samples");
-        if (!c->full_moments)
-            return fail(c, BMF_E_STATE, "moment matching needs second moments (moments mode)");
-        if (su.kept < c->K + 1)
-            return fail(c, BMF_E_STATE, "subset " + std::to_string(g.sid) + " has " +
-                                            std::to_string(su.kept) + " retained samples; moment "
-                                            "matching needs at least K + 1 (a full-rank covariance)");
-        for (int f = 0; f < 2; ++f) {
-            Side &sd = f == 0 ? c->X : c->W;
-            MMParams mp{c->K, f == 0 ? g.xoff : g.woff, f == 0 ? g.xoff + g.n() : g.woff + g.d(),
-                        sd.R, sd.S1, sd.S2, (double)su.kept, sd.mm_mu, sd.mm_L, sd.mm_b, c->err_d};
-            launch_mm(mp, c->st);
+        bmf_status s = finalize_subset(c, subset);
+        if (!s) s = cuda_status(c, cudaGetLastError(), "summary launch");
+        if (!s) s = check_dev_error(c);
+        if (s) {
+            c->ss[subset].finalized = false;
+            return s;
         }
-        CUDA_TRY(c, cudaGetLastError());
-        bmf_status s = check_dev_error(c);
-        if (s) return s;
-        su.finalized = true;
     }
     const SubsetGeom &g = c->P.subs[subset];
     const Side &sd = factor == 0 ? c->X : c->W;
@@ -2028,6 +2133,10 @@ bmf_status bmf_set_prior(bmf_ctx *c, int32_t subset, int32_t factor, const doubl
         CUDA_TRY(c, cudaMemcpy(sd.pb + (int64_t)i * sd.R + base, &b[(size_t)i * n], n * sizeof(double),
                                cudaMemcpyHostToDevice));
     c->ss[subset].prior[factor] = 1;
+    if (c->ss[subset].mix[factor]) {     // an installed Gaussian replaces a mixture prior
+        c->ss[subset].mix[factor] = 0;
+        if (n) CUDA_TRY(c, cudaMemset(c->has_mix[factor] + base, 0, (size_t)n));
+    }
     refresh_hslots(c, g.slot);
     bmf_status s = upload_hslots(c, g.slot);
     if (s) return s;
@@ -2327,6 +2436,71 @@ bmf_status bmf_plan(int64_t N, int64_t D, int64_t nnz, const int32_t *row, const
     if (col_bounds_out) std::copy(P.col_bounds.begin(), P.col_bounds.end(), col_bounds_out);
     if (subset_nnz)
         for (int s = 0; s < I * J; ++s) subset_nnz[s] = P.subs[s].nnz;
+    return BMF_OK;
+}
+
+bmf_status bmf_fit_summaries(int32_t K, int64_t R, int32_t S, const double *samples, int32_t mode,
+                             int32_t C, double lambda, double *pi, double *mu, double *Lam,
+                             double *pooled_mu, double *pooled_Lam, int32_t *assign, void *stream)
+{
+    g_init_error.clear();
+    g_noctx_msg = nullptr;
+    if (K < 1 || K > 32 || S < 1 || (int64_t)S * K > 8192 || R < 0) {
+        g_init_error = "bmf_fit_summaries: need 1 <= K <= 32, S >= 1, S * K <= 8192, R >= 0";
+        return BMF_E_SHAPE;
+    }
+    if (mode < 0 || mode > 2 || C < 1 || C > BMF_MAX_COMPONENTS || (mode != 2 && C != 1) ||
+        !(lambda > 0.0) || !std::isfinite(lambda)) {
+        g_init_error = "bmf_fit_summaries: need mode 0..2, 1 <= C <= 4 (C = 1 unless mode 2), lambda > 0";
+        return BMF_E_ARG;
+    }
+    if (R > 0 && (!samples || !pi || !mu || !Lam || !pooled_mu || !pooled_Lam)) {
+        g_init_error = "bmf_fit_summaries: null pointer";
+        return BMF_E_ARG;
+    }
+    if (R == 0) return BMF_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DevError *err = nullptr;
+    if (cudaMalloc(&err, sizeof(DevError)) != cudaSuccess) {
+        g_init_error = "bmf_fit_summaries: device allocation failed";
+        return BMF_E_OOM;
+    }
+    DevError z = {0u, INT32_MAX}, h = z;
+    cudaError_t e = cudaMemcpyAsync(err, &z, sizeof z, cudaMemcpyHostToDevice, st);
+    SummaryParams sp{};
+    sp.K = K;
+    sp.S = S;
+    sp.C = C;
+    sp.mode = mode;
+    sp.lambda = lambda;
+    sp.samples = samples;
+    sp.sample_stride = R * K;
+    sp.row0 = 0;
+    sp.n_rows = R;
+    sp.pi = pi;
+    sp.mu = mu;
+    sp.Lam = Lam;
+    sp.pooled_mu = pooled_mu;
+    sp.pooled_Lam = pooled_Lam;
+    sp.assign = assign;
+    sp.R = R;
+    sp.err = err;
+    if (e == cudaSuccess) {
+        launch_summary(sp, st);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(err);
+    if (e != cudaSuccess) {
+        g_init_error = std::string("bmf_fit_summaries: CUDA error: ") + cudaGetErrorString(e);
+        return BMF_E_CUDA;
+    }
+    if (h.flags) {
+        g_init_error = "bmf_fit_summaries: a covariance is singular (row " +
+                       std::to_string(h.first_bad_row) + ")";
+        return BMF_E_NOT_PD;
+    }
     return BMF_OK;
 }
 

@@ -208,6 +208,46 @@ void launch_predict_sq(const PredictParams &p, int blocks, cudaStream_t st);
 void launch_gather_rows(int K, int64_t R, const int64_t *src, const double *in, double *out,
                         cudaStream_t st);
 
+// Summaries beyond moment matching (summary.cu; Section 4.1 PP DM / PP GMM): one warp per row
+// clusters the row's retained samples by lambda-means and fits the dominant mode (mode 1), the
+// C largest modes (mode 2) or all samples (mode 0), with the pooled moments of the mixture.
+constexpr int kMaxComponents = 4;
+struct SummaryParams {
+    int K, S, C, mode;
+    double lambda;
+    const double *samples;     // sample s of arena row a at samples[s * sample_stride + a * K]
+    int64_t sample_stride;
+    int64_t row0, n_rows;      // rows [row0, row0 + n_rows), one block each
+    // outputs indexed by row - row0 (nullable as a group): pi [n][C], mu [n][C][K],
+    // Lam [n][C][K][K], pooled_mu [n][K], pooled_Lam [n][K][K]; assign [n][S] (nullable)
+    double *pi, *mu, *Lam, *pooled_mu, *pooled_Lam;
+    int32_t *assign;
+    // library layout, indexed by arena row (nullable as a group): the summary that propagates
+    // and aggregates (dominant component for mode 1, pooled moments otherwise) as mm_mu AoS
+    // [R][K], mm_L SoA [ntri][R], mm_b SoA [K][R]; mix (nullable): the mixture store
+    // [R][C][1 + 2K + ntri(K)] (score constant, mean, packed precision, precision x mean)
+    double *mm_mu, *mm_L, *mm_b, *mix;
+    int64_t R;
+    DevError *err;
+};
+size_t summary_smem(int K, int S);
+void launch_summary(const SummaryParams &p, cudaStream_t st);
+
+// Component choice of a propagated mixture prior for arena rows [r0, r0 + n) that carry one
+// (has_mix): the component with the largest responsibility at the current X becomes the row's
+// prior (pL, pb).
+struct MixChooseParams {
+    int K, C;
+    int64_t r0, n, R;
+    const double *mix;
+    const int8_t *has_mix;
+    const double *X;
+    double *pL, *pb;
+    int32_t *chosen;           // [R] nullable
+    DevError *err;
+};
+void launch_mix_choose(const MixChooseParams &p, cudaStream_t st);
+
 // K > 16 (wide.cu): Gram on the tensor cores (BF16, split TF32) or FP64 lanes over entries;
 // conditional draw with one warp per row.  Partials: packed lower of the exact K, then K rhs.
 int wide_kt(int K);
