@@ -767,65 +767,92 @@ PART_GRIDS = (1, 3, 5, 10, 30)
 PART_SWEEPS, PART_BURNIN, PART_THIN = 1200, 800, 2    # the paper's chains (200 samples kept)
 
 
+PART_DATASETS = 5                                     # independent data sets (Table 3 means)
+
+
 def run_partitions(args, rank, world, local_rank):
-    """One PP run per r x r grid and row/column order on the simulated data: three stages of
-    1200 sweeps (burn-in 800, thin 2; device generator), then aggregation (Eq. 14, Algorithm 2)
-    and the posterior-mean prediction of every held-out cell.  FP64 throughout, as in the
-    paper's runs.  Time per run: CUDA events around the stages plus the prediction call."""
+    """One PP run per r x r grid and row/column order on each of PART_DATASETS independent
+    simulated data sets (the paper averages five): three stages of 1200 sweeps (burn-in 800,
+    thin 2; device generator), then aggregation (Eq. 14, Algorithm 2) and the posterior-mean
+    prediction of every held-out cell.  FP64 throughout, as in the paper's runs.  Time per run:
+    host clock around the stages plus the prediction call.  Reported per grid and order: the
+    mean test RMSE over the data sets (and each one), the mean time."""
     import torch
-    from paper_1703_00734_gb300 import bmf
+    from paper_1703_00734_gb300 import bmf, synth
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
-    d = load_workload(args.workload, args.scale)
-    K, tau = d["K"], d["tau"]
     T, B = PART_SWEEPS, PART_BURNIN
     if args.scale < 1.0:                  # shrunk runs (tests, captures): shorter chains
         T, B = 120, 80
+    n_sets = args.datasets if args.datasets > 0 else PART_DATASETS
+    base_seed = synth.WORKLOADS[args.workload]["seed"]
     runs, launches = [], 0
     with ClockSampler(local_rank) as clk:
-        for order in ("decreasing", "none"):
-            for g in PART_GRIDS:
-                if g > min(d["N"], d["D"]):
-                    continue
-                m = bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], K, tau, "fp64",
-                            I=g, J=g, X0=d["X0"], W0=d["W0"], order=order, burnin=B,
-                            thin=PART_THIN, seed=rank, stream=stream.cuda_stream)
-                torch.cuda.synchronize()
-                n0 = m.launch_count()
-                stage_ms = []
-                t0 = time.perf_counter()
-                for stage in ((1,) if g == 1 else (1, 2, 3)):
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    m.stage(stage, T, None)
-                    e1.record(stream)
-                    e1.synchronize()
-                    stage_ms.append(e0.elapsed_time(e1))
-                _, rmse = m.predict(d["test_row"], d["test_col"], d["test_val"])
-                secs = time.perf_counter() - t0
-                launches += m.launch_count() - n0
-                m.close()
-                runs.append({"grid": f"{g}x{g}", "order": order, "rmse": rmse,
-                             "seconds": secs, "stage_ms": stage_ms})
-                log(f"{order} {g}x{g}: rmse {rmse:.4f} in {secs:.2f} s")
+        for ds in range(n_sets):
+            # data set 0 is the named workload; the others draw X, W, E and the missing cells
+            # from independent seeds
+            t0 = time.time()
+            d = synth.make_workload(args.workload, scale=args.scale,
+                                    **({} if ds == 0 else {"seed": base_seed + 1000 * ds}))
+            log(f"data set {ds}: N={d['N']} D={d['D']} train={len(d['row'])} "
+                f"test={len(d['test_row'])} ({time.time() - t0:.1f}s)")
+            K, tau = d["K"], d["tau"]
+            for order in ("decreasing", "none"):
+                for g in PART_GRIDS:
+                    if g > min(d["N"], d["D"]):
+                        continue
+                    m = bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], K, tau, "fp64",
+                                I=g, J=g, X0=d["X0"], W0=d["W0"], order=order, burnin=B,
+                                thin=PART_THIN, seed=rank + 17 * ds, stream=stream.cuda_stream)
+                    m.set_monitor(False)
+                    torch.cuda.synchronize()
+                    n0 = m.launch_count()
+                    stage_ms = []
+                    t0 = time.perf_counter()
+                    for stage in ((1,) if g == 1 else (1, 2, 3)):
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        m.stage(stage, T, None)
+                        e1.record(stream)
+                        e1.synchronize()
+                        stage_ms.append(e0.elapsed_time(e1))
+                    _, rmse = m.predict(d["test_row"], d["test_col"], d["test_val"])
+                    secs = time.perf_counter() - t0
+                    launches += m.launch_count() - n0
+                    m.close()
+                    runs.append({"dataset": ds, "grid": f"{g}x{g}", "order": order, "rmse": rmse,
+                                 "seconds": secs, "stage_ms": stage_ms})
+                    log(f"set {ds} {order} {g}x{g}: rmse {rmse:.4f} in {secs:.2f} s")
     if rank != 0:
         return None
-    for r in runs:
-        base = next(q for q in runs if q["order"] == r["order"] and q["grid"] == "1x1")
-        r["wts"] = base["seconds"] / r["seconds"]
-    head = next((r for r in runs if r["grid"] == "10x10" and r["order"] == "decreasing"), runs[-1])
+    table = []
+    for order in ("decreasing", "none"):
+        for g in PART_GRIDS:
+            rs = [q for q in runs if q["order"] == order and q["grid"] == f"{g}x{g}"]
+            if not rs:
+                continue
+            table.append({"grid": f"{g}x{g}", "order": order,
+                          "rmse_mean": float(np.mean([q["rmse"] for q in rs])),
+                          "rmse_sd": float(np.std([q["rmse"] for q in rs])),
+                          "rmse_by_dataset": [q["rmse"] for q in rs],
+                          "seconds_mean": float(np.mean([q["seconds"] for q in rs])),
+                          "datasets": len(rs)})
+    for r in table:
+        base = next(q for q in table if q["order"] == r["order"] and q["grid"] == "1x1")
+        r["wts"] = base["seconds_mean"] / r["seconds_mean"]
+    head = next((r for r in table if r["grid"] == "10x10" and r["order"] == "decreasing"),
+                table[-1])
     return {
         "metric": "test RMSE of PP by partition (simulated data, Section 5.3)", "impl": "ours",
-        "value": head["rmse"], "unit": "RMSE", "n_gpus": world, "steps": T, "warmup": 0,
-        "ms_per_step": head["seconds"] * 1e3 / (3 * T), "higher_is_better": False,
+        "value": head["rmse_mean"], "unit": "RMSE", "n_gpus": world, "steps": T, "warmup": 0,
+        "ms_per_step": head["seconds_mean"] * 1e3 / (3 * T), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "N": d["N"], "D": d["D"],
-                   "train_obs": len(d["row"]), "test_obs": len(d["test_row"]), "K": K,
-                   "tau": tau, "sweeps_per_stage": T, "burnin": B, "thin": PART_THIN,
-                   "value_run": f"{head['grid']} {head['order']}"},
-        "runs": runs, "gpu_launches": launches, "clocks": clk.summary(),
+        "config": {"workload": args.workload, "K": 5, "tau": 1.0, "sweeps_per_stage": T,
+                   "burnin": B, "thin": PART_THIN, "datasets": n_sets,
+                   "value_run": f"{head['grid']} {head['order']}, mean over {n_sets} data sets"},
+        "table": table, "runs": runs, "gpu_launches": launches, "clocks": clk.summary(),
     }
 
 
@@ -1061,6 +1088,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch schedule instead of running the schedule tuner")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--datasets", type=int, default=0,
+                    help="simulated-data experiment: independent data sets (0: five)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload (rows and columns by s, observations by s^2); "
                          "for profiling captures only, not a bench configuration")

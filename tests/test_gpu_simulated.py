@@ -11,7 +11,9 @@ import sys
 import numpy as np
 import pytest
 
+import oracle
 from paper_1703_00734_gb300 import synth
+from pairing import Pair, assert_rows_close
 
 pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -37,14 +39,36 @@ def test_pp_matches_the_full_chain_on_simulated_data(name):
     assert abs(pp - full) < 0.05
 
 
+@pytest.mark.parametrize("name", ["sim-6040x3706-k5", "sim-6040x3706-k5-structured"])
+def test_fine_grid_pp_matches_the_oracle_per_state(name):
+    """A 10 x 10 grid (100 subsets, 81 in stage 3) on a tenth-size simulated data set: every
+    subset chain of the three stages against the oracle on the same generated draws, the
+    moment-matched summaries, and the aggregated posterior means."""
+    d = synth.make_workload(name, scale=0.1)
+    pr = Pair(d, 5, I=10, J=10, burnin=10, thin=2, gen=True, seed=21)
+    for stage in (1, 2, 3):
+        pr.run_stage(stage, 40)
+        for s in pr.p.stage_subsets(stage):
+            pr.compare_subset(s.sid, rel=1e-7)
+        pr.finish_stage(stage)
+    Xo, Wo, nco = oracle.aggregate_plan(pr.p, pr.finals, 5)
+    Xm, Wm, nc = pr.m.posterior_means()
+    assert nc == nco
+    assert_rows_close(Xm, Xo[np.argsort(pr.p.row_perm)], 1e-6, "aggregated X")
+    assert_rows_close(Wm, Wo[np.argsort(pr.p.col_perm)], 1e-6, "aggregated W")
+    pr.m.close()
+
+
 def test_partition_mode_of_the_benchmark():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--workload",
-                        "sim-6040x3706-k5", "--scale", "0.1"], capture_output=True, text=True,
-                       timeout=600, cwd=ROOT)
+                        "sim-6040x3706-k5", "--scale", "0.1", "--datasets", "2"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     out = json.loads(r.stdout.strip().splitlines()[-1])
-    grids = {(q["grid"], q["order"]) for q in out["runs"]}
+    grids = {(q["grid"], q["order"]) for q in out["table"]}
     assert grids == {(f"{g}x{g}", o) for g in (1, 3, 5, 10, 30) for o in ("decreasing", "none")}
+    assert all(q["datasets"] == 2 for q in out["table"])
+    assert {q["dataset"] for q in out["runs"]} == {0, 1}
     table = [(q["grid"], q["order"], round(q["rmse"], 4)) for q in out["runs"]]
     assert all(np.isfinite(q["rmse"]) and q["rmse"] > 1.0 for q in out["runs"]), table
     # at a tenth of the size a 10 x 10 grid leaves about 7 training cells per row and subset
