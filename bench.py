@@ -856,6 +856,109 @@ def run_partitions(args, rank, world, local_rank):
     }
 
 
+# ---------------------------------------------------------------------------------------
+# correlations of the subset posteriors (Section 5.6): PP against independent subsets
+# ---------------------------------------------------------------------------------------
+CORR_GRIDS = (3, 5, 10)
+
+
+def align_latent(A, B):
+    """B's latent columns permuted and sign-flipped to match A's: greedily pair the columns with
+    the largest absolute correlation (the alignment applied to embarrassingly parallel MCMC
+    before correlating its subset posteriors, Section 5.6)."""
+    K = A.shape[1]
+    Az = (A - A.mean(0)) / (A.std(0) + 1e-300)
+    Bz = (B - B.mean(0)) / (B.std(0) + 1e-300)
+    Cm = Az.T @ Bz / len(A)
+    perm, sign = np.zeros(K, int), np.ones(K)
+    free_a, free_b = set(range(K)), set(range(K))
+    for _ in range(K):
+        i, j = max(((i, j) for i in free_a for j in free_b), key=lambda ij: abs(Cm[ij]))
+        perm[i], sign[i] = j, 1.0 if Cm[i, j] >= 0 else -1.0
+        free_a.discard(i)
+        free_b.discard(j)
+    return B[:, perm] * sign
+
+
+def block_correlation(A, B):
+    """Pearson correlation of two posterior-mean blocks over all their entries."""
+    a, b = A.ravel() - A.mean(), B.ravel() - B.mean()
+    return float(a @ b / np.sqrt((a @ a) * (b @ b)))
+
+
+def subset_correlations(means, I, J):
+    """cor(X^(i,0), X^(i,j)) for j >= 1 and cor(W^(0,j), W^(i,j)) for i >= 1 (0-based), raw and
+    after aligning the latent dimensions; means[sid] = (X mean block, W mean block)."""
+    raw, aligned = [], []
+    for i in range(I):
+        for j in range(1, J):
+            A, B = means[i * J][0], means[i * J + j][0]
+            raw.append(block_correlation(A, B))
+            aligned.append(block_correlation(A, align_latent(A, B)))
+    for j in range(J):
+        for i in range(1, I):
+            A, B = means[j][1], means[i * J + j][1]
+            raw.append(block_correlation(A, B))
+            aligned.append(block_correlation(A, align_latent(A, B)))
+    stats = lambda v: {"mean": float(np.mean(v)), "min": float(np.min(v)), "max": float(np.max(v)),
+                       "pairs": len(v)}
+    return {"raw": stats(raw), "aligned": stats(aligned)}
+
+
+def run_correlations(args, rank, world, local_rank):
+    """Section 5.6 on the simulated data: for each grid, PP (Algorithm 1, moment matching) and
+    embarrassingly parallel MCMC (every subset with the standard priors, no propagation) on the
+    same data, 1200 sweeps per subset chain (burn-in 800, thin 2; device generator); the
+    posterior means of every subset's X and W blocks (means of the retained samples), and the
+    correlations between blocks estimated in subsets that share rows or columns."""
+    import torch
+    from paper_1703_00734_gb300 import bmf
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    d = load_workload(args.workload, args.scale)
+    K, tau = d["K"], d["tau"]
+    T, B = PART_SWEEPS, PART_BURNIN
+    if args.scale < 1.0:
+        T, B = 120, 80
+    out_rows = []
+    with ClockSampler(local_rank) as clk:
+        for g in CORR_GRIDS:
+            if g > min(d["N"], d["D"]):
+                continue
+            row = {"grid": f"{g}x{g}"}
+            for method, indep in (("pp", False), ("independent", True)):
+                m = bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], K, tau, "fp64", I=g,
+                            J=g, X0=d["X0"], W0=d["W0"], burnin=B, thin=PART_THIN, seed=rank + 5,
+                            independent=indep, moments="full", stream=stream.cuda_stream)
+                t0 = time.perf_counter()
+                for stage in (1, 2, 3):
+                    m.stage(stage, T, None)
+                means = {sid: (m.get_posterior(sid, 0)[0], m.get_posterior(sid, 1)[0])
+                         for sid in range(g * g)}
+                _, rmse = m.predict(d["test_row"], d["test_col"], d["test_val"])
+                row[method] = dict(subset_correlations(means, g, g), rmse=rmse,
+                                   seconds=time.perf_counter() - t0)
+                m.close()
+                log(f"{g}x{g} {method}: corr raw {row[method]['raw']['mean']:.3f} aligned "
+                    f"{row[method]['aligned']['mean']:.3f} rmse {rmse:.4f}")
+            out_rows.append(row)
+    if rank != 0:
+        return None
+    head = next((r for r in out_rows if r["grid"] == "5x5"), out_rows[-1])
+    return {
+        "metric": "correlation of subset posterior means (Section 5.6)", "impl": "ours",
+        "value": head["pp"]["raw"]["mean"], "unit": "Pearson r", "n_gpus": world, "steps": T,
+        "warmup": 0, "ms_per_step": head["pp"]["seconds"] * 1e3 / (3 * T),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "K": K,
+                                         "sweeps_per_stage": T, "burnin": B, "thin": PART_THIN,
+                                         "value_run": f"{head['grid']} PP, raw correlation"},
+        "grids": out_rows, "clocks": clk.summary(),
+    }
+
+
 def traffic_for(kernel, prec, workload):
     """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary, if one
     matches (null otherwise)."""
@@ -1090,6 +1193,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--datasets", type=int, default=0,
                     help="simulated-data experiment: independent data sets (0: five)")
+    ap.add_argument("--experiment", default="partitions", choices=["partitions", "correlations"],
+                    help="simulated data: the partition experiment (Section 5.3) or the "
+                         "subset-posterior correlations (Section 5.6)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload (rows and columns by s, observations by s^2); "
                          "for profiling captures only, not a bench configuration")
@@ -1116,6 +1222,8 @@ def main():
                     out["plain_sweep_zipf"] = plain
         elif MODES.get(args.workload) == "adjoint":
             out = run_adjoint(args, rank, world, local_rank)
+        elif MODES.get(args.workload) == "partitions" and args.experiment == "correlations":
+            out = run_correlations(args, rank, world, local_rank)
         elif MODES.get(args.workload) == "partitions":
             out = run_partitions(args, rank, world, local_rank)
         else:

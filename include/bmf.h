@@ -147,6 +147,10 @@ typedef struct {
     int32_t max_samples; /* DM / GMM: retained samples kept per chain (a ring of max_samples x
                           K doubles per factor row); a call that would retain more fails with
                           BMF_E_STATE */
+    int32_t independent; /* 1: no propagation -- every subset keeps the standard priors with its
+                          own hyperparameter draws and its chain starts at the initial state
+                          (the embarrassingly parallel MCMC baseline of Section 5.4, used by the
+                          subset-posterior correlations of Section 5.6); 0: Algorithm 1 */
 } bmf_config;
 
 enum { BMF_MOMENTS_AUTO = 0, BMF_MOMENTS_MEAN = 1, BMF_MOMENTS_FULL = 2 };

@@ -597,11 +597,14 @@ def finalize(st: ChainState, summary="mm", lam=0.0, C=3):
             dict(pi=fw["pi"], mu=fw["mu"], Lam=fw["Lam"]))
 
 
-def setup_stage_chains(plan_: Plan, stage, X0, W0, K, finals: dict, summary="mm"):
+def setup_stage_chains(plan_: Plan, stage, X0, W0, K, finals: dict, summary="mm",
+                       propagate=True):
     """Chains of one stage.  X0/W0 are the caller's initial states in the reordered index
     space.  Propagated priors (Algorithm 1):
       stage 2, (i,0): W^(0) from subset (0,0);  (0,j): X^(0) from subset (0,0);
-      stage 3, (i,j): X^(i) from subset (i,0), W^(j) from subset (0,j)."""
+      stage 3, (i,j): X^(i) from subset (i,0), W^(j) from subset (0,j).
+    propagate=False: every subset keeps the standard priors and starts at the initial state
+    (embarrassingly parallel MCMC, the baseline of Sections 5.4 and 5.6)."""
     J = plan_.J
     chains = {}
     for s in plan_.stage_subsets(stage):
@@ -609,7 +612,9 @@ def setup_stage_chains(plan_: Plan, stage, X0, W0, K, finals: dict, summary="mm"
         if summary != "mm":
             st.samples_X, st.samples_W = [], []
         src_x = src_w = None
-        if stage == 2:
+        if not propagate:
+            pass
+        elif stage == 2:
             if s.j == 0:
                 src_w = 0                  # subset (0,0)
             else:
@@ -660,7 +665,7 @@ def aggregate_plan(plan_: Plan, finals: dict, K, eps_rel=1e-6):
 
 
 def pp_run(plan_: Plan, K, tau, prior, X0, W0, draws_fn, T, burnin, thin, eps_rel=1e-6,
-           summary="mm", lam=0.0, C=3):
+           summary="mm", lam=0.0, C=3, propagate=True):
     """Algorithm 1: stages I, II, III (each stage's subsets in id order), then Algorithm 2.
     ``draws_fn(stage, t)`` gives the stage's draw buffer for sweep t.  X0/W0 are in the
     reordered index space.  ``summary``: the approximation propagated between stages and
@@ -673,7 +678,7 @@ def pp_run(plan_: Plan, K, tau, prior, X0, W0, draws_fn, T, burnin, thin, eps_re
         subs = plan_.stage_subsets(stage)
         if not subs:
             continue
-        chains = setup_stage_chains(plan_, stage, X0, W0, K, finals, summary)
+        chains = setup_stage_chains(plan_, stage, X0, W0, K, finals, summary, propagate)
         run_stage(plan_, stage, chains, K, tau, prior, lambda t: draws_fn(stage, t), T,
                   burnin, thin)
         for sid, st in chains.items():

@@ -36,7 +36,7 @@ class Config(ctypes.Structure):
                 ("thin", ctypes.c_int32), ("seed", ctypes.c_uint64), ("eps_rel", ctypes.c_double),
                 ("moments", ctypes.c_int32), ("summary", ctypes.c_int32),
                 ("components", ctypes.c_int32), ("lam", ctypes.c_double),
-                ("max_samples", ctypes.c_int32)]
+                ("max_samples", ctypes.c_int32), ("independent", ctypes.c_int32)]
 
 
 class Draws(ctypes.Structure):
@@ -223,7 +223,7 @@ class BMF:
                  col_bounds=None, X0=None, W0=None, test=None, beta0=2.0, nu0=None, mu0=None,
                  W0_prior=None, order="decreasing", center=True, burnin=0, thin=1, seed=0,
                  eps_rel=1e-6, moments="auto", summary="mm", components=3, lam=0.0,
-                 max_samples=0, stream=None):
+                 max_samples=0, independent=False, stream=None):
         L = load()
         self.L = L
         self.N, self.D, self.K, self.I, self.J = int(N), int(D), int(K), int(I), int(J)
@@ -248,7 +248,8 @@ class BMF:
                      order=ORDER[order], center=int(bool(center)), burnin=int(burnin),
                      thin=int(thin), seed=int(seed), eps_rel=float(eps_rel),
                      moments=MOMENTS[moments], summary=SUMMARY[summary],
-                     components=int(components), lam=float(lam), max_samples=int(max_samples))
+                     components=int(components), lam=float(lam), max_samples=int(max_samples),
+                     independent=int(bool(independent)))
         self.precision = cfg.precision
         h = ctypes.c_void_p()
         st = L.bmf_init(ctypes.byref(h), ctypes.byref(cfg), N, D, len(row), _ptr(row), _ptr(col),

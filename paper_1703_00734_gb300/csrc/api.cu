@@ -185,6 +185,7 @@ struct bmf_ctx {
     // DM / GMM summaries (Section 4.1): retained samples per arena ([max_samples][R][K]), the
     // mixture store of propagated mixture priors per arena and which rows carry one
     int summary = BMF_SUMMARY_MM, ncomp = 3, max_samples = 0;
+    bool independent = false;        // no propagation between stages (cfg.independent)
     double lambda = 0.0;
     double *ring[2] = {nullptr, nullptr};
     double *mix[2] = {nullptr, nullptr};
@@ -1197,7 +1198,7 @@ bmf_status open_stage(bmf_ctx *c, int stage)
     int sl0, sl1;
     if (!stage_slots(c, stage, sl0, sl1))
         return fail(c, BMF_E_STATE, "stage " + std::to_string(stage) + " has no subsets");
-    if (stage > 1) {
+    if (stage > 1 && !c->independent) {
         bmf_status s = finalize_stage(c, stage - 1);
         if (s) return s;
         const int J = c->P.J;
@@ -1240,8 +1241,11 @@ bmf_status aggregate_all(bmf_ctx *c, int64_t *n_corrected)
     const int I = c->P.I, J = c->P.J, K = c->K;
     bool single = (I == 1 && J == 1);
     if (!single) {
-        s = finalize_stage(c, c->stage_open);
-        if (s) return s;
+        // with propagation the earlier stages were summarised when the next one opened
+        for (int st = c->independent ? 1 : c->stage_open; st <= c->stage_open; ++st) {
+            s = finalize_stage(c, st);
+            if (s) return s;
+        }
     }
     CUDA_TRY(c, cudaMemsetAsync(c->ncorr_d, 0, sizeof(unsigned long long), c->st));
     int64_t nb_done = 0;   // launches so far (their bases are at agg_base + nb_done * max(I, J))
@@ -1418,6 +1422,7 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
         return BMF_E_ARG;
     }
     c->summary = cfg->summary;
+    c->independent = cfg->independent != 0;
     if (c->summary != BMF_SUMMARY_MM) {
         c->ncomp = c->summary == BMF_SUMMARY_DM ? 1 : (cfg->components > 0 ? cfg->components : 3);
         c->lambda = cfg->lambda;

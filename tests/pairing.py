@@ -31,11 +31,13 @@ class Pair:
     """A library context and the oracle's chains on the same data."""
 
     def __init__(self, d, K, I=1, J=1, precision="fp64", burnin=0, thin=1, seed=11, center=True,
-                 order="decreasing", prior=None, gen=False, **kw):
+                 order="decreasing", prior=None, gen=False, propagate=True, **kw):
         """gen: draws from the counter-based generator (the library's device generator with
         draws == NULL, the oracle's own implementation of it), else from synth."""
         from paper_1703_00734_gb300 import bmf
-        self.d, self.K, self.seed, self.gen = d, K, seed, gen
+        self.d, self.K, self.seed, self.gen, self.propagate = d, K, seed, gen, propagate
+        if not propagate:
+            kw["independent"] = True
         if gen:
             kw["seed"] = seed
         self.prior = prior or oracle.NWPrior(K)
@@ -66,7 +68,8 @@ class Pair:
         if cpu:
             if t0 == 0:
                 self.chains.update(oracle.setup_stage_chains(self.p, stage, self.X0, self.W0,
-                                                             self.K, self.finals))
+                                                             self.K, self.finals,
+                                                             propagate=self.propagate))
             stage_chains = {s.sid: self.chains[s.sid] for s in subs}
             oracle.run_stage(self.p, stage, stage_chains, self.K, self.d["tau"], self.prior,
                              lambda t: self.draws(stage, t0 + t), T, self.burnin, self.thin)

@@ -257,3 +257,23 @@ def test_restart_reproduces_a_run_and_test_rmse_matches_predict():
     assert r5 == r1
     np.testing.assert_array_equal(X5, X1)
     f.close()
+
+
+def test_independent_subsets_fp64_parity():
+    """The embarrassingly parallel baseline (no propagation: standard priors and hyperparameter
+    draws in every subset, chains from the initial state) against the oracle with the same
+    draws, through the three stages, and the aggregation of its subset posteriors."""
+    d = small(N=240, D=160, M=9000, K=4, seed=17)
+    pr = Pair(d, 4, I=3, J=2, burnin=3, propagate=False)
+    for stage in (1, 2, 3):
+        pr.run_stage(stage, 12)
+        for s in pr.p.stage_subsets(stage):
+            pr.compare_subset(s.sid, rel=1e-7)
+            st = pr.chains[s.sid]
+            assert not st.prior_x and not st.prior_w
+        pr.finish_stage(stage)
+    Xm_o, Wm_o, nc_o = oracle.aggregate_plan(pr.p, pr.finals, 4)
+    Xm, Wm, nc = pr.m.posterior_means()
+    assert nc == nc_o
+    assert_rows_close(Xm, Xm_o[np.argsort(pr.p.row_perm)], 1e-6, "aggregated X")
+    assert_rows_close(Wm, Wm_o[np.argsort(pr.p.col_perm)], 1e-6, "aggregated W")

@@ -76,3 +76,18 @@ def test_partition_mode_of_the_benchmark():
     # are held to the full chain's neighbourhood here; the full-size runs are the experiment
     assert all(q["rmse"] < 1.2 for q in out["runs"] if q["grid"] in ("1x1", "3x3")), table
     assert out["gpu_launches"] > 0
+
+
+def test_correlation_experiment_of_the_benchmark():
+    """Section 5.6 at a tenth of the size: PP's subset posterior means correlate across subsets
+    sharing rows or columns more strongly than those of independent subsets (without the
+    alignment the baseline's latent dimensions disagree)."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--workload",
+                        "sim-6040x3706-k5", "--scale", "0.1", "--experiment", "correlations"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    assert [g["grid"] for g in out["grids"]] == ["3x3", "5x5", "10x10"]
+    for g in out["grids"]:
+        assert g["pp"]["raw"]["mean"] > g["independent"]["raw"]["mean"], g
+        assert g["pp"]["raw"]["mean"] > g["independent"]["aligned"]["mean"], g

@@ -213,3 +213,44 @@ def test_stage_sources_and_hyperparameter_rule(orc):
             mx0, mw0 = before[s.sid]
             assert np.array_equal(st.muX, mx0) == bool(st.prior_x)   # drawn iff not propagated
             assert np.array_equal(st.muW, mw0) == bool(st.prior_w)
+
+
+def test_independent_subsets_are_standalone_chains(orc):
+    """Without propagation (the embarrassingly parallel baseline of Sections 5.4 and 5.6) every
+    subset's chain is the plain sampler on that subset's data alone: a 1 x 1 plan built from
+    the block's entries, its own hyperparameter draws and z's taken from the stage's buffer,
+    the initial state of the block."""
+    K, I, J, T = 3, 3, 2, 4
+    d = synth.make_workload(None, N=54, D=40, M=1300, pattern="uniform", K=K, sigma=0.5,
+                            tau=4.0, seed=23)
+    p = orc.plan(d["N"], d["D"], d["row"], d["col"], d["val"], I, J)
+    prior = orc.NWPrior(K)
+    X0, W0 = d["X0"][p.row_perm], d["W0"][p.col_perm]
+    rrank, crank = np.argsort(p.row_perm), np.argsort(p.col_perm)
+    nr, nc = rrank[d["row"]], crank[d["col"]]
+    vc = d["val"] - p.offset
+    H = orc.hyper_block_len(K)
+    for stage in (1, 2, 3):
+        subs = p.stage_subsets(stage)
+        chains = orc.setup_stage_chains(p, stage, X0, W0, K, {}, propagate=False)
+        rng = np.random.default_rng(100 + stage)
+        bufs = [synth.sweep_draws([(s.n, s.d) for s in subs], K, prior.nu0, rng) for _ in range(T)]
+        orc.run_stage(p, stage, chains, K, d["tau"], prior, lambda t: bufs[t], T)
+        lay = orc.stage_draw_layout(subs, K)
+        for s in subs:
+            st = chains[s.sid]
+            assert not st.prior_x and not st.prior_w
+            m = (nr >= s.r0) & (nr < s.r1) & (nc >= s.c0) & (nc < s.c1)
+            q = orc.plan(s.n, s.d, nr[m] - s.r0, nc[m] - s.c0, vc[m], 1, 1, order="none",
+                         center=False)
+            alone = orc.new_chain(X0[s.r0:s.r1], W0[s.c0:s.c1], K)
+            for t in range(T):
+                b = bufs[t]
+                orc.sweep_subset(q.subsets[0], alone, K, d["tau"], prior,
+                                 b[lay[(s.sid, "hx")]:lay[(s.sid, "hx")] + H],
+                                 b[lay[(s.sid, "hw")]:lay[(s.sid, "hw")] + H],
+                                 b[lay[(s.sid, "zx")]:lay[(s.sid, "zx")] + s.n * K],
+                                 b[lay[(s.sid, "zw")]:lay[(s.sid, "zw")] + s.d * K])
+            np.testing.assert_array_equal(st.X, alone.X)
+            np.testing.assert_array_equal(st.W, alone.W)
+            np.testing.assert_array_equal(st.LamX, alone.LamX)
