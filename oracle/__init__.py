@@ -85,9 +85,12 @@ def lib():
         i64, i32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_double
         L.orc_nw_posterior.argtypes = [i32, i64, P, P, f64, f64, P, P, P, P, P, P, P]
         L.orc_nw_draw.argtypes = [i32, P, f64, P, P, P, P, P, P]
-        L.orc_update_rows.argtypes = [i32, i64, P, P, P, P, f64, i32, P, P, P, P, P]
+        L.orc_update_rows.argtypes = [i32, i64, P, P, P, P, f64, P, P, i32, P, P, P, P, P]
         L.orc_sweep.argtypes = [i32, i64, i64, P, P, P, P, P, P, f64, P, f64, f64, P,
-                                i32, P, P, i32, P, P, P, P, P, P, P, P, P, P]
+                                i32, P, P, i32, P, P, P, P, P, P, P, P, P,
+                                i32, f64, f64, P, P, P]
+        L.orc_noise_update.argtypes = [i32, i64, P, P, P, P, P, i32, f64, f64, P, P]
+        L.orc_gen_noise.argtypes = [ctypes.c_uint64, i64, i32, i64, P, P]
         L.orc_moments_accumulate.argtypes = [i32, i64, P, P, P]
         L.orc_moments_accumulate.restype = None
         L.orc_mm_finalize.argtypes = [i32, i64, i64, P, P, P, P, P]
@@ -185,8 +188,10 @@ def nw_draw(post, hdraw, K):
     return mu, Lam
 
 
-def update_rows(ptr, idx, val, P, tau, mu_p, Lam_p, z, per_row_prior=False):
-    """Draw every row of a CSR block from its Gaussian conditional (see bmf_oracle.c)."""
+def update_rows(ptr, idx, val, P, tau, mu_p, Lam_p, z, per_row_prior=False, tau_partner=None,
+                tau_row=None):
+    """Draw every row of a CSR block from its Gaussian conditional (see bmf_oracle.c); the
+    noise precision of an entry is tau_partner[partner], tau_row[row] or tau."""
     mu_p, Lam_p, z = _f64(mu_p), _f64(Lam_p), _f64(z)
     K = mu_p.shape[-1]
     P = _f64(P).reshape(-1, K)
@@ -196,11 +201,51 @@ def update_rows(ptr, idx, val, P, tau, mu_p, Lam_p, z, per_row_prior=False):
     R = len(ptr) - 1
     out = np.zeros((R, K))
     bad = ctypes.c_int64(-1)
-    st = lib().orc_update_rows(K, R, _p(ptr), _p(idx), _p(val), _p(P), tau, int(per_row_prior),
-                               _p(mu_p), _p(Lam_p), _p(z), _p(out), ctypes.byref(bad))
+    tp = None if tau_partner is None else _f64(tau_partner)
+    tr = None if tau_row is None else _f64(tau_row)
+    st = lib().orc_update_rows(K, R, _p(ptr), _p(idx), _p(val), _p(P), tau, _p(tp), _p(tr),
+                               int(per_row_prior), _p(mu_p), _p(Lam_p), _p(z), _p(out),
+                               ctypes.byref(bad))
     if st:
         raise OracleError(f"update_rows: row {bad.value} not positive definite")
     return out
+
+
+@dataclass
+class NoiseModel:
+    """Sampled noise precision (Section 2.1): mode "global" (one precision per chain) or
+    "column" (one per column, tau_d), Gamma(a0, b0) priors (shape, rate), chains starting at
+    tau0."""
+    mode: str
+    a0: float
+    b0: float
+    tau0: float
+
+    @property
+    def code(self):
+        return {"fixed": 0, "global": 1, "column": 2}[self.mode]
+
+
+def noise_update(cptr, cidx, cval, X, W, mode, a0, b0, draw):
+    """The noise precisions given the new X, W and their chi-square variates (see
+    orc_noise_update); returns tau per column."""
+    X, W = _f64(X), _f64(W)
+    D, K = W.shape
+    tau = np.zeros(D)
+    lib().orc_noise_update(K, D, _p(np.ascontiguousarray(cptr, np.int64)),
+                           _p(np.ascontiguousarray(cidx, np.int32)), _p(_f64(cval)), _p(X), _p(W),
+                           {"global": 1, "column": 2}[mode], float(a0), float(b0), _p(_f64(draw)),
+                           _p(tau))
+    return tau
+
+
+def noise_dofs(sub, noise: NoiseModel):
+    """Degrees of freedom of a subset's noise variates: 2 a0 + n_d per column, or 2 a0 + the
+    subset's entries."""
+    counts = np.diff(sub.cptr).astype(np.float64)
+    if noise.mode == "column":
+        return 2.0 * noise.a0 + counts
+    return np.array([2.0 * noise.a0 + counts.sum()])
 
 
 def mm_finalize(S1, S2, S):
@@ -378,8 +423,9 @@ def plan(N, D, row, col, val, I=1, J=1, order="decreasing", row_bounds=None, col
 # Draw buffer layout (shared convention; see the module docstring)
 # ---------------------------------------------------------------------------------------
 
-def stage_draw_layout(subsets, K):
-    """Offsets of one sweep's draws for a list of subsets processed together."""
+def stage_draw_layout(subsets, K, noise: NoiseModel = None):
+    """Offsets of one sweep's draws for a list of subsets processed together; with sampled
+    noise, each subset's noise variates follow the z's (one per column, or one)."""
     H = hyper_block_len(K)
     lay = {}
     off = 0
@@ -393,6 +439,10 @@ def stage_draw_layout(subsets, K):
     for s in subsets:
         lay[(s.sid, "zw")] = off
         off += s.d * K
+    if noise is not None and noise.mode != "fixed":
+        for s in subsets:
+            lay[(s.sid, "nz")] = off
+            off += s.d if noise.mode == "column" else 1
     lay["total"] = off
     return lay
 
@@ -421,11 +471,23 @@ def gen_subset(seed, t, sid, K, nu0, n, d):
     return hx, hw, zx, zw
 
 
-def gen_batch_draws(subsets, K, nu0, seed, t):
+def gen_noise(seed, t, sid, dof):
+    """The noise-precision chi-square variates of sweep t of subset sid (orc_gen_noise)."""
+    dof = _f64(dof)
+    out = np.zeros(len(dof))
+    _check(lib().orc_gen_noise(int(seed), int(t), int(sid), len(dof), _p(dof), _p(out)),
+           "gen_noise")
+    return out
+
+
+def gen_batch_draws(subsets, K, nu0, seed, t, noise: NoiseModel = None):
     """One sweep's generated draws for subsets processed together, in the shared layout."""
     parts = [gen_subset(seed, t, s.sid, K, nu0, s.n, s.d) for s in subsets]
+    tail = []
+    if noise is not None and noise.mode != "fixed":
+        tail = [gen_noise(seed, t, s.sid, noise_dofs(s, noise)) for s in subsets]
     return np.concatenate([np.concatenate([p[0], p[1]]) for p in parts]
-                          + [p[2].ravel() for p in parts] + [p[3].ravel() for p in parts])
+                          + [p[2].ravel() for p in parts] + [p[3].ravel() for p in parts] + tail)
 
 
 # ---------------------------------------------------------------------------------------
@@ -456,6 +518,7 @@ class ChainState:
     samples_W: list = None
     mixX: dict = None            # propagated mixture prior (GMM summary): pi, mu, Lam per row
     mixW: dict = None
+    tau_col: np.ndarray = None   # sampled noise precision per column (None: the fixed tau)
 
 
 def new_chain(X0, W0, K):
@@ -466,19 +529,27 @@ def new_chain(X0, W0, K):
                       S1W=np.zeros((D, K)), S2W=np.zeros((D, K, K)))
 
 
-def sweep_subset(sub: Subset, st: ChainState, K, tau, prior: NWPrior, hx, hw, zX, zW):
-    """One Gibbs sweep of one subset (order: Theta_X, Theta_W, X, W)."""
+def sweep_subset(sub: Subset, st: ChainState, K, tau, prior: NWPrior, hx, hw, zX, zW,
+                 noise: NoiseModel = None, noise_draw=None):
+    """One Gibbs sweep of one subset (order: Theta_X, Theta_W, X, W, then the sampled noise
+    precision when ``noise`` is given)."""
     hyper = np.concatenate([st.muX, st.LamX.ravel(), st.muW, st.LamW.ravel()])
     bad = ctypes.c_int64(-1)
     X, W = st.X, st.W
     hx, hw, zX, zW = _f64(hx).copy(), _f64(hw).copy(), _f64(zX).copy(), _f64(zW).copy()
+    nmode = 0 if noise is None else noise.code
+    if nmode and st.tau_col is None:
+        st.tau_col = np.full(sub.d, float(noise.tau0))
+    nd = None if not nmode else _f64(noise_draw).copy()
     st_ = lib().orc_sweep(K, sub.n, sub.d, _p(sub.rptr), _p(sub.ridx), _p(sub.rval),
                           _p(sub.cptr), _p(sub.cidx), _p(sub.cval), float(tau),
                           _p(prior.mu0), prior.beta0, prior.nu0, _p(prior.W0),
                           st.prior_x, _p(st.muX_row), _p(st.LamX_row),
                           st.prior_w, _p(st.muW_row), _p(st.LamW_row),
                           _p(hx), _p(hw), _p(zX), _p(zW),
-                          _p(X), _p(W), _p(hyper), ctypes.byref(bad))
+                          _p(X), _p(W), _p(hyper), nmode,
+                          float(noise.a0) if nmode else 0.0, float(noise.b0) if nmode else 0.0,
+                          _p(nd), _p(st.tau_col if nmode else None), ctypes.byref(bad))
     if st_:
         raise OracleError(f"sweep of subset {sub.sid}: status {st_}, row {bad.value}")
     KK = K * K
@@ -552,11 +623,12 @@ def mix_choose(mix, X):
 
 
 def run_stage(plan_: Plan, stage, chains: dict, K, tau, prior, draws_per_sweep, T, burnin=0,
-              thin=1):
+              thin=1, noise: NoiseModel = None):
     """T sweeps of every subset of one stage.  ``draws_per_sweep(t)`` returns the stage's
     draw buffer of sweep t (0-based)."""
     subs = plan_.stage_subsets(stage)
-    lay = stage_draw_layout(subs, K)
+    lay = stage_draw_layout(subs, K, noise)
+    sampled = noise is not None and noise.mode != "fixed"
     for t in range(T):
         dr = np.asarray(draws_per_sweep(t), np.float64)
         assert dr.shape == (lay["total"],), (dr.shape, lay["total"])
@@ -570,11 +642,16 @@ def run_stage(plan_: Plan, stage, chains: dict, K, tau, prior, draws_per_sweep, 
                 _, st.muX_row, st.LamX_row = mix_choose(st.mixX, st.X)
             if st.mixW is not None:
                 _, st.muW_row, st.LamW_row = mix_choose(st.mixW, st.W)
+            nz = None
+            if sampled:
+                m = s.d if noise.mode == "column" else 1
+                nz = dr[lay[(s.sid, "nz")]:lay[(s.sid, "nz")] + m]
             sweep_subset(s, st, K, tau, prior,
                          dr[lay[(s.sid, "hx")]:lay[(s.sid, "hx")] + H],
                          dr[lay[(s.sid, "hw")]:lay[(s.sid, "hw")] + H],
                          dr[lay[(s.sid, "zx")]:lay[(s.sid, "zx")] + s.n * K],
-                         dr[lay[(s.sid, "zw")]:lay[(s.sid, "zw")] + s.d * K])
+                         dr[lay[(s.sid, "zw")]:lay[(s.sid, "zw")] + s.d * K],
+                         noise if sampled else None, nz)
             if keep_sample(st.t, burnin, thin):
                 accumulate(st)
 

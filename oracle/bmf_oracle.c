@@ -250,9 +250,11 @@ int orc_nw_draw(int K, const double *mu_star, double beta_star, const double *Ws
 /* ------------------------------------------------------------------------------------- */
 
 /* For each row r of a CSR block (ptr/idx/val; idx indexes rows of the partner matrix P):
- *   Lambda_r = Lambda_p + tau sum_{d in Omega_r} p_d p_d^T,
- *   b_r      = Lambda_p mu_p + tau sum_{d in Omega_r} y_rd p_d,
- *   x_r      = Lambda_r^{-1} b_r + L_r^{-T} z_r,   Lambda_r = L_r L_r^T.
+ *   Lambda_r = Lambda_p + sum_{d in Omega_r} t_rd p_d p_d^T,
+ *   b_r      = Lambda_p mu_p + sum_{d in Omega_r} t_rd y_rd p_d,
+ *   x_r      = Lambda_r^{-1} b_r + L_r^{-T} z_r,   Lambda_r = L_r L_r^T,
+ * with the noise precision t_rd = tau_partner[d] (per-column precisions, row side: the
+ * partner is the column), tau_row[r] (column side: the row is the column), or tau (Eq. 3).
  * The prior (mu_p, Lambda_p) is shared by all rows (per_row_prior = 0: mu_p[K],
  * Lam_p[K*K]) or given per row (per_row_prior = 1: mu_p[R*K], Lam_p[R*K*K]).
  * If some Lambda_r is not positive definite, *bad_row = the first such r and ORC_NOT_PD is
@@ -261,8 +263,9 @@ int orc_nw_draw(int K, const double *mu_star, double beta_star, const double *Ws
  * arithmetic is the same as in the serial build, whose loop compiles as if the OpenMP lines
  * were absent. */
 int orc_update_rows(int K, int64_t R, const int64_t *ptr, const int32_t *idx, const double *val,
-                    const double *P, double tau, int per_row_prior, const double *mu_p,
-                    const double *Lam_p, const double *z, double *X_out, int64_t *bad_row)
+                    const double *P, double tau, const double *tau_partner, const double *tau_row,
+                    int per_row_prior, const double *mu_p, const double *Lam_p, const double *z,
+                    double *X_out, int64_t *bad_row)
 {
     size_t KK = (size_t)K * K;
 #ifdef _OPENMP
@@ -299,9 +302,12 @@ int orc_update_rows(int K, int64_t R, const int64_t *ptr, const int32_t *idx, co
         for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) {
             const double *p = P + (int64_t)idx[e] * K;
             double y = val[e];
+            /* noise precision of this observation: the partner column's (row side), the row's
+             * own column's (column side), or the shared one */
+            const double t = tau_partner ? tau_partner[idx[e]] : (tau_row ? tau_row[r] : tau);
             for (int i = 0; i < K; ++i) {
-                for (int j = 0; j < K; ++j) A[i * K + j] += tau * p[i] * p[j];
-                b[i] += tau * y * p[i];
+                for (int j = 0; j < K; ++j) A[i * K + j] += t * p[i] * p[j];
+                b[i] += t * y * p[i];
             }
         }
         if (chol_lower(K, A, L)) {
@@ -337,19 +343,57 @@ int orc_update_rows(int K, int64_t R, const int64_t *ptr, const int32_t *idx, co
 /* ------------------------------------------------------------------------------------- */
 
 /* Order within a sweep: (mu_X, Lambda_X) | X, then (mu_W, Lambda_W) | W, then every x_n | W,
- * then every w_d | X (the new X).  A factor whose prior is propagated from an earlier PP stage
+ * then every w_d | X (the new X), then (noise_mode != 0) the noise precisions | X, W
+ * (orc_noise_update; tau_col [D] in/out, noise_draw its chi-square variates; noise_mode 0
+ * keeps the fixed tau).  A factor whose prior is propagated from an earlier PP stage
  * (prior_x / prior_w = 1) keeps that per-row prior and draws no hyperparameters
  * (Section 5.1); otherwise its hyperparameters are drawn and shared by its rows.
  * hdraw_* = one hyperparameter draw block (chi2[K], nrm[K(K-1)/2], zmu[K]).
  * hyper_out receives mu_X[K], Lambda_X[K*K], mu_W[K], Lambda_W[K*K] (unchanged entries
  * for a propagated factor). */
+/* Noise precision update after a sweep's W half (Section 2.1: per-column precisions tau_d, or
+ * one precision, with conjugate Gamma(a0, b0) priors, shape-rate):
+ *   mode 1 (one precision):  tau | X, W ~ Gamma(a0 + |Omega| / 2, b0 + SSE / 2),
+ *   mode 2 (per column):     tau_d | X, W ~ Gamma(a0 + n_d / 2, b0 + SSE_d / 2),
+ * SSE_d = sum_{n in Omega_d} (y_nd - x_n^T w_d)^2 over the column's entries in order, SSE the
+ * sum of the SSE_d in column order.  A Gamma(a, b) variate is c / (2 b) with c ~ chi^2(2 a),
+ * the variate given in draw[] (one per column, or one).  tau[] (D entries) receives the new
+ * precisions (mode 1: the same value in every entry). */
+int orc_noise_update(int K, int64_t D, const int64_t *cptr, const int32_t *cidx,
+                     const double *cval, const double *X, const double *W, int mode, double a0,
+                     double b0, const double *draw, double *tau)
+{
+    (void)a0;
+    double total = 0.0;
+    for (int64_t d = 0; d < D; ++d) {
+        double sse = 0.0;
+        for (int64_t e = cptr[d]; e < cptr[d + 1]; ++e) {
+            const double *x = X + (int64_t)cidx[e] * K, *w = W + d * K;
+            double pr = 0.0;
+            for (int k = 0; k < K; ++k) pr += x[k] * w[k];
+            const double r = cval[e] - pr;
+            sse += r * r;
+        }
+        if (mode == 2)
+            tau[d] = draw[d] / (2.0 * b0 + sse);
+        else
+            total += sse;
+    }
+    if (mode == 1) {
+        const double t = draw[0] / (2.0 * b0 + total);
+        for (int64_t d = 0; d < D; ++d) tau[d] = t;
+    }
+    return ORC_OK;
+}
+
 int orc_sweep(int K, int64_t N, int64_t D, const int64_t *rptr, const int32_t *ridx,
               const double *rval, const int64_t *cptr, const int32_t *cidx, const double *cval,
               double tau, const double *mu0, double beta0, double nu0, const double *W0,
               int prior_x, const double *muX_row, const double *LamX_row, int prior_w,
               const double *muW_row, const double *LamW_row, const double *hdraw_x,
               const double *hdraw_w, const double *zX, const double *zW, double *X, double *W,
-              double *hyper_out, int64_t *bad_row)
+              double *hyper_out, int noise_mode, double a0, double b0, const double *noise_draw,
+              double *tau_col, int64_t *bad_row)
 {
     size_t KK = (size_t)K * K;
     int st;
@@ -370,11 +414,18 @@ int orc_sweep(int K, int64_t N, int64_t D, const int64_t *rptr, const int32_t *r
         if (!st) st = orc_nw_draw(K, mus, bs, Wsi, hdraw_w, hdraw_w + K, hdraw_w + K + nlow, muW, LamW);
         if (st) goto done;
     }
-    st = orc_update_rows(K, N, rptr, ridx, rval, W, tau, prior_x, prior_x ? muX_row : muX,
-                         prior_x ? LamX_row : LamX, zX, X, bad_row);
+    /* with sampled noise precisions the rows see their columns' current values (one shared
+     * value in mode 1 is stored per column too) */
+    st = orc_update_rows(K, N, rptr, ridx, rval, W, tau, noise_mode ? tau_col : NULL, NULL,
+                         prior_x, prior_x ? muX_row : muX, prior_x ? LamX_row : LamX, zX, X,
+                         bad_row);
     if (st) goto done;
-    st = orc_update_rows(K, D, cptr, cidx, cval, X, tau, prior_w, prior_w ? muW_row : muW,
-                         prior_w ? LamW_row : LamW, zW, W, bad_row);
+    st = orc_update_rows(K, D, cptr, cidx, cval, X, tau, NULL, noise_mode ? tau_col : NULL,
+                         prior_w, prior_w ? muW_row : muW, prior_w ? LamW_row : LamW, zW, W,
+                         bad_row);
+    if (st) goto done;
+    if (noise_mode)
+        st = orc_noise_update(K, D, cptr, cidx, cval, X, W, noise_mode, a0, b0, noise_draw, tau_col);
 done:
     free(w);
     return st;
@@ -671,6 +722,22 @@ static int stream_chi2(const uint64_t key[2], int64_t t, uint64_t tag, int k, do
         }
     }
     return ORC_ARG;
+}
+
+#define ORC_KIND_NOISE 4
+
+/* The noise-precision variates of sweep t of subset `sid` (Section 2.1 with sampled noise):
+ * m chi-square variates, variate k with dof[k], drawn like the hyperparameter chi-squares with
+ * tag (sid, W, kind 4) and counter (k, t, tag, attempt). */
+int orc_gen_noise(uint64_t seed, int64_t t, int32_t sid, int64_t m, const double *dof,
+                  double *out)
+{
+    const uint64_t key[2] = {seed, 0};
+    for (int64_t k = 0; k < m; ++k) {
+        int st = stream_chi2(key, t, orc_tag(sid, 1, ORC_KIND_NOISE), (int)k, dof[k], &out[k]);
+        if (st) return st;
+    }
+    return ORC_OK;
 }
 
 /* The draws of sweep t (1-based) of subset `sid` with n rows and d columns: the X and W

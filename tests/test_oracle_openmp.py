@@ -64,7 +64,7 @@ def test_openmp_build_reports_the_first_failing_row():
             X = np.zeros((R, K))
             bad = ctypes.c_int64(-1)
             st = oracle.lib().orc_update_rows(K, R, ptr.ctypes.data, idx.ctypes.data,
-                                              val.ctypes.data, P.ctypes.data, 1.0, 1,
+                                              val.ctypes.data, P.ctypes.data, 1.0, None, None, 1,
                                               mu.ctypes.data, Lam.ctypes.data, z.ctypes.data,
                                               X.ctypes.data, ctypes.byref(bad))
         finally:
