@@ -22,7 +22,11 @@
  *    [W*]^{-1} = W0^{-1} + N Sbar + (beta0 N / (beta0 + N)) (mu0 - xbar)(mu0 - xbar)^T,
  *    beta* = beta0 + N, nu* = nu0 + N, mu* = (beta0 mu0 + N xbar) / beta*;
  *    mu ~ N(mu*, (beta* Lambda)^{-1}).
- *  - Sweep order: (mu_X, Lambda_X) | X, (mu_W, Lambda_W) | W, then X | W, then W | X.
+ *  - Sweep order: (mu_X, Lambda_X) | X, (mu_W, Lambda_W) | W, then X | W, then W | X, then
+ *    (sampled noise) the noise precisions | X, W: tau_d ~ Gamma(a0 + n_d / 2, b0 + SSE_d / 2)
+ *    with SSE_d the squared residuals of column d's entries (one precision: the subset's
+ *    entries and summed SSE), drawn as c / (2 b0 + SSE) from a chi-square variate c.  The row
+ *    conditionals weight entry (n, d) by tau_d, the column conditional of w_d takes tau_d.
  *  - Ordering (Section 5.2): BMF_ORDER_DECREASING sorts rows (columns) by decreasing number
  *    of training observations, ties by original index; row_bounds/col_bounds are given in
  *    that order.  Subset (i, j) (0-based) has id s = i*J + j and stage 1 if i = j = 0,
@@ -65,7 +69,10 @@
  *      row (k = 1..K-1, l = 0..k-1), z_mu[K].  The block of a propagated factor is present and
  *      ignored.
  *    then z for every X row of the batch (subsets in id order, rows in local order), K each;
- *    then z for every W row of the batch, K each.
+ *    then z for every W row of the batch, K each;
+ *    then (sampled noise) for each subset in id order its noise chi-square variates: one per
+ *      column in local order with dof 2 a0 + the column's entries in the subset, or one with
+ *      dof 2 a0 + the subset's entries.
  *  Consecutive sweeps follow each other.
  *
  * Device generator (draws == NULL).  The library then computes the same buffer on the GPU from
@@ -81,7 +88,9 @@
  *      2000), attempt j on counter (k, t, tag, j) with the candidate normal from words 0, 1
  *      (cosine), the acceptance uniform u1 of word 2 and, when dof < 2, the factor
  *      U^(2 / dof) with U = u1 of word 3 (the shape-below-one boost).  64 rejections in a row
- *      fail the call with BMF_E_CUDA (probability below 1e-80).
+ *      fail the call with BMF_E_CUDA (probability below 1e-80);
+ *    kind 4, noise chi-square variate k of a subset (factor W): drawn the same way with the
+ *      dof of the layout above.
  *  The numbers depend only on (seed, subset, factor, t, position): batching a stage or
  *  splitting sweeps across calls does not change them.  bmf_generate_draws returns them.
  *
@@ -151,10 +160,16 @@ typedef struct {
                           own hyperparameter draws and its chain starts at the initial state
                           (the embarrassingly parallel MCMC baseline of Section 5.4, used by the
                           subset-posterior correlations of Section 5.6); 0: Algorithm 1 */
+    int32_t noise;     /* noise precision (Section 2.1): BMF_NOISE_FIXED tau (default);
+                          BMF_NOISE_GLOBAL one precision per chain, BMF_NOISE_COLUMN one per column
+                          (tau_d), sampled after each sweep's W half from Gamma(a0, b0) priors
+                          (shape, rate); every chain starts at tau */
+    double noise_a0, noise_b0; /* the Gamma prior of a sampled precision (both > 0) */
 } bmf_config;
 
 enum { BMF_MOMENTS_AUTO = 0, BMF_MOMENTS_MEAN = 1, BMF_MOMENTS_FULL = 2 };
 enum { BMF_SUMMARY_MM = 0, BMF_SUMMARY_DM = 1, BMF_SUMMARY_GMM = 2 };
+enum { BMF_NOISE_FIXED = 0, BMF_NOISE_GLOBAL = 1, BMF_NOISE_COLUMN = 2 };
 #define BMF_MAX_COMPONENTS 4
 
 typedef struct {
@@ -328,6 +343,10 @@ bmf_status bmf_get_posterior(bmf_ctx *ctx, int32_t subset, int32_t factor, doubl
  * replacing its hyperparameter draws (as a propagated prior does). */
 bmf_status bmf_set_prior(bmf_ctx *ctx, int32_t subset, int32_t factor, const double *mu,
                          const double *Lam);
+
+/* Current noise precision of each column of one subset's chain, tau [n_cols] host (the fixed
+ * tau when the noise is not sampled). */
+bmf_status bmf_get_noise(bmf_ctx *ctx, int32_t subset, double *tau);
 
 /* Grid geometry of one subset, and the reordering (new -> original index) of rows/columns. */
 bmf_status bmf_get_subset_info(const bmf_ctx *ctx, int32_t subset, bmf_subset_info *info);

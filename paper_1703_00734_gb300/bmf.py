@@ -16,6 +16,7 @@ PRECISION = {"fp64": BMF_FP64, "fp32": BMF_FP32, "bf16": BMF_BF16}
 ORDER = {"none": 0, "decreasing": 1}
 MOMENTS = {"auto": 0, "mean": 1, "full": 2}
 SUMMARY = {"mm": 0, "dm": 1, "gmm": 2}
+NOISE = {"fixed": 0, "global": 1, "column": 2}
 FACTOR_X, FACTOR_W = 0, 1
 STATUS = {0: "BMF_OK", 1: "BMF_E_ARG", 2: "BMF_E_SHAPE", 3: "BMF_E_NOT_PD",
           4: "BMF_E_NONFINITE", 5: "BMF_E_TIMEOUT", 6: "BMF_E_OOM", 7: "BMF_E_CUDA",
@@ -36,7 +37,9 @@ class Config(ctypes.Structure):
                 ("thin", ctypes.c_int32), ("seed", ctypes.c_uint64), ("eps_rel", ctypes.c_double),
                 ("moments", ctypes.c_int32), ("summary", ctypes.c_int32),
                 ("components", ctypes.c_int32), ("lam", ctypes.c_double),
-                ("max_samples", ctypes.c_int32), ("independent", ctypes.c_int32)]
+                ("max_samples", ctypes.c_int32), ("independent", ctypes.c_int32),
+                ("noise", ctypes.c_int32), ("noise_a0", ctypes.c_double),
+                ("noise_b0", ctypes.c_double)]
 
 
 class Draws(ctypes.Structure):
@@ -112,6 +115,8 @@ def load(path: str = LIB_PATH):
     L.bmf_get_posterior.restype = st
     L.bmf_set_prior.argtypes = [P, i32, i32, P, P]
     L.bmf_set_prior.restype = st
+    L.bmf_get_noise.argtypes = [P, i32, P]
+    L.bmf_get_noise.restype = st
     L.bmf_get_subset_info.argtypes = [P, i32, ctypes.POINTER(SubsetInfo)]
     L.bmf_get_subset_info.restype = st
     L.bmf_get_perm.argtypes = [P, P, P]
@@ -223,7 +228,8 @@ class BMF:
                  col_bounds=None, X0=None, W0=None, test=None, beta0=2.0, nu0=None, mu0=None,
                  W0_prior=None, order="decreasing", center=True, burnin=0, thin=1, seed=0,
                  eps_rel=1e-6, moments="auto", summary="mm", components=3, lam=0.0,
-                 max_samples=0, independent=False, stream=None):
+                 max_samples=0, independent=False, noise="fixed", noise_a0=1.0, noise_b0=1.0,
+                 stream=None):
         L = load()
         self.L = L
         self.N, self.D, self.K, self.I, self.J = int(N), int(D), int(K), int(I), int(J)
@@ -249,7 +255,8 @@ class BMF:
                      thin=int(thin), seed=int(seed), eps_rel=float(eps_rel),
                      moments=MOMENTS[moments], summary=SUMMARY[summary],
                      components=int(components), lam=float(lam), max_samples=int(max_samples),
-                     independent=int(bool(independent)))
+                     independent=int(bool(independent)), noise=NOISE[noise],
+                     noise_a0=float(noise_a0), noise_b0=float(noise_b0))
         self.precision = cfg.precision
         h = ctypes.c_void_p()
         st = L.bmf_init(ctypes.byref(h), ctypes.byref(cfg), N, D, len(row), _ptr(row), _ptr(col),
@@ -373,6 +380,13 @@ class BMF:
         nc = ctypes.c_int64()
         self._check(self.L.bmf_posterior_means(self.h, _ptr(Xm), _ptr(Wm), ctypes.byref(nc)))
         return Xm, Wm, nc.value
+
+    def get_noise(self, s):
+        """Current noise precision of each column of subset s (bmf_get_noise)."""
+        _, d = self._dims(s)
+        tau = np.zeros(d)
+        self._check(self.L.bmf_get_noise(self.h, s, _ptr(tau)))
+        return tau
 
     def subset_info(self, s):
         info = SubsetInfo()

@@ -186,6 +186,14 @@ struct bmf_ctx {
     // mixture store of propagated mixture priors per arena and which rows carry one
     int summary = BMF_SUMMARY_MM, ncomp = 3, max_samples = 0;
     bool independent = false;        // no propagation between stages (cfg.independent)
+    // sampled noise precision (cfg.noise): tau per W arena row, the row-side Gram's scaled copy
+    // of W and scaled values (the originals kept), per-row SSE, the batch's subset blocks
+    int noise = BMF_NOISE_FIXED;
+    double noise_a0 = 1.0, noise_b0 = 1.0;
+    double *tau_w = nullptr, *noise_sse = nullptr;
+    void *Ws = nullptr, *xval_orig = nullptr;
+    NoiseBlock *noise_blocks = nullptr;
+    std::vector<NoiseBlock> h_noise_blocks;
     double lambda = 0.0;
     double *ring[2] = {nullptr, nullptr};
     double *mix[2] = {nullptr, nullptr};
@@ -352,6 +360,8 @@ int64_t per_sweep_draws(const bmf_ctx *c, int sl0, int sl1)
 {
     int64_t n = 2 * (int64_t)(sl1 - sl0) * hyper_block_len(c->K);
     for (int sl = sl0; sl < sl1; ++sl) n += (geom_of_slot(c, sl).n() + geom_of_slot(c, sl).d()) * c->K;
+    // sampled noise precisions: one chi-square per column of each subset, or one per subset
+    for (int sl = sl0; sl < sl1 && c->noise; ++sl) n += c->noise == 2 ? geom_of_slot(c, sl).d() : 1;
     return n;
 }
 
@@ -580,10 +590,11 @@ bmf_status prepare_gen(bmf_ctx *c, int sl0, int sl1, int64_t per, int nbuf, int6
     std::vector<GenSubset> subs;
     for (int sl = sl0; sl < sl1; ++sl) {
         const SubsetGeom &g = geom_of_slot(c, sl);
-        subs.push_back(GenSubset{g.sid, g.n(), g.d()});
+        subs.push_back(GenSubset{g.sid, g.n(), g.d(), g.woff,
+                                 c->W.h_obs[g.woff + g.d()] - c->W.h_obs[g.woff]});
     }
     std::vector<GenSeg> segs;
-    *units = gen_segments(subs, c->K, c->nu0, segs);
+    *units = gen_segments(subs, c->K, c->nu0, c->noise, c->noise_a0, segs);
     *n_segs = (int)segs.size();
     if ((int64_t)segs.size() > c->gen_segs_cap) {
         if (c->gen_segs_d) cudaFree(c->gen_segs_d);
@@ -612,7 +623,7 @@ bmf_status prepare_gen(bmf_ctx *c, int sl0, int sl1, int64_t per, int nbuf, int6
 
 void enqueue_gen(bmf_ctx *c, int64_t units, int n_segs, int64_t t, double *out)
 {
-    GenParams gp{c->gen_segs_d, n_segs, units, c->seed, t, out, c->err_d};
+    GenParams gp{c->gen_segs_d, n_segs, units, c->seed, t, out, c->W.ptr, c->err_d};
     traced(c, c->st, K_GEN, 1, [&] { launch_gen(gp, c->st); });
 }
 
@@ -768,6 +779,25 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
     }
     const int64_t hyper_len = 2 * (int64_t)(sl1 - sl0) * HB;
     const int64_t zx_len = (rx1 - rx0) * K;
+    const int64_t zw_len = (rw1 - rw0) * K;
+    if (c->noise && n_sweeps > 0) {
+        // each subset's W rows and the offset of its noise variates in a sweep's draws
+        c->h_noise_blocks.clear();
+        int64_t off = hyper_len + zx_len + zw_len;
+        for (int sl = sl0; sl < sl1; ++sl) {
+            const SubsetGeom &g = geom_of_slot(c, sl);
+            c->h_noise_blocks.push_back(NoiseBlock{g.woff, g.woff + g.d(), off});
+            off += c->noise == BMF_NOISE_COLUMN ? g.d() : 1;
+        }
+        CUDA_TRY(c, cudaMemcpyAsync(c->noise_blocks, c->h_noise_blocks.data(),
+                                    c->h_noise_blocks.size() * sizeof(NoiseBlock),
+                                    cudaMemcpyHostToDevice, c->st));
+    }
+    // the row-side Gram's copies scaled by the current noise precisions
+    auto noise_scale = [&]() {
+        launch_noise_scale(K, c->prec, rw0, rw1, c->tau_w, c->W.F, c->Ws, c->ldg, c->X.h_obs[rx0],
+                           c->X.h_obs[rx1], c->X.idx, c->xval_orig, c->X.val, c->st);
+    };
     int64_t kept = c->ss[g0.sid].kept;
     // the DM / GMM summaries keep every retained sample: the ring must hold this call's
     bool any_mix[2] = {false, false};
@@ -841,6 +871,7 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
     }
     // from here the batch's statistics are in flux until the call completes
     for (int sl = sl0; sl < sl1 && n_sweeps > 0; ++sl) c->stats_ok[sl] = 0;
+    if (c->noise && n_sweeps > 0) noise_scale();
     for (int it = 0; it < n_sweeps; ++it) {
         const double *d = draws_of(it);
         const int64_t t = t_start + it + 1;
@@ -860,7 +891,7 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
             gp.n_items = i1 - i0;
             gp.idx = me.idx;
             gp.val = me.val;
-            gp.P = other.G;
+            gp.P = (c->noise && f == 0) ? c->Ws : other.G;
             gp.ldP = c->ldg;
             gp.part = c->part;
             gp.ld = c->ld_part;
@@ -940,7 +971,10 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
             cp.multi_idx = me.multi_idx;
             cp.rowsum = me.rowsum;
             cp.ld_sum = part_nv(K);
-            cp.tau = c->tau;
+            // sampled noise: the row side has the precisions in its Gram sums (scaled copies),
+            // the column side takes each column's own
+            cp.tau = c->noise ? 1.0 : c->tau;
+            cp.tau_row = (c->noise && f == 1) ? c->tau_w : nullptr;
             cp.row_hslot = me.hslot;
             cp.hyper = c->hyper;
             cp.prior_L = me.pL;
@@ -988,6 +1022,16 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
                 CUDA_TRY(c, cudaMemcpyAsync(c->ring[f] + (kept - 1) * me.R * K + r0 * K, me.F + r0 * K,
                                             (size_t)(r1 - r0) * K * sizeof(double),
                                             cudaMemcpyDeviceToDevice, c->st));
+            if (c->noise && f == 1) {
+                // the noise precisions given the new X and W, then the scaled copies of the
+                // next sweep's row-side Gram
+                launch_noise_sse(K, rw0, rw1, c->W.ptr, c->W.idx, c->W.val, c->prec, c->X.F, c->W.F,
+                                 c->noise_sse, c->st);
+                launch_noise_tau(c->noise, c->noise_b0, c->noise_blocks, sl1 - sl0, d, c->noise_sse,
+                                 c->tau_w, c->st);
+                noise_scale();
+                c->launches += 3;
+            }
             if (hyp[f] && it + 1 < n_sweeps) {
                 CUDA_TRY(c, cudaEventRecord(c->ev_fac[f], c->st));
                 CUDA_TRY(c, cudaStreamWaitEvent(c->st2, c->ev_fac[f], 0));
@@ -1015,7 +1059,7 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
         }
         if (tail_gen) {
             GenParams gp{c->gen_segs_d, gen_segs, gen_units, c->seed, t + 2,
-                         c->gen_d + (int64_t)(it & 1) * per, c->err_d};
+                         c->gen_d + (int64_t)(it & 1) * per, c->W.ptr, c->err_d};
             traced(c, c->st5, K_GEN, 1, [&] { launch_gen(gp, c->st5); });
             CUDA_TRY(c, cudaEventRecord(c->ev_gen[it & 1], c->st5));
         }
@@ -1325,6 +1369,13 @@ bmf_status restart_chains(bmf_ctx *c)
     for (int f = 0; f < 2; ++f)
         if (c->has_mix[f])
             CUDA_TRY(c, cudaMemsetAsync(c->has_mix[f], 0, (size_t)(f == 0 ? c->X.R : c->W.R), c->st));
+    if (c->tau_w && c->W.R) {
+        // every chain's noise precisions start at the configured tau
+        const std::vector<double> t0((size_t)c->W.R, c->tau);
+        CUDA_TRY(c, cudaMemcpyAsync(c->tau_w, t0.data(), t0.size() * sizeof(double),
+                                    cudaMemcpyHostToDevice, c->st));
+        CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    }
     c->ss.assign(S, SubState());
     c->stats_ok.assign(S, 0);
     for (int sl = 0; sl < S; ++sl) {
@@ -1423,6 +1474,16 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
     }
     c->summary = cfg->summary;
     c->independent = cfg->independent != 0;
+    if (cfg->noise < BMF_NOISE_FIXED || cfg->noise > BMF_NOISE_COLUMN ||
+        (cfg->noise != BMF_NOISE_FIXED && (!(cfg->noise_a0 > 0.0) || !(cfg->noise_b0 > 0.0) ||
+                                           !std::isfinite(cfg->noise_a0) || !std::isfinite(cfg->noise_b0)))) {
+        g_init_error = "noise must be FIXED, GLOBAL or COLUMN, with a0 > 0 and b0 > 0 when sampled";
+        delete c;
+        return BMF_E_ARG;
+    }
+    c->noise = cfg->noise;
+    c->noise_a0 = cfg->noise_a0;
+    c->noise_b0 = cfg->noise_b0;
     if (c->summary != BMF_SUMMARY_MM) {
         c->ncomp = c->summary == BMF_SUMMARY_DM ? 1 : (cfg->components > 0 ? cfg->components : 3);
         c->lambda = cfg->lambda;
@@ -1568,6 +1629,18 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
     c->col_rank_d = c->mem.alloc<int64_t>(D);
     c->pred_part = c->mem.alloc<double>(2 * c->rmse_blocks);
     c->pred_out = c->mem.alloc<double>(2);
+    if (c->noise != BMF_NOISE_FIXED) {
+        const size_t gb = c->prec == BMF_FP64 ? 8 : (c->prec == BMF_FP32 ? 4 : 2);
+        const size_t vb = c->prec == BMF_FP64 ? 8 : 4;
+        const int64_t nx = c->X.h_obs[c->P.RX];
+        c->tau_w = c->mem.alloc<double>(c->P.RW);
+        c->noise_sse = c->mem.alloc<double>(c->P.RW);
+        c->Ws = c->mem.alloc<char>((size_t)c->P.RW * c->ldg * gb);
+        c->xval_orig = c->mem.alloc<char>((size_t)nx * vb);
+        c->noise_blocks = c->mem.alloc<NoiseBlock>(S);
+        if (c->mem.ok && nx)
+            cudaMemcpy(c->xval_orig, c->X.val, (size_t)nx * vb, cudaMemcpyDeviceToDevice);
+    }
     if (c->summary != BMF_SUMMARY_MM)
         for (int f = 0; f < 2; ++f) {
             const int64_t R = f == 0 ? c->P.RX : c->P.RW;
@@ -1750,6 +1823,7 @@ bmf_status bmf_autotune(bmf_ctx *c, int32_t stage, int32_t subset, int32_t sweep
     }
     snap.add(c, c->hyper + (int64_t)2 * sl0 * hyper_slot_len(K),
              (size_t)2 * (sl1 - sl0) * hyper_slot_len(K) * sizeof(double));
+    if (c->tau_w) snap.add(c, c->tau_w + g0.woff, (size_t)(gl.woff + gl.d() - g0.woff) * sizeof(double));
     const int64_t tt0 = g0.test_off, tt1 = gl.test_off + gl.n_test;
     snap.add(c, c->ysum + tt0, (size_t)(tt1 - tt0) * sizeof(double));
     if (!snap.ok || !snap.mem.ok) return fail(c, BMF_E_OOM, "device allocation failed (tuner)");
@@ -2146,6 +2220,21 @@ bmf_status bmf_set_prior(bmf_ctx *c, int32_t subset, int32_t factor, const doubl
     bmf_status s = upload_hslots(c, g.slot);
     if (s) return s;
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    return BMF_OK;
+}
+
+bmf_status bmf_get_noise(bmf_ctx *c, int32_t subset, double *tau)
+{
+    if (!c || !tau) return BMF_E_ARG;
+    if (!valid_subset(c, subset)) return fail(c, BMF_E_ARG, "subset out of range");
+    const SubsetGeom &g = c->P.subs[subset];
+    if (!c->tau_w) {
+        for (int64_t k = 0; k < g.d(); ++k) tau[k] = c->tau;
+        return BMF_OK;
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    if (g.d())
+        CUDA_TRY(c, cudaMemcpy(tau, c->tau_w + g.woff, g.d() * sizeof(double), cudaMemcpyDeviceToHost));
     return BMF_OK;
 }
 

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kCondBlock) cond_kernel(CondParams a)
         }
         // 2. assemble with the prior: a shared hyperparameter slot or a per-row propagated prior
         const int h = a.row_hslot[r];
-        const double tau = a.tau;
+        const double tau = a.tau_row ? a.tau_row[r] : a.tau;
         if (h >= 0) {
             const double *hp = a.hyper + (int64_t)h * hyper_slot_len(K);
             for (int e = 0; e < NT; ++e) SM(e) = fma(tau, SM(e), hp[K + e]);
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kCondBlock) cond_kernel_k(CondParams a)
             for (int i = 0; i < K; ++i) B[i] = 0.0;
         }
         const int h = a.row_hslot[r];
-        const double tau = a.tau;
+        const double tau = a.tau_row ? a.tau_row[r] : a.tau;
         if (h >= 0) {
             const double *hp = a.hyper + (int64_t)h * hyper_slot_len(K);
 #pragma unroll

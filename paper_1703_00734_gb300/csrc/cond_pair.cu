@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kPairThreads) cond_pair_kernel(CondParams a)
     const bool active = q < blk.n;
     const int64_t r = blk.row0 + (active ? q : 0);
     const int64_t R = a.R;
-    const double tau = a.tau;
+    const double tau = a.tau_row ? a.tau_row[r] : a.tau;
     double M[S][K];
     double B[S], RI[S];
     // the moment sums of this row are fetched now and used after the draw (their global-memory

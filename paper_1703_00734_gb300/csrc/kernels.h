@@ -66,6 +66,7 @@ struct CondParams {
     const double *rowsum;        // FP64 sums of multi-item rows [slots x ld_sum]
     int ld_sum;
     double tau;
+    const double *tau_row;       // [R] per-row noise precision (sampled per column), or null
     const int32_t *row_hslot;    // [R] hyper slot of the row, or -1 for a per-row prior
     const double *hyper;         // [slots x hyper_slot_len(K)]
     const double *prior_L;       // per-row priors, SoA: [ntri(K)][R]
@@ -302,7 +303,8 @@ struct GenSeg {
     int64_t out;     // offset in the sweep's draw buffer
     uint64_t tag;    // subset id * 256 + factor * 16 + kind
     double dof0;
-    int32_t kind;
+    int32_t kind;    // 1 chi-square (dof0 - k), 2/3 normals, 4 chi-square (dof0 + entries)
+    int64_t row0;    // kind 4: W arena row of variate 0 (dof0 + its entries), or -1 (dof0)
 };
 struct GenParams {
     const GenSeg *segs;
@@ -311,16 +313,39 @@ struct GenParams {
     uint64_t seed;
     int64_t t;       // 1-based sweep number of the batch's chains
     double *out;
+    const int64_t *cnt_ptr;   // kind 4: W arena observation offsets (entries of a column)
     DevError *err;
 };
 struct GenSubset {
     int32_t sid;
     int64_t n, d;
+    int64_t woff, nnz;   // W arena row of the subset's first column, its training entries
 };
 void launch_gen(const GenParams &p, cudaStream_t st);
 // Segments of one sweep's buffer for the batch `subs` (id order); returns the thread count.
-int64_t gen_segments(const std::vector<GenSubset> &subs, int K, double nu0,
+// noise: 0 none, 1 one precision per subset, 2 one per column (kind-4 chi-squares after the z's,
+// dof 2 a0 + entries).
+int64_t gen_segments(const std::vector<GenSubset> &subs, int K, double nu0, int noise, double a0,
                      std::vector<GenSeg> &segs);
+
+// Sampled noise precision (Section 2.1).  noise_sse: per W arena row of [r0, r1), the sum of
+// squared residuals over the column's entries (FP64, in order) into sse.  noise_tau: the new
+// precisions from the chi-square variates (column mode: tau = c / (2 b0 + SSE) per row; global
+// mode: per subset block [b0_k, b1_k) one value from the block's summed SSE).  noise_scale:
+// the scaled copies the row-side Gram takes, Ws[r] = sqrt(tau[r]) W[r] for rows [r0, r1) and
+// val[q] = val_orig[q] sqrt(tau[idx[q]]) for entries [q0, q1).
+void launch_noise_sse(int K, int64_t r0, int64_t r1, const int64_t *ptr, const int32_t *idx,
+                      const void *val, int prec, const double *X, const double *W, double *sse,
+                      cudaStream_t st);
+struct NoiseBlock {
+    int64_t r0, r1;      // W arena rows of one subset
+    int64_t draw;        // offset of its variates in the sweep's draw buffer
+};
+void launch_noise_tau(int mode, double b0, const NoiseBlock *blocks, int n_blocks,
+                      const double *draws, const double *sse, double *tau, cudaStream_t st);
+void launch_noise_scale(int K, int prec, int64_t r0, int64_t r1, const double *tau,
+                        const double *W, void *Ws, int ldg, int64_t q0, int64_t q1,
+                        const int32_t *idx, const void *val_orig, void *val, cudaStream_t st);
 
 // Device helpers
 void launch_fill_gather(int K, int prec, int64_t R, const double *X, void *Xg, int ldg,

@@ -12,7 +12,10 @@
 //   kind 1 (chi-square, dof nu0 + n - k for diagonal entry k): 2 Gamma(dof / 2) by Marsaglia &
 //     Tsang (ACM TOMS 2000), attempt j on counter (k, t, tag, j): a candidate from the
 //     cosine normal of words (0, 1), the acceptance uniform from word 2 and, for shape < 1,
-//     the U^(1/a) boost from word 3.  64 rejections in a row set an error flag.
+//     the U^(1/a) boost from word 3.  64 rejections in a row set an error flag;
+//   kind 4 (chi-square of a sampled noise precision, factor W): variate k drawn the same way
+//     with dof 2 a0 + the entries of column k of the subset (one precision per column) or
+//     2 a0 + the subset's entries (one precision per subset, k = 0).
 // One thread per Philox call (normal streams) or per variate (chi-square).
 #include "common.cuh"
 #include "kernels.h"
@@ -60,8 +63,14 @@ __global__ void __launch_bounds__(256) gen_kernel(GenParams p)
     const GenSeg sg = p.segs[lo];
     const int64_t l = u - sg.unit0;
     double *out = p.out + sg.out;
-    if (sg.kind == 1) {
-        const double dof = sg.dof0 - (double)l;
+    if (sg.kind == 1 || sg.kind == 4) {
+        // kind 1: the Bartlett diagonal, dof0 - k; kind 4: the noise precision of a column
+        // (dof0 + its entries) or of a subset (dof0)
+        const double dof = sg.kind == 1 ? sg.dof0 - (double)l
+                                        : sg.dof0 + (sg.row0 >= 0
+                                                         ? (double)(p.cnt_ptr[sg.row0 + l + 1] -
+                                                                    p.cnt_ptr[sg.row0 + l])
+                                                         : 0.0);
         const double a = 0.5 * dof;
         const bool boost = a < 1.0;
         const double d = (boost ? a + 1.0 : a) - 1.0 / 3.0, c = 1.0 / sqrt(9.0 * d);
@@ -107,13 +116,13 @@ void launch_gen(const GenParams &p, cudaStream_t st)
 }
 
 // Host side: the segments of one sweep's draw buffer for a batch (layout of the public header).
-int64_t gen_segments(const std::vector<GenSubset> &subs, int K, double nu0,
+int64_t gen_segments(const std::vector<GenSubset> &subs, int K, double nu0, int noise, double a0,
                      std::vector<GenSeg> &segs)
 {
     segs.clear();
     const int64_t HN = (int64_t)K * (K - 1) / 2 + K;
     int64_t unit = 0, off = 0;
-    auto add = [&](int kind, int64_t count, uint64_t tag, double dof0) {
+    auto add = [&](int kind, int64_t count, uint64_t tag, double dof0, int64_t row0 = -1) {
         if (count <= 0) return;
         GenSeg s;
         s.unit0 = unit;
@@ -122,8 +131,9 @@ int64_t gen_segments(const std::vector<GenSubset> &subs, int K, double nu0,
         s.tag = tag;
         s.dof0 = dof0;
         s.kind = kind;
+        s.row0 = row0;
         segs.push_back(s);
-        unit += kind == 1 ? count : (count + 3) / 4;
+        unit += (kind == 1 || kind == 4) ? count : (count + 3) / 4;
         off += count;
     };
     auto tag = [](int sid, int f, int kind) {
@@ -137,6 +147,12 @@ int64_t gen_segments(const std::vector<GenSubset> &subs, int K, double nu0,
         }
     for (int f = 0; f < 2; ++f)
         for (const GenSubset &s : subs) add(3, (f == 0 ? s.n : s.d) * K, tag(s.sid, f, 3), 0.0);
+    // noise precisions: one chi-square per column (dof 2 a0 + the column's entries) or one per
+    // subset (dof 2 a0 + its entries), stream (subset, W, kind 4)
+    if (noise == 2)
+        for (const GenSubset &s : subs) add(4, s.d, tag(s.sid, 1, 4), 2.0 * a0, s.woff);
+    else if (noise == 1)
+        for (const GenSubset &s : subs) add(4, 1, tag(s.sid, 1, 4), 2.0 * a0 + (double)s.nnz, -1);
     return unit;
 }
 

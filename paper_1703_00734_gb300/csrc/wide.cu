@@ -522,6 +522,7 @@ __global__ void __launch_bounds__(32 * kWideWarps) cond_team_kernel(CondParams a
             const double *hp = h >= 0 ? a.hyper + (int64_t)h * hyper_slot_len(K) : nullptr;
             const AT *pp = static_cast<const AT *>(a.part) + (i0 - a.item0) * (int64_t)a.ld;
             const double *ps = mi >= 0 ? a.rowsum + (int64_t)mi * a.ld_sum : nullptr;
+            const double tau_r = a.tau_row ? a.tau_row[r] : tau;
             for (int e = tl; e < NT + K; e += T) {
                 const int src = e < NT ? e : a.part_rhs + (e - NT);
                 const double gsum = ps ? ps[src] : (i1 > i0 ? widen(pp[src]) : 0.0);
@@ -530,7 +531,7 @@ __global__ void __launch_bounds__(32 * kWideWarps) cond_team_kernel(CondParams a
                     prior = hp ? hp[K + e] : a.prior_L[(int64_t)e * R + r];
                 else
                     prior = hp ? hp[K + NT + (e - NT)] : a.prior_b[(int64_t)(e - NT) * R + r];
-                M[e] = fma(tau, gsum, prior);   // M[NT + i] is B[i]
+                M[e] = fma(tau_r, gsum, prior);   // M[NT + i] is B[i]
             }
         }
         __syncwarp(mask);
