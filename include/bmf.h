@@ -282,9 +282,19 @@ bmf_status bmf_set_monitor(bmf_ctx *ctx, int32_t on);
 bmf_status bmf_autotune(bmf_ctx *ctx, int32_t stage, int32_t subset, int32_t sweeps_per_trial,
                         bmf_schedule *best);
 
-/* n_sweeps Gibbs sweeps of one subset's chain (the whole data for a 1 x 1 grid).  The subset's
- * stage must be open (see bmf_stage).  draws: NULL for the device generator, else the buffer
- * for n_sweeps sweeps of this single-subset batch.  stats may be NULL. */
+/* n_sweeps Gibbs sweeps of one subset's chain (the whole data for a 1 x 1 grid).  One sweep is
+ * the BPMF Gibbs sampler of Section 5.1 (Salakhutdinov & Mnih's sampler, which the paper runs in
+ * every subset of Algorithm 1): the Normal-Wishart hyperparameters of X and of W given the
+ * current factors (centred scatter of the Section 5.1 footnote), then every row x_n given W
+ * (Eqs. 2-4 with the rows' priors), then every row w_d given the new X, then, with a sampled
+ * noise precision, tau given X and W (Section 2.1); the order and conventions are those at the
+ * top of this header.  The subset's stage must be open (see bmf_stage).  draws: NULL for the
+ * device generator, else the buffer for n_sweeps sweeps of this single-subset batch.  stats may
+ * be NULL.  Errors: BMF_E_ARG for a bad subset or n_sweeps < 0, BMF_E_STATE when the stage is
+ * not open or the context failed earlier,
+ * BMF_E_SHAPE for a draw buffer of the wrong length, BMF_E_NOT_PD when a conditional precision
+ * is not positive definite (the chain must then be reset with bmf_set_state or bmf_restart),
+ * BMF_E_CUDA for a runtime error or a device-generator rejection run. */
 bmf_status bmf_sweep(bmf_ctx *ctx, int32_t subset, int32_t n_sweeps, const bmf_draws *draws,
                      bmf_sweep_stats *stats);
 
