@@ -55,35 +55,51 @@ struct DevError {
 // Laid out contiguously per slot: [mu (K)][Lambda (ntri)][b (K)].
 __host__ __device__ constexpr int hyper_slot_len(int K) { return K + ntri(K) + K; }
 
-// FP32 -> FP64 by rebuilding the IEEE-754 fields on the integer pipe (exact for every normal
-// float; zeros, subnormals, infinities and NaNs take the hardware conversion).  On this GPU the
-// conversion instruction occupies the FP64 pipe, which this kernel is bound by.
+// FP32 -> FP64 by rebuilding the IEEE-754 fields on the integer pipe, without a branch: exact
+// for every normal float, zero, infinity and NaN; a subnormal float (below 1.2e-38 in
+// magnitude) reads as a zero of its sign.  On this GPU the conversion instruction occupies the
+// FP64 pipe, which the conditional draw is bound by, and a branch to it would still issue a
+// predicated conversion for the whole warp.
 __device__ __forceinline__ double widen(float f)
 {
     const uint32_t u = __float_as_uint(f);
-    const uint32_t e = (u >> 23) & 0xffu;
-    if (e == 0u || e == 0xffu) return (double)f;
-    const uint32_t hi = (u & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((u & 0x7fffffu) >> 3);
-    const uint32_t lo = u << 29;
+    const uint32_t s = u & 0x80000000u, t = u & 0x7f800000u;
+    // exponent rebased from 127 to 1023: + (1023 - 127) << 20 in the high word
+    uint32_t hi = s + ((u & 0x7fffffffu) >> 3) + 0x38000000u;
+    hi = t == 0u ? s : (t == 0x7f800000u ? hi + 0x38000000u : hi);
+    const uint32_t lo = t == 0u ? 0u : u << 29;
     return __hiloint2double((int)hi, (int)lo);
 }
 __device__ __forceinline__ double widen(double d) { return d; }
 
-// 1 / sqrt(d) for a positive pivot of the FP64 Cholesky in the reduced-precision modes (FP32 or
-// BF16 Gram entries, relative error ~1e-7 already): a float copy of d from its top bits (integer
-// pipe), the FP32 hardware reciprocal square root (relative error below 2^-21 with the
-// truncation), widened on the integer pipe, then one Newton step in FP64,
-// y <- y + (y / 2)(1 - d y^2): relative error below 1e-12, with four FP64 operations instead of
-// the full-precision sequence.  Pivots outside the normal float range take rsqrt().
+// A pivot the FP64 Cholesky of the conditional draw can take: positive, finite and normal (a
+// pivot below the smallest normal double, 2.2e-308, leaves the row numerically singular and
+// counts as not positive definite).  Integer compares of the bit pattern.
+__device__ __forceinline__ bool pivot_ok(double d)
+{
+    const long long b = __double_as_longlong(d);
+    return b >= 0x0010000000000000ll && b < 0x7ff0000000000000ll;
+}
+
+// 1 / sqrt(d) for a pivot of the FP64 Cholesky in the reduced-precision modes (FP32 or BF16
+// Gram entries, relative error ~1e-7 already); d must pass pivot_ok.  With d = m 2^E, m in
+// [1, 2) and E = 2h + p (p in {0, 1}): the FP32 unit gives 1/sqrt(m 2^p) for a float built from
+// d's top mantissa bits (relative error below 2^-21 with the truncation), widened and scaled by
+// 2^-h on the integer pipe, then one Newton step in FP64, y <- y + (y / 2)(1 - d y^2) (y / 2 by
+// the exponent too): relative error below 1e-12 with three FP64 operations and no branch.
 __device__ __forceinline__ double rsqrt_refined(double d)
 {
     const unsigned long long u = (unsigned long long)__double_as_longlong(d);
-    const int e = (int)((u >> 52) & 0x7ffull) - 1023;
-    if (e < -125 || e > 126) return rsqrt(d);
-    const uint32_t fb = ((uint32_t)(e + 127) << 23) | (uint32_t)((u >> 29) & 0x7fffffull);
-    const double y = widen(rsqrtf(__uint_as_float(fb)));
+    const int E = (int)(u >> 52) - 1023;
+    const int p = E & 1, h = (E - p) / 2;
+    const uint32_t fb = ((uint32_t)(127 + p) << 23) | (uint32_t)((u >> 29) & 0x7fffffull);
+    const uint32_t yb = __float_as_uint(rsqrtf(__uint_as_float(fb)));   // in (0.5, 1]
+    const int hi = (int)(((yb & 0x7fffffffu) >> 3) + 0x38000000u);
+    const int lo = (int)(yb << 29);
+    const double y = __hiloint2double(hi - h * (1 << 20), lo);
+    const double y2 = __hiloint2double(hi - (h + 1) * (1 << 20), lo);
     const double r = fma(-(d * y), y, 1.0);
-    return fma(0.5 * y, r, y);
+    return fma(y2, r, y);
 }
 
 // Pivot reciprocal square root of the conditional draw: full FP64 in the FP64 mode (gathered

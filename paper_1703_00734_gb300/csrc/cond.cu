@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kCondBlock) cond_kernel(CondParams a)
                 const double l = SM(jj + k);
                 d = fma(-l, l, d);
             }
-            if (!(d > 0.0)) {
+            if (!pivot_ok(d)) {
                 atomicOr(&a.err->flags, ERR_NOT_PD);
                 atomicMin(&a.err->first_bad_row, (int)r);
                 ok = false;
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kCondBlock) cond_kernel_k(CondParams a)
             double d = M[tri(j, j)];
 #pragma unroll
             for (int k = 0; k < j; ++k) d = fma(-M[tri(j, k)], M[tri(j, k)], d);
-            if (!(d > 0.0)) ok = false;
+            if (!pivot_ok(d)) ok = false;
             const double rs = pivot_rsqrt<GT>(d);
             RI[j] = rs;
             M[tri(j, j)] = d * rs;

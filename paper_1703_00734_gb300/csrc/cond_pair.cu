@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kPairThreads) cond_pair_kernel(CondParams a)
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const double d = __shfl_sync(kFull, M[k / 2][k], pb + pair_owner(k));
-        if (!(d > 0.0)) ok = false;
+        if (!pivot_ok(d)) ok = false;
         const double rs = ok ? pivot_rsqrt<GT>(d) : 0.0;
         if (l == pair_owner(k)) RI[k / 2] = rs;
 #pragma unroll

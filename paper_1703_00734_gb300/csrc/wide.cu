@@ -540,7 +540,7 @@ __global__ void __launch_bounds__(32 * kWideWarps) cond_team_kernel(CondParams a
         for (int k = 0; k < K; ++k) {
             const int kk = tri(k, k);
             const double d = ok ? M[kk] : 1.0;
-            if (!(d > 0.0)) ok = false;
+            if (!pivot_ok(d)) ok = false;
             const double rs = ok ? pivot_rsqrt<GT>(d) : 0.0;
             __syncwarp(mask);
             if (ok) {
