@@ -458,11 +458,16 @@ bmf_status setup_side(bmf_ctx *c, Side &s, int64_t R, const std::vector<int64_t>
     }
     s.h_item_ptr[R] = (int64_t)items.size();
     std::vector<int32_t> midx(R, -1);
-    for (int64_t r = 0; r < R; ++r)
-        if (s.h_item_ptr[r + 1] - s.h_item_ptr[r] > 1) {
+    const bool fuse = c->K >= kTeamMinK && c->K <= kNarrowMaxK;
+    for (int64_t r = 0; r < R; ++r) {
+        const int64_t ni = s.h_item_ptr[r + 1] - s.h_item_ptr[r];
+        if (ni > 1) {
             midx[r] = (int32_t)s.h_multi.size();
             s.h_multi.push_back((int32_t)r);
+        } else if (fuse && ni == 1 && items[s.h_item_ptr[r]].count <= kFuseMaxObs) {
+            midx[r] = kFusedRow;   // Gram sums formed by the conditional draw
         }
+    }
     const size_t nctr = s.h_multi.size() * (size_t)part_parts(c->K, c->prec);
     s.counters = c->mem.alloc<int>(nctr);
     s.multi_idx = c->mem.alloc<int32_t>(R);
@@ -489,7 +494,7 @@ bmf_status setup_side(bmf_ctx *c, Side &s, int64_t R, const std::vector<int64_t>
                     s.blk_task.push_back((int64_t)tasks.size());
                 }
                 const int64_t i0 = s.h_item_ptr[r], i1 = s.h_item_ptr[r + 1];
-                if (i1 == i0) continue;
+                if (i1 == i0 || midx[r] == kFusedRow) continue;
                 const int G = (i1 - i0 > 1) ? 32 : gram_group(items[i0].count);
                 if (G == 32) {
                     if (cur.n) tasks.push_back(cur), cur.n = 0;
@@ -990,6 +995,11 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
             cp.S2 = me.S2;
             cp.stats = c->stats;
             cp.err = c->err_d;
+            cp.obs_ptr = me.ptr;
+            cp.obs_idx = me.idx;
+            cp.obs_val = me.val;
+            cp.P = gp.P;
+            cp.ldP = gp.ldP;
             // lanes per row of the conditional: one thread per row below K = 13, a team above
             const int team = K >= kTeamMinK
                                  ? (c->sched.cond_lanes > 0 ? c->sched.cond_lanes : cond_team_size(K))

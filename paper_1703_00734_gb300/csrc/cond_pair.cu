@@ -11,7 +11,9 @@
 // holds row 2s + (l xor (s & 1)), so both lanes hold about half of the packed triangle.  Column
 // k of L reaches the other lane by shuffles.  Every entry sees the operations of the team kernel
 // in the same order (right-looking Cholesky, column-oriented solves), so the values are
-// bit-identical to it.
+// bit-identical to it.  A row with few observations (kFusedRow) forms its own G_n and r_n from
+// its list and the gathered partner rows, each entry accumulated in list order in the Gram
+// pass's accumulation type, instead of reading Gram partials.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -62,6 +64,48 @@ __device__ __forceinline__ void prefetch_wait() { asm volatile("cp.async.wait_al
 
 int cond_pair_smem(int K) { return kCondBlock * (ntri(K) + K) * (int)sizeof(double); }
 
+// The first K entries of a gathered partner row (16-byte aligned, at least the padded K
+// entries long) with vector loads, in the accumulation type of the Gram sums.
+template <int K, typename GT, typename AT>
+__device__ __forceinline__ void load_partner(const GT *__restrict__ p, AT (&w)[K])
+{
+    if constexpr (sizeof(GT) == 8) {
+        const double2 *q = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+        for (int c = 0; c < (K + 1) / 2; ++c) {
+            const double2 v = __ldg(q + c);
+            w[2 * c] = v.x;
+            if (2 * c + 1 < K) w[2 * c + 1] = v.y;
+        }
+    } else if constexpr (sizeof(GT) == 4) {
+        const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+        for (int c = 0; c < (K + 3) / 4; ++c) {
+            const float4 v = __ldg(q + c);
+            const float f[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (4 * c + u < K) w[4 * c + u] = f[u];
+        }
+    } else {
+        const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+        for (int c = 0; c < (K + 7) / 8; ++c) {
+            const uint4 v = __ldg(q + c);
+            const uint32_t u4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u4[u]));
+                if (8 * c + 2 * u < K) w[8 * c + 2 * u] = f.x;
+                if (8 * c + 2 * u + 1 < K) w[8 * c + 2 * u + 1] = f.y;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ float macc(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double macc(double a, double b, double c) { return fma(a, b, c); }
+
 template <int K, typename GT, typename AT>
 __global__ void __launch_bounds__(kPairThreads) cond_pair_kernel(CondParams a)
 {
@@ -106,26 +150,88 @@ __global__ void __launch_bounds__(kPairThreads) cond_pair_kernel(CondParams a)
         const double *hp = h >= 0 ? a.hyper + (int64_t)h * hyper_slot_len(K) : nullptr;
         const AT *pp = static_cast<const AT *>(a.part) + (i0 - a.item0) * (int64_t)a.ld;
         const double *ps = mi >= 0 ? a.rowsum + (int64_t)mi * a.ld_sum : nullptr;
+        if (mi == kFusedRow) {
+            // a row with few observations: its Gram sums from its own list, each entry
+            // accumulated in list order (the Gram pass skips the row)
+            AT G[S][K], Rv[S];
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const int i = pair_row(s, l);
-            if (i < K) {
+            for (int s = 0; s < S; ++s) {
 #pragma unroll
-                for (int j = 0; j < slot_len(K, s); ++j)
-                    if (j <= i) {
-                        const int e = tri(i, j);
-                        const double gsum = ps ? ps[e] : (i1 > i0 ? widen(pp[e]) : 0.0);
-                        const double prior = hp ? hp[K + e] : a.prior_L[(int64_t)e * R + r];
-                        M[s][j] = fma(tau, gsum, prior);
+                for (int j = 0; j < slot_len(K, s); ++j) G[s][j] = AT(0);
+                Rv[s] = AT(0);
+            }
+            const int64_t o0 = a.obs_ptr[r];
+            const int no = (int)(a.obs_ptr[r + 1] - o0);
+            // observations in groups of four: indices and values first, then the partner rows
+            constexpr int QG = 4;
+            for (int c0 = 0; c0 < no; c0 += QG) {
+                int32_t pid[QG];
+                AT yv[QG];
+#pragma unroll
+                for (int q2 = 0; q2 < QG; ++q2)
+                    if (c0 + q2 < no) {
+                        pid[q2] = a.obs_idx[o0 + c0 + q2];
+                        yv[q2] = static_cast<const AT *>(a.obs_val)[o0 + c0 + q2];
                     }
-                const int src = a.part_rhs + i;
-                const double gsum = ps ? ps[src] : (i1 > i0 ? widen(pp[src]) : 0.0);
-                const double prior = hp ? hp[K + NT + i] : a.prior_b[(int64_t)i * R + r];
-                B[s] = fma(tau, gsum, prior);
-            } else {
 #pragma unroll
-                for (int j = 0; j < slot_len(K, s); ++j) M[s][j] = 0.0;
-                B[s] = 0.0;
+                for (int q2 = 0; q2 < QG; ++q2)
+                    if (c0 + q2 < no) {
+                        AT pv[K];
+                        load_partner<K, GT, AT>(static_cast<const GT *>(a.P) + (int64_t)pid[q2] * a.ldP,
+                                                pv);
+#pragma unroll
+                        for (int s = 0; s < S; ++s) {
+                            const int i = pair_row(s, l);
+                            if (i < K) {
+#pragma unroll
+                                for (int j = 0; j < slot_len(K, s); ++j)
+                                    if (j <= i) G[s][j] = macc(pv[i], pv[j], G[s][j]);
+                                Rv[s] = macc(yv[q2], pv[i], Rv[s]);
+                            }
+                        }
+                    }
+            }
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const int i = pair_row(s, l);
+                if (i < K) {
+#pragma unroll
+                    for (int j = 0; j < slot_len(K, s); ++j)
+                        if (j <= i) {
+                            const int e = tri(i, j);
+                            const double prior = hp ? hp[K + e] : a.prior_L[(int64_t)e * R + r];
+                            M[s][j] = fma(tau, widen(G[s][j]), prior);
+                        }
+                    const double prior = hp ? hp[K + NT + i] : a.prior_b[(int64_t)i * R + r];
+                    B[s] = fma(tau, widen(Rv[s]), prior);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < slot_len(K, s); ++j) M[s][j] = 0.0;
+                    B[s] = 0.0;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const int i = pair_row(s, l);
+                if (i < K) {
+#pragma unroll
+                    for (int j = 0; j < slot_len(K, s); ++j)
+                        if (j <= i) {
+                            const int e = tri(i, j);
+                            const double gsum = ps ? ps[e] : (i1 > i0 ? widen(pp[e]) : 0.0);
+                            const double prior = hp ? hp[K + e] : a.prior_L[(int64_t)e * R + r];
+                            M[s][j] = fma(tau, gsum, prior);
+                        }
+                    const int src = a.part_rhs + i;
+                    const double gsum = ps ? ps[src] : (i1 > i0 ? widen(pp[src]) : 0.0);
+                    const double prior = hp ? hp[K + NT + i] : a.prior_b[(int64_t)i * R + r];
+                    B[s] = fma(tau, gsum, prior);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < slot_len(K, s); ++j) M[s][j] = 0.0;
+                    B[s] = 0.0;
+                }
             }
         }
     } else {

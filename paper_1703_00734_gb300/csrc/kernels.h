@@ -83,8 +83,23 @@ struct CondParams {
     double *stats;               // per-block sums of x and x x^T of the new state
                                  // [blocks x (K + ntri(K))], at slot blk0 + blockIdx.x
     DevError *err;
+    // rows marked kFusedRow in multi_idx form their own Gram sums from their observations (in
+    // list order), which the Gram pass skips: the row's list and the gathered partner copy
+    const int64_t *obs_ptr;      // [R+1]
+    const int32_t *obs_idx;      // partner arena rows
+    const void *obs_val;         // values (double for FP64, float otherwise)
+    const void *P;               // gathered partner copy [rows x ldP]
+    int ldP;
 };
 void launch_cond(int prec, const CondParams &a, int n_blocks, cudaStream_t st);
+// multi_idx of a row whose Gram sums the conditional draw forms itself: 13 <= K <= 16 (the
+// two-lane and team conditionals) and 1 to kFuseMaxObs observations in one work item.  Such a
+// row's partner rows are few and mostly cached, where its Gram partials would be a round trip
+// through memory.  Measured on the 100k x 20k, K = 16 PP workload (FP32, 3 x 60 sweeps with
+// resident draws): 237.1 ms without fusion, 225.6 / 215.2 / 209.7 / 204.9 / 205.4 / 226.3 ms
+// with at most 8 / 16 / 32 / 64 / 128 / 512 observations fused.
+constexpr int32_t kFusedRow = -2;
+constexpr int kFuseMaxObs = 64;
 constexpr int kCondBlock = 64;
 
 // Per-chunk sums for the hyperparameter step: for each chunk, sum x and the packed lower

@@ -483,54 +483,50 @@ static int row_block(size_t per_row)
     return (int)(fit >= (size_t)kRowBlock ? kRowBlock : (fit < 1 ? 1 : fit));
 }
 
-// In-place packed lower Cholesky; returns false if a pivot is not > 0.
-__device__ bool row_chol(double *P, int K, int rb)
+// In-place packed lower Cholesky (Crout order) with one reciprocal square root per pivot and no
+// division: L_jj in P, 1 / L_jj in ri.  Returns false if a pivot is not > 0.
+__device__ bool row_chol(double *P, double *ri, int K, int rb)
 {
     for (int j = 0; j < K; ++j) {
         const int jj = tri(j, 0);
         double d = RS(P, jj + j);
         for (int k = 0; k < j; ++k) d = fma(-RS(P, jj + k), RS(P, jj + k), d);
         if (!(d > 0.0)) return false;
-        const double sd = sqrt(d);
-        RS(P, jj + j) = sd;
+        const double rs = rsqrt(d);
+        RS(ri, j) = rs;
+        RS(P, jj + j) = d * rs;
         for (int i = j + 1; i < K; ++i) {
             const int ii = tri(i, 0);
             double s = RS(P, ii + j);
             for (int k = 0; k < j; ++k) s = fma(-RS(P, ii + k), RS(P, jj + k), s);
-            RS(P, ii + j) = s / sd;
+            RS(P, ii + j) = s * rs;
         }
     }
     return true;
 }
 
-// Solve (L L^T) x = b in place in vector v (interleaved), L packed in P.
-__device__ void row_solve(const double *P, double *v, int K, int rb)
+// Solve (L L^T) x = b in place in vector v (interleaved), L packed in P, 1 / L_ii in ri.
+__device__ void row_solve(const double *P, const double *ri, double *v, int K, int rb)
 {
     for (int i = 0; i < K; ++i) {
         const int ii = tri(i, 0);
         double s = RS(v, i);
         for (int k = 0; k < i; ++k) s = fma(-RS(P, ii + k), RS(v, k), s);
-        RS(v, i) = s / RS(P, ii + i);
+        RS(v, i) = s * RS(ri, i);
     }
     for (int i = K - 1; i >= 0; --i) {
         double s = RS(v, i);
         for (int k = i + 1; k < K; ++k) s = fma(-RS(P, tri(k, i)), RS(v, k), s);
-        RS(v, i) = s / RS(P, tri(i, i));
-    }
-}
-
-// Inverse of L L^T (L packed in P) into packed Out: column c from (L L^T) x = e_c, using tmp[K].
-__device__ void row_inverse(const double *P, double *Out, double *tmp, int K, int rb)
-{
-    for (int c = 0; c < K; ++c) {
-        for (int i = 0; i < K; ++i) RS(tmp, i) = (i == c) ? 1.0 : 0.0;
-        row_solve(P, tmp, K, rb);
-        for (int i = c; i < K; ++i) RS(Out, tri(i, c)) = RS(tmp, i);
+        RS(v, i) = s * RS(ri, i);
     }
 }
 
 // ------------------------------------------------------------------------------------------
 // Moment matching: mu = S1/S, Sigma = S2/S - mu mu^T, Lambda = Sigma^{-1}, b = Lambda mu.
+// Sigma = L L^T in place, then W = L^{-1} in place (columns left to right; W_ij =
+// -(1/L_ii) sum_{k=j}^{i-1} L_ik W_kj reads only entries of L right of column j and entries of W
+// already written), then Lambda = W^T W in place (rows top to bottom through a K-vector: row i
+// of Lambda needs only rows k >= i of W), then b.  K^3/2 multiply-adds and no division.
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kRowBlock) mm_kernel(MMParams a)
 {
@@ -539,24 +535,44 @@ __global__ void __launch_bounds__(kRowBlock) mm_kernel(MMParams a)
     const int64_t r = a.r0 + (int64_t)blockIdx.x * rb + t;
     if (r >= a.r1) return;
     const int K = a.K, NT = ntri(K);
-    double *Sg = sm + t, *Lm = Sg + NT * rb, *mu = Lm + NT * rb, *tmp = mu + K * rb;
-    for (int i = 0; i < K; ++i) RS(mu, i) = a.S1[(int64_t)i * a.R + r] / a.S;
-    for (int i = 0; i < K; ++i)
+    const int64_t R = a.R;
+    double *A = sm + t, *mu = A + NT * rb, *v = mu + K * rb;
+    const double inv = 1.0 / a.S;
+    for (int i = 0; i < K; ++i) RS(mu, i) = a.S1[(int64_t)i * R + r] * inv;
+    for (int i = 0; i < K; ++i) {
+        const double mi = RS(mu, i);
         for (int j = 0; j <= i; ++j)
-            RS(Sg, tri(i, j)) = a.S2[(int64_t)tri(i, j) * a.R + r] / a.S - RS(mu, i) * RS(mu, j);
-    if (!row_chol(Sg, K, rb)) {
+            RS(A, tri(i, j)) = fma(-mi, RS(mu, j), a.S2[(int64_t)tri(i, j) * R + r] * inv);
+    }
+    if (!row_chol(A, v, K, rb)) {
         atomicOr(&a.err->flags, ERR_NOT_PD);
         atomicMin(&a.err->first_bad_row, (int)r);
         return;
     }
-    row_inverse(Sg, Lm, tmp, K, rb);
+    for (int j = 0; j < K; ++j) {
+        RS(A, tri(j, j)) = RS(v, j);
+        for (int i = j + 1; i < K; ++i) {
+            const int ii = tri(i, 0);
+            double s = 0.0;
+            for (int k = j; k < i; ++k) s = fma(RS(A, ii + k), RS(A, tri(k, j)), s);
+            RS(A, ii + j) = -s * RS(v, i);
+        }
+    }
+    for (int i = 0; i < K; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double s = 0.0;
+            for (int k = i; k < K; ++k) s = fma(RS(A, tri(k, i)), RS(A, tri(k, j)), s);
+            RS(v, j) = s;
+        }
+        for (int j = 0; j <= i; ++j) RS(A, tri(i, j)) = RS(v, j);
+    }
     for (int i = 0; i < K; ++i) a.mu[r * K + i] = RS(mu, i);
-    for (int e = 0; e < NT; ++e) a.L[(int64_t)e * a.R + r] = RS(Lm, e);
+    for (int e = 0; e < NT; ++e) a.L[(int64_t)e * R + r] = RS(A, e);
     for (int i = 0; i < K; ++i) {
         double acc = 0.0;
         for (int k = 0; k < K; ++k)
-            acc = fma(RS(Lm, i >= k ? tri(i, k) : tri(k, i)), RS(mu, k), acc);
-        a.b[(int64_t)i * a.R + r] = acc;
+            acc = fma(RS(A, i >= k ? tri(i, k) : tri(k, i)), RS(mu, k), acc);
+        a.b[(int64_t)i * R + r] = acc;
     }
 }
 
@@ -564,7 +580,7 @@ void launch_mm(const MMParams &a, cudaStream_t st)
 {
     const int64_t n = a.r1 - a.r0;
     if (n <= 0) return;
-    const size_t per_row = (size_t)(2 * ntri(a.K) + 2 * a.K);
+    const size_t per_row = (size_t)(ntri(a.K) + 2 * a.K);
     const int rb = row_block(per_row);
     const size_t smem = per_row * rb * sizeof(double);
     if (smem > 48 * 1024)
@@ -614,10 +630,11 @@ void launch_propagate(const PropParams &a, cudaStream_t st)
 
 // Smallest eigenvalue of the symmetric matrix held packed-lower in A (interleaved; destroyed):
 // Householder reduction to tridiagonal form T = Q^T A Q (Golub & Van Loan, Algorithm 8.3.1),
-// then bisection on the Sturm count of T (the number of negative pivots of the LDL^T
-// factorisation of T - x I equals the number of eigenvalues below x; Golub & Van Loan,
-// Section 8.4.1).  Both steps are backward stable, so the result is the smallest eigenvalue to
-// O(u |A|).  v: K scratch slots, dg / of: the K diagonal and K - 1 off-diagonal entries of T.
+// then bisection on the Sturm count of T (the sign changes of the leading principal minors of
+// T - x I equal the number of eigenvalues below x; Golub & Van Loan, Section 8.4.1) to an
+// interval of 2^-50 |T|, the rounding level of the count.  The result is the smallest
+// eigenvalue to O(2^-50 |A|).  v: K scratch slots, dg / of: the K diagonal and K - 1
+// off-diagonal entries of T (of: their squares, scaled, after the reduction).
 __device__ double min_eig_tridiag(double *A, double *v, double *dg, double *of, int K, int rb)
 {
 #define AP(i, j) RS(A, (i) >= (j) ? tri(i, j) : tri(j, i))
@@ -662,32 +679,62 @@ __device__ double min_eig_tridiag(double *A, double *v, double *dg, double *of, 
     }
     RS(dg, K - 1) = AP(K - 1, K - 1);
 #undef AP
-    // Gershgorin interval of T
-    double lo = 0.0, hi = 0.0;
+    // Gershgorin interval of T; lambda_min <= min_i T_ii (the Rayleigh quotient of e_i) lowers
+    // its top end
+    double lo = 0.0, hi = 0.0, dmin = 0.0;
     for (int i = 0; i < K; ++i) {
         const double r = (i > 0 ? fabs(RS(of, i - 1)) : 0.0) + (i + 1 < K ? fabs(RS(of, i)) : 0.0);
         const double a = RS(dg, i) - r, b = RS(dg, i) + r;
         lo = i == 0 ? a : fmin(lo, a);
         hi = i == 0 ? b : fmax(hi, b);
+        dmin = i == 0 ? RS(dg, i) : fmin(dmin, RS(dg, i));
     }
-    const double tol = 0x1.0p-48 * fmax(fabs(lo), fabs(hi)) + 1e-300;
-    for (int it = 0; it < 200 && hi - lo > tol; ++it) {
+    const double nrm = fmax(fabs(lo), fabs(hi));
+    if (!(nrm > 0.0)) return 0.0;
+    // T / s with s the power of two at or above the norm bound (exact scaling): entries and the
+    // bisection interval within [-1, 1], so the Sturm sequence below neither overflows nor, short
+    // of K near-coincident eigenvalues, underflows
+    const int se = ilogb(nrm) + 1;
+    for (int i = 0; i < K; ++i) RS(dg, i) = scalbn(RS(dg, i), -se);
+    for (int i = 0; i + 1 < K; ++i) {
+        const double e = scalbn(RS(of, i), -se);
+        RS(of, i) = e * e;
+    }
+    lo = scalbn(lo, -se);
+    hi = fmin(scalbn(hi, -se), scalbn(dmin, -se) + 0x1.0p-44);
+    // bisection on the Sturm count: the number of sign changes of p_0 = 1, p_1 = d_0 - x,
+    // p_{i+1} = (d_i - x) p_i - e_{i-1}^2 p_{i-1} (the leading principal minors of T - x I, a zero
+    // taking the sign opposite to its predecessor) is the number of eigenvalues below x
+    // (Golub & Van Loan, Section 8.4.1); no division, signs read from the bit patterns
+    for (int it = 0; it < 100 && hi - lo > 0x1.0p-50; ++it) {
         const double x = 0.5 * (lo + hi);
-        int below = 0;
-        double q = RS(dg, 0) - x;
-        for (int i = 0;; ++i) {
-            if (fabs(q) < 1e-300) q = -1e-300;
-            below += q < 0.0;
-            if (i + 1 == K) break;
-            const double e = RS(of, i);
-            q = RS(dg, i + 1) - x - e * e / q;
+        double pm = 1.0, pc = RS(dg, 0) - x;
+        long long bc = __double_as_longlong(pc);
+        unsigned sc = (bc << 1) == 0 ? 1u : (unsigned)((unsigned long long)bc >> 63);
+        unsigned below = sc;
+        for (int i = 1; i < K; ++i) {
+            double pn = fma(RS(dg, i) - x, pc, -RS(of, i - 1) * pm);
+            const int em = max((int)((__double_as_longlong(pn) >> 52) & 0x7ff),
+                               (int)((__double_as_longlong(pc) >> 52) & 0x7ff));
+            if (em < 1023 - 600) {
+                // both terms below 2^-600: rescale them by the same power of two (exact)
+                const double f = scalbn(1.0, 1023 - max(em, 1));
+                pn *= f;
+                pc *= f;
+            }
+            const long long b2 = __double_as_longlong(pn);
+            const unsigned sn = (b2 << 1) == 0 ? (sc ^ 1u) : (unsigned)((unsigned long long)b2 >> 63);
+            below += sn ^ sc;
+            pm = pc;
+            pc = pn;
+            sc = sn;
         }
         if (below >= 1)
             hi = x;
         else
             lo = x;
     }
-    return 0.5 * (lo + hi);
+    return scalbn(0.5 * (lo + hi), se);
 }
 
 // Algorithm 2 in two passes.  Pass 1, one thread per (row n, submodel j >= 1): the difference
@@ -707,7 +754,7 @@ __device__ bool row_pd_test(double *P, int K, int rb)
         double d = RS(P, jj + j);
         for (int k = 0; k < j; ++k) d = fma(-RS(P, jj + k), RS(P, jj + k), d);
         if (!(d > 0.0)) return false;
-        const double r = 1.0 / sqrt(d);
+        const double r = rsqrt(d);
         for (int i = j + 1; i < K; ++i) {
             const int ii = tri(i, 0);
             double s = RS(P, ii + j);
@@ -751,7 +798,7 @@ __global__ void __launch_bounds__(kRowBlock) aggregate_corr_kernel(AggParams a, 
     if ((t & 31) == __ffs(am) - 1 && votes) atomicAdd(a.n_corrected, (unsigned long long)__popc(votes));
 }
 
-static inline size_t agg_slots(int K) { return (size_t)2 * ntri(K) + K; }
+static inline size_t agg_slots(int K) { return (size_t)2 * ntri(K) + 2 * K; }
 
 __global__ void __launch_bounds__(kRowBlock) aggregate_kernel(AggParams a)
 {
@@ -760,7 +807,7 @@ __global__ void __launch_bounds__(kRowBlock) aggregate_kernel(AggParams a)
     const int64_t n = (int64_t)blockIdx.x * rb + t;
     if (n >= a.n_rows) return;
     const int K = a.K, NT = ntri(K), J = a.J;
-    double *Ls = sm + t, *Dm = Ls + NT * rb, *h = Dm + NT * rb;
+    double *Ls = sm + t, *Dm = Ls + NT * rb, *h = Dm + NT * rb, *ri = h + K * rb;
     const int64_t r1 = a.sub_base[0] + n;
     const double c0 = 2.0 - (double)J;
     for (int e = 0; e < NT; ++e) RS(Ls, e) = c0 * a.L[(int64_t)e * a.R + r1];
@@ -793,12 +840,12 @@ __global__ void __launch_bounds__(kRowBlock) aggregate_kernel(AggParams a)
             RS(h, i) += s;
         }
     }
-    if (!row_chol(Ls, K, rb)) {
+    if (!row_chol(Ls, ri, K, rb)) {
         atomicOr(&a.err->flags, ERR_NOT_PD);
         atomicMin(&a.err->first_bad_row, (int)n);
         return;
     }
-    row_solve(Ls, h, K, rb);
+    row_solve(Ls, ri, h, K, rb);
     for (int i = 0; i < K; ++i) a.out[n * K + i] = RS(h, i);
 }
 

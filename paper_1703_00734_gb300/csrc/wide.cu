@@ -470,6 +470,15 @@ __device__ __forceinline__ float to_gather_w<float>(double x) { return (float)x;
 template <>
 __device__ __forceinline__ __nv_bfloat16 to_gather_w<__nv_bfloat16>(double x) { return __double2bfloat16(x); }
 
+template <typename AT>
+__device__ __forceinline__ AT to_acc(double x) { return x; }
+template <typename AT>
+__device__ __forceinline__ AT to_acc(float x) { return x; }
+template <typename AT>
+__device__ __forceinline__ AT to_acc(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ float acc_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double acc_fma(double a, double b, double c) { return fma(a, b, c); }
+
 __device__ __forceinline__ void decode_packed(int e, int &i, int &j)
 {
     i = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
@@ -525,7 +534,26 @@ __global__ void __launch_bounds__(32 * kWideWarps) cond_team_kernel(CondParams a
             const double tau_r = a.tau_row ? a.tau_row[r] : tau;
             for (int e = tl; e < NT + K; e += T) {
                 const int src = e < NT ? e : a.part_rhs + (e - NT);
-                const double gsum = ps ? ps[src] : (i1 > i0 ? widen(pp[src]) : 0.0);
+                double gsum;
+                if (mi == kFusedRow) {
+                    // a row with few observations: the entry from its list, in list order (the
+                    // same operations as the two-lane conditional)
+                    int ii, jj;
+                    if (e < NT)
+                        decode_packed(e, ii, jj);
+                    else
+                        ii = e - NT, jj = -1;
+                    AT acc = AT(0);
+                    for (int64_t o = a.obs_ptr[r]; o < a.obs_ptr[r + 1]; ++o) {
+                        const GT *pr = static_cast<const GT *>(a.P) + (int64_t)a.obs_idx[o] * a.ldP;
+                        const AT pi = to_acc<AT>(pr[ii]);
+                        acc = jj >= 0 ? acc_fma(pi, to_acc<AT>(pr[jj]), acc)
+                                      : acc_fma(static_cast<const AT *>(a.obs_val)[o], pi, acc);
+                    }
+                    gsum = widen(acc);
+                } else {
+                    gsum = ps ? ps[src] : (i1 > i0 ? widen(pp[src]) : 0.0);
+                }
                 double prior;
                 if (e < NT)
                     prior = hp ? hp[K + e] : a.prior_L[(int64_t)e * R + r];
