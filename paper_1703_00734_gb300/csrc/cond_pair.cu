@@ -120,6 +120,12 @@ __global__ void __launch_bounds__(kPairThreads) cond_pair_kernel(CondParams a)
     const int64_t r = blk.row0 + (active ? q : 0);
     const int64_t R = a.R;
     const double tau = a.tau_row ? a.tau_row[r] : a.tau;
+    // the row's indices first, all in flight together (the observation range too, which a row
+    // forming its own Gram sums needs before its first gather)
+    const int64_t i0 = a.item_ptr[r], i1 = a.item_ptr[r + 1];
+    const int mi = a.multi_idx[r];
+    const int h = a.row_hslot[r];
+    const int64_t o0 = a.obs_ptr[r], o1 = a.obs_ptr[r + 1];
     double M[S][K];
     double B[S], RI[S];
     // the moment sums of this row are fetched now and used after the draw (their global-memory
@@ -144,9 +150,6 @@ __global__ void __launch_bounds__(kPairThreads) cond_pair_kernel(CondParams a)
     // 1-2. G, r and the prior (inactive pairs carry an identity, so their arithmetic stays
     //      finite; they write nothing)
     if (active) {
-        const int64_t i0 = a.item_ptr[r], i1 = a.item_ptr[r + 1];
-        const int mi = a.multi_idx[r];
-        const int h = a.row_hslot[r];
         const double *hp = h >= 0 ? a.hyper + (int64_t)h * hyper_slot_len(K) : nullptr;
         const AT *pp = static_cast<const AT *>(a.part) + (i0 - a.item0) * (int64_t)a.ld;
         const double *ps = mi >= 0 ? a.rowsum + (int64_t)mi * a.ld_sum : nullptr;
@@ -160,8 +163,7 @@ __global__ void __launch_bounds__(kPairThreads) cond_pair_kernel(CondParams a)
                 for (int j = 0; j < slot_len(K, s); ++j) G[s][j] = AT(0);
                 Rv[s] = AT(0);
             }
-            const int64_t o0 = a.obs_ptr[r];
-            const int no = (int)(a.obs_ptr[r + 1] - o0);
+            const int no = (int)(o1 - o0);
             // observations in groups of four: indices and values first, then the partner rows
             constexpr int QG = 4;
             for (int c0 = 0; c0 < no; c0 += QG) {
