@@ -254,8 +254,10 @@ typedef struct {
                           once (kept and updated in place across calls of the same shape); 0: launch
                           directly.  Ignored while profiling is on. */
     int32_t cond_lanes; /* K >= 13: lanes that factor one row in the FP64 conditional draw (2, 4,
-                          8, 16 or 32; every choice gives bit-identical values; 2 at K <= 16
-                          keeps the row's matrix in registers); 0: a default from K (2 up to
+                          8, 16 or 32; every choice gives bit-identical values; 2, only for
+                          K <= 16, keeps the row's matrix in registers; a team of 4 to 32 lanes
+                          keeps it in shared memory, and bmf_set_schedule rejects a team whose
+                          rows do not fit there, BMF_E_ARG); 0: a default from K (2 up to
                           K = 16, 16 up to 48, 32 above).  Ignored for K <= 12 (one thread per
                           row). */
 } bmf_schedule;
@@ -273,7 +275,8 @@ bmf_status bmf_set_monitor(bmf_ctx *ctx, int32_t on);
 
 /* Schedule tuner: on the batch of `stage` (subset < 0) or of one subset, times candidate
  * schedules -- Gram grid 2/4/8 blocks per SM, then 1-4 row chunks for each half, then the split
- * weight, then (K >= 13) 2/4/8 lanes per row of the conditional, then the CUDA-graph launch --
+ * weight, then (K >= 13) 2/4/8 (K <= 16) or 8/16/32 lanes per row of the conditional, those that
+ * fit, then the CUDA-graph launch --
  * with one untimed and sweeps_per_trial timed sweeps each (device generator), and installs the
  * fastest.  Every trial starts from the same state and the
  * chains are restored afterwards (state, gathered copies, moment sums, hyperparameters, running

@@ -1743,6 +1743,10 @@ bmf_status bmf_set_schedule(bmf_ctx *c, const bmf_schedule *s)
     if (s->cond_lanes != 0 && s->cond_lanes != 2 && s->cond_lanes != 4 && s->cond_lanes != 8 &&
         s->cond_lanes != 16 && s->cond_lanes != 32)
         return fail(c, BMF_E_ARG, "cond_lanes must be 0, 2, 4, 8, 16 or 32");
+    if (s->cond_lanes != 0 && c->K >= kTeamMinK && !cond_lanes_valid(c->K, s->cond_lanes))
+        return fail(c, BMF_E_ARG, "cond_lanes " + std::to_string(s->cond_lanes) +
+                                      " cannot factor rows of K = " + std::to_string(c->K) +
+                                      " (two lanes: 13 <= K <= 16; teams must fit in shared memory)");
     c->sched = *s;
     return BMF_OK;
 }
@@ -1901,8 +1905,10 @@ bmf_status bmf_autotune(bmf_ctx *c, int32_t stage, int32_t subset, int32_t sweep
     if (!s && K >= kTeamMinK) {
         // lanes per row of the conditional (every choice gives bit-identical values)
         cands.clear();
-        for (int lanes : {2, 4, 8})
-            if (lanes != (best.cond_lanes > 0 ? best.cond_lanes : cond_team_size(K))) {
+        const std::vector<int> tries = K <= 16 ? std::vector<int>{2, 4, 8} : std::vector<int>{8, 16, 32};
+        for (int lanes : tries)
+            if (cond_lanes_valid(K, lanes) &&
+                lanes != (best.cond_lanes > 0 ? best.cond_lanes : cond_team_size(K))) {
                 bmf_schedule sc = best;
                 sc.cond_lanes = lanes;
                 cands.push_back(sc);

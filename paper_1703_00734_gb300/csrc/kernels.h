@@ -272,6 +272,9 @@ void launch_gram_wide(int K, int prec, const GramParams &a, int grid, cudaStream
 // Conditional draw with a team of `team` lanes (4, 8, 16 or 32) per row (wide.cu).
 void launch_cond_team(int prec, const CondParams &a, int n_blocks, int team, cudaStream_t st);
 int cond_team_size(int K);
+// Whether the conditional can factor a row of dimension K with `lanes` lanes: two lanes (the
+// register-resident kernel) for 13 <= K <= 16, else a team whose rows fit in shared memory.
+bool cond_lanes_valid(int K, int lanes);
 // The same draw for 13 <= K <= 16 with two lanes per row and the row's matrix in registers
 // (cond_pair.cu; bit-identical to the team kernel).  False for other K (nothing launched).
 bool launch_cond_pair(int prec, const CondParams &a, int n_blocks, cudaStream_t st);

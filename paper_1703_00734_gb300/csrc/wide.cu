@@ -505,6 +505,14 @@ __host__ __device__ constexpr int team_stride(int K, int T)
     return (ntri(K) + (team_colcopy(T) ? 3 : 2) * K + 7) / 8 * 8 + (T % 16 == 0 ? 4 : T % 16);
 }
 
+bool cond_lanes_valid(int K, int lanes)
+{
+    if (lanes == 2 && K >= 13 && K <= 16) return true;
+    if (lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32) return false;
+    const size_t smem = (size_t)(32 * kWideWarps / lanes) * team_stride(K, lanes) * sizeof(double);
+    return smem <= 227 * 1024;
+}
+
 template <typename GT, typename AT, int T>
 __global__ void __launch_bounds__(32 * kWideWarps) cond_team_kernel(CondParams a)
 {

@@ -75,6 +75,26 @@ def test_schedule_argument_errors():
     m.close()
 
 
+def test_lanes_that_do_not_fit_are_rejected_and_the_tuner_skips_them():
+    """Two lanes per row exist only for 13 <= K <= 16 and a team's rows must fit in shared
+    memory: at K = 64 a team of 8 lanes would need 291 KB per block."""
+    from paper_1703_00734_gb300 import bmf
+    for K, bad, good in [(32, 2, 16), (64, 8, 32)]:
+        d = synth.make_workload(None, N=300, D=200, M=6000, pattern="zipf", K=min(K, 10),
+                                sigma=0.5, tau=4.0, seed=K, s_row=1.2, s_col=1.2)
+        m = bmf.BMF(d["N"], d["D"], d["row"], d["col"], d["val"], K, d["tau"], "bf16",
+                    X0=None, W0=None, seed=2, burnin=1)
+        with pytest.raises(bmf.BmfError) as e:
+            m.set_schedule(1, 1, 4, 0.0, 0, bad)
+        assert e.value.status == 1
+        m.set_schedule(1, 1, 4, 0.0, 0, good)
+        m.sweep(0, 1, None)
+        sc = m.autotune(1, -1, 1)
+        assert sc["cond_lanes"] in (0, 8, 16, 32)
+        m.sweep(0, 1, None)
+        m.close()
+
+
 @pytest.mark.parametrize("I,J,stage", [(1, 1, 1), (2, 3, 2)])
 def test_autotune_restores_the_chain(I, J, stage):
     from paper_1703_00734_gb300 import bmf
