@@ -37,6 +37,27 @@ def test_single_transition_fp64(K):
     pr.compare_subset(0)
 
 
+@pytest.mark.parametrize("K,prec,rel", [(16, "fp64", 1e-9), (13, "fp64", 1e-9), (16, "fp32", 1e-3)])
+def test_rows_forming_their_own_gram_sums(K, prec, rel):
+    """13 <= K <= 16: rows with at most 64 observations form G_n, r_n inside the conditional
+    draw, longer rows come from the Gram pass; both kinds against the oracle, over sweeps that
+    keep moments (FP32: one transition, within the error of its FP32 Gram sums)."""
+    d = small(N=600, D=250, M=30_000, K=K, pattern="zipf", seed=40 + K)
+    for side, n in (("row", d["N"]), ("col", d["D"])):
+        counts = np.bincount(d[side], minlength=n)
+        assert (counts > 64).any() and ((counts > 0) & (counts <= 64)).any(), side
+    pr = Pair(d, K, precision=prec, burnin=1, moments="full")
+    pr.run_stage(1, 1)
+    pr.compare_subset(0, rel=rel)
+    if prec != "fp64":
+        return
+    pr.run_stage(1, 3, t0=1)
+    pr.compare_subset(0, rel=10 * rel)
+    S1, S2, kept = pr.m.get_moments(0, 0)
+    assert kept == 3
+    assert_rows_close(S2.reshape(len(S2), -1), pr.chains[0].S2X.reshape(len(S2), -1), 10 * rel, "S2X")
+
+
 def test_multi_sweep_fp64_with_moments():
     d = small(K=4, N=257, D=129, M=5000, seed=7)
     pr = Pair(d, 4, burnin=2, thin=2, moments="full")
