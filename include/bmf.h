@@ -252,7 +252,9 @@ typedef struct {
     double row_weight;
     int32_t graph;     /* 1: capture each call's launch sequence into one CUDA graph and launch it
                           once (kept and updated in place across calls of the same shape); 0: launch
-                          directly.  Ignored while profiling is on. */
+                          directly.  Ignored while profiling is on, and for a call given host
+                          draws: their copy then runs in groups of sweeps beside the sweeps,
+                          each sweep waiting only for its own group. */
     int32_t cond_lanes; /* K >= 13: lanes that factor one row in the FP64 conditional draw (2, 4,
                           8, 16 or 32; every choice gives bit-identical values; 2, only for
                           K <= 16, keeps the row's matrix in registers; a team of 4 to 32 lanes

@@ -85,6 +85,7 @@ struct SubState {
 }  // namespace
 
 constexpr int kMaxChunks = BMF_MAX_CHUNKS;
+constexpr int kCopyGroups = 16;   // copy groups of a host draw buffer (events per call)
 
 struct bmf_ctx {
     ~bmf_ctx()
@@ -95,7 +96,9 @@ struct bmf_ctx {
                 cudaStreamDestroy(x);
             }
         for (cudaEvent_t e : {ev_fork, ev_fac[0], ev_fac[1], ev_hyp[0], ev_hyp[1], ev_cdone, ev_tail,
-                              ev_tail2, ev_rmse, ev_gen[0], ev_gen[1], ev_copy, ev_copy_h})
+                              ev_tail2, ev_rmse, ev_gen[0], ev_gen[1]})
+            if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : ev_copyq)
             if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : ev_chunk)
             if (e) cudaEventDestroy(e);
@@ -119,8 +122,9 @@ struct bmf_ctx {
     cudaEvent_t ev_fork = nullptr, ev_fac[2] = {nullptr, nullptr}, ev_hyp[2] = {nullptr, nullptr};
     cudaEvent_t ev_chunk[kMaxChunks] = {}, ev_cdone = nullptr;
     cudaEvent_t ev_tail = nullptr, ev_tail2 = nullptr, ev_rmse = nullptr, ev_gen[2] = {nullptr, nullptr};
-    cudaEvent_t ev_copy = nullptr;   // host draw buffer on the device (copied on the generator stream)
-    cudaEvent_t ev_copy_h = nullptr; // its first part: the hyperparameter blocks of the first sweep
+    // a host draw buffer is copied on the generator stream in groups of sweeps, an event after
+    // each group, so that sweep t waits only for its own group
+    cudaEvent_t ev_copyq[kCopyGroups] = {};
     struct Readback {
         DevError err;
         double rmse[2];
@@ -548,9 +552,11 @@ bmf_status setup_side(bmf_ctx *c, Side &s, int64_t R, const std::vector<int64_t>
     return BMF_OK;
 }
 
-// Draw buffer of a call on the device.
+// Draw buffer of a call on the device.  A host buffer is copied on copy_st; with `groups`
+// (offsets in doubles, ascending, from 0 to need) in pieces, event evs[q] recorded after piece q.
 bmf_status stage_draws(bmf_ctx *c, const bmf_draws *d, int64_t need, const double **out,
-                       cudaStream_t copy_st, int64_t first = 0, cudaEvent_t first_ev = nullptr)
+                       cudaStream_t copy_st, const std::vector<int64_t> *groups = nullptr,
+                       cudaEvent_t *evs = nullptr)
 {
     if (!d) {
         *out = nullptr;   // the device generator fills the sweep buffers
@@ -571,18 +577,18 @@ bmf_status stage_draws(bmf_ctx *c, const bmf_draws *d, int64_t need, const doubl
             return fail(c, BMF_E_OOM, "device allocation failed (draw buffer)");
         c->draws_cap = need;
     }
-    // a host buffer: the first `first` doubles are copied first and `first_ev` recorded after
-    // them, so that their readers need not wait for the whole buffer
-    int64_t done = 0;
-    if (first > 0 && first < need && first_ev) {
-        CUDA_TRY(c, cudaMemcpyAsync(c->draws_d, d->ptr, first * sizeof(double), cudaMemcpyHostToDevice,
-                                    copy_st));
-        CUDA_TRY(c, cudaEventRecord(first_ev, copy_st));
-        done = first;
+    if (groups && evs) {
+        for (size_t q = 0; q + 1 < groups->size(); ++q) {
+            const int64_t a = (*groups)[q], b = (*groups)[q + 1];
+            if (b > a)
+                CUDA_TRY(c, cudaMemcpyAsync(c->draws_d + a, d->ptr + a, (b - a) * sizeof(double),
+                                            cudaMemcpyHostToDevice, copy_st));
+            CUDA_TRY(c, cudaEventRecord(evs[q], copy_st));
+        }
+    } else {
+        CUDA_TRY(c, cudaMemcpyAsync(c->draws_d, d->ptr, need * sizeof(double),
+                                    cudaMemcpyHostToDevice, copy_st));
     }
-    CUDA_TRY(c, cudaMemcpyAsync(c->draws_d + done, d->ptr + done, (need - done) * sizeof(double),
-                                cudaMemcpyHostToDevice, copy_st));
-    if (first > 0 && first_ev && done == 0) CUDA_TRY(c, cudaEventRecord(first_ev, copy_st));
     *out = c->draws_d;
     return BMF_OK;
 }
@@ -706,15 +712,49 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
     const bool mon = c->monitor && tt1 > tt0;
     const int64_t per = per_sweep_draws(c, sl0, sl1);
     const double *dr = nullptr;
-    const bool use_graph = c->sched.graph && !c->prof && n_sweeps > 0;
-    // host draw buffers are copied on the generator stream (idle with host draws), so that the
-    // first Gram pass, which needs no draws, starts at once; the first readers wait for it
-    const bool copy_async = draws && !draws->on_device && !use_graph && n_sweeps > 0;
-    // the call's first hyperparameter draws read only the first sweep's hyperparameter blocks
-    const int64_t first_hyper = 2 * (int64_t)(sl1 - sl0) * hyper_block_len(K);
+    // host draw buffers are copied on the generator stream (idle with host draws) in groups of
+    // sweeps -- 1, 2, 4, ..., 32, then equal groups, at most kCopyGroups -- and each sweep's readers
+    // wait only for their group, so the copy of later sweeps overlaps the sweeps; the graph
+    // schedule (which would have to finish the copy before its launch) is not used then
+    const bool host_draws = draws && !draws->on_device && n_sweeps > 0;
+    const bool use_graph = c->sched.graph && !c->prof && n_sweeps > 0 && !host_draws;
+    const bool copy_async = host_draws;
+    std::vector<int64_t> gsweep;   // first sweep of each group, then n_sweeps
+    if (copy_async) {
+        gsweep.push_back(0);
+        int64_t step = 1;
+        while (gsweep.back() < n_sweeps) {
+            const int left = kCopyGroups - (int)gsweep.size();
+            int64_t next = gsweep.back() + step;
+            if (left <= 1 || next > n_sweeps) next = n_sweeps;
+            gsweep.push_back(next);
+            if (step < 32) step *= 2;
+            else step = std::max<int64_t>(step, (n_sweeps - next + left - 2) / std::max(1, left - 1));
+        }
+    }
+    std::vector<int64_t> goff(gsweep.size());
+    for (size_t q = 0; q < gsweep.size(); ++q) goff[q] = gsweep[q] * per;
     bmf_status s = stage_draws(c, draws, per * n_sweeps, &dr, copy_async ? c->st5 : c->st,
-                               copy_async ? first_hyper : 0, c->ev_copy_h);
+                               copy_async ? &goff : nullptr, c->ev_copyq);
     if (s) return s;
+    // readers of sweep `it`'s draws on stream sx wait for its copy group (once per group and
+    // stream)
+    cudaStream_t wst[3] = {nullptr, nullptr, nullptr};
+    int wgot[3] = {-1, -1, -1};
+    auto wait_draws = [&](cudaStream_t sx, int64_t it) -> bmf_status {
+        if (!copy_async) return BMF_OK;
+        int q = 0;
+        while (gsweep[q + 1] <= it) ++q;
+        int k = 0;
+        while (k < 3 && wst[k] && wst[k] != sx) ++k;
+        if (k == 3) return fail(c, BMF_E_STATE, "internal: too many draw-reading streams");
+        wst[k] = sx;
+        if (q > wgot[k]) {
+            CUDA_TRY(c, cudaStreamWaitEvent(sx, c->ev_copyq[q], 0));
+            wgot[k] = q;
+        }
+        return BMF_OK;
+    };
     // the caller's host buffer is read until the copy completes: never return before that
     struct CopyWait {
         cudaStream_t st;
@@ -724,7 +764,6 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
             if (on) cudaStreamSynchronize(st);
         }
     } copy_wait{c->st5, copy_async};
-    if (copy_async) CUDA_TRY(c, cudaEventRecord(c->ev_copy, c->st5));
     // with the device generator, sweep it's draws live in ring buffer it % 2: the main stream
     // fills sweep it + 2 after sweep it's conditionals, which are ordered after every reader
     // of that buffer (the side stream's hyperparameter draw of sweep it finishes before them)
@@ -821,6 +860,7 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
     // W | X of sweep it and the Gram pass of sweep it+1 (and symmetrically for W).
     auto side_hyper = [&](int f, int it) -> bmf_status {
         const double *d = draws_of(it);
+        if (bmf_status sw = wait_draws(c->st2, it)) return sw;
         if (gen && it >= 2) CUDA_TRY(c, cudaStreamWaitEvent(c->st2, c->ev_gen[it & 1], 0));
         const int j0 = f == 0 ? 0 : nj[0];
         HyperParams hp{K, c->d_jobs2 + j0, nj[f], c->stats2, c->mu0_d, c->beta0, c->nu0,
@@ -860,7 +900,6 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
         // slots left them current (the conditional kernel keeps them current from then on)
         CUDA_TRY(c, cudaEventRecord(c->ev_fork, c->st));
         CUDA_TRY(c, cudaStreamWaitEvent(c->st2, c->ev_fork, 0));
-        if (copy_async) CUDA_TRY(c, cudaStreamWaitEvent(c->st2, c->ev_copy_h, 0));
         bool current = true;
         for (int sl = sl0; sl < sl1; ++sl) current = current && c->stats_ok[sl];
         for (int f = 0; f < 2; ++f) {
@@ -945,7 +984,7 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
                 // the previous sweep's RMSE pass reads the gathered copies this sweep rewrites;
                 // the generator fills this sweep's draws on the tail stream
                 if (it > 0 && mon) CUDA_TRY(c, cudaStreamWaitEvent(cs, c->ev_rmse, 0));
-                if (it == 0 && copy_async) CUDA_TRY(c, cudaStreamWaitEvent(cs, c->ev_copy, 0));
+                if ((s = wait_draws(cs, it))) return s;
                 if (gen && it >= 2) CUDA_TRY(c, cudaStreamWaitEvent(cs, c->ev_gen[it & 1], 0));
             }
             if (nch == 1) {
@@ -1546,8 +1585,10 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
         ok = ok && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) == cudaSuccess;
         for (cudaEvent_t *e : {&c->ev_fork, &c->ev_fac[0], &c->ev_fac[1], &c->ev_hyp[0], &c->ev_hyp[1],
                                &c->ev_cdone, &c->ev_tail, &c->ev_tail2, &c->ev_rmse, &c->ev_gen[0],
-                               &c->ev_gen[1], &c->ev_copy, &c->ev_copy_h})
+                               &c->ev_gen[1]})
             ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+        for (cudaEvent_t &e : c->ev_copyq)
+            ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
         for (cudaEvent_t &e : c->ev_chunk)
             ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
         ok = ok && cudaMallocHost(&c->rb, sizeof(*c->rb)) == cudaSuccess;
