@@ -148,7 +148,9 @@ __global__ void __launch_bounds__(kCondBlock) cond_kernel(CondParams a)
     // 7. statistics of the new state for the next hyperparameter draw: per block, sum x and
     //    the packed lower sum x x^T over the block's rows (thread e computes entry e, in row
     //    order); skipped when the caller computes them on another stream (stats == nullptr)
-    if (a.stats == nullptr) return;
+    // (only blocks whose factor draws its hyperparameters need them: a block of rows with
+    // propagated per-row priors skips them; every row of a block shares its subset's prior)
+    if (a.stats == nullptr || a.row_hslot[blk.row0] < 0) return;
     __syncthreads();
     const int NS = K + NT;
     double *out = a.stats + (a.blk0 + blockIdx.x) * (int64_t)NS;
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__(kCondBlock) cond_kernel_k(CondParams a)
 #pragma unroll
         for (int i = 0; i < K; ++i) B[i] = 0.0;
     }
-    if (a.stats == nullptr) return;
+    if (a.stats == nullptr || a.row_hslot[blk.row0] < 0) return;   // as in cond_kernel
 #pragma unroll
     for (int i = 0; i < K; ++i) XS[i][t] = B[i];
     __syncthreads();

@@ -343,7 +343,9 @@ __global__ void __launch_bounds__(kPairThreads) cond_pair_kernel(CondParams a)
     }
     // 7. per-block statistics of the new state (unless computed on another stream), read back
     //    from the state rows this block has just written, each entry over the rows in order
-    if (a.stats == nullptr) return;
+    // (only blocks whose factor draws its hyperparameters need them: a block of rows with
+    // propagated per-row priors skips them; every row of a block shares its subset's prior)
+    if (a.stats == nullptr || a.row_hslot[blk.row0] < 0) return;
     __syncthreads();
     constexpr int NS = K + NT;
     const double *Xb = a.X + blk.row0 * K;

@@ -663,7 +663,9 @@ __global__ void __launch_bounds__(32 * kWideWarps) cond_team_kernel(CondParams a
     // 7. per-block statistics of the new state (unless computed on another stream), read back
     //    from the state rows this block has just written (visible to the block after the
     //    barrier, and still in L1); no shared-memory copy, so more blocks fit on an SM
-    if (a.stats == nullptr) return;
+    // (only blocks whose factor draws its hyperparameters need them: a block of rows with
+    // propagated per-row priors skips them; every row of a block shares its subset's prior)
+    if (a.stats == nullptr || a.row_hslot[blk.row0] < 0) return;
     __syncthreads();
     const int NS = K + NT;
     const double *Xb = a.X + blk.row0 * K;
