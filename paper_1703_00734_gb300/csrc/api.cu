@@ -168,6 +168,8 @@ struct bmf_ctx {
     unsigned long long *ncorr_d = nullptr;
     int64_t *agg_base = nullptr;     // [(I + J) max(I, J)] submodel base rows of every launch
     double *agg_corr = nullptr;      // eigenvalue corrections of every (row, submodel) pair
+    int32_t *agg_list = nullptr;     // pairs needing an eigenvalue (scratch of one launch)
+    unsigned *agg_list_n = nullptr;
     // bmf_restart: the initial states in the original order and the original index of every
     // arena row (the chains restart by a gather on the device)
     double *X0o = nullptr, *W0o = nullptr;
@@ -1359,8 +1361,11 @@ bmf_status aggregate_all(bmf_ctx *c, int64_t *n_corrected)
                                  1.0 / (double)su.kept, out, c->st);
                 continue;
             }
+            if (n * (int64_t)(ns - 1) > (int64_t)INT32_MAX)
+                return fail(c, BMF_E_SHAPE, "too many (row, submodel) pairs in one aggregation block");
             AggParams ap{K, n, ns, c->agg_base + nb_done * MB, sd.mm_mu, sd.mm_L, sd.R,
-                         c->eps_rel, out, c->agg_corr, c->ncorr_d, c->err_d};
+                         c->eps_rel, out, c->agg_corr, c->ncorr_d, c->err_d, c->agg_list,
+                         c->agg_list_n};
             launch_aggregate(ap, c->st);
         }
     }
@@ -1670,6 +1675,8 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
     // eigenvalue corrections of one aggregation launch (at most N (J - 1) or D (I - 1) pairs;
     // the launches run in order on the context stream and reuse the buffer)
     c->agg_corr = c->mem.alloc<double>((size_t)N * std::max(J - 1, 0) + (size_t)D * std::max(I - 1, 0));
+    c->agg_list = c->mem.alloc<int32_t>((size_t)N * std::max(J - 1, 0) + (size_t)D * std::max(I - 1, 0));
+    c->agg_list_n = c->mem.alloc<unsigned>(1);
     c->X0o = c->mem.alloc<double>(N * K);
     c->W0o = c->mem.alloc<double>(D * K);
     c->xsrc = c->mem.alloc<int64_t>(c->P.RX);

@@ -195,6 +195,8 @@ struct AggParams {
     double *corr;             // [(J - 1) x n_rows] eigenvalue correction of each (row, j >= 1)
     unsigned long long *n_corrected;
     DevError *err;
+    int32_t *list;            // [(J - 1) x n_rows] scratch: pairs whose difference is not PD
+    unsigned *list_n;         // their count (reset by the launcher)
 };
 void launch_aggregate(const AggParams &a, cudaStream_t st);
 

@@ -765,32 +765,62 @@ __device__ bool row_pd_test(double *P, int K, int rb)
     return true;
 }
 
+static inline size_t agg_pd_slots(int K) { return (size_t)ntri(K); }
 static inline size_t agg_corr_slots(int K) { return (size_t)ntri(K) + 3 * K; }
 
-__global__ void __launch_bounds__(kRowBlock) aggregate_corr_kernel(AggParams a, int64_t n_pairs)
+// Pass 1a, one thread per (row n, submodel j >= 1): corr = 0 where the difference is positive
+// definite, else the pair is appended to a list for pass 1b (one atomic per warp).  Splitting
+// the eigenvalue off keeps pass 1b's warps free of pairs that need none (otherwise a warp's
+// positive-definite pairs idle while its others take the eigenvalue path).
+__global__ void __launch_bounds__(kRowBlock) aggregate_pd_kernel(AggParams a, int64_t n_pairs)
 {
     extern __shared__ double sm[];
     const int t = threadIdx.x, rb = blockDim.x;
     const int64_t q = (int64_t)blockIdx.x * rb + t;
-    unsigned long long nc = 0;
+    bool listed = false;
     if (q < n_pairs) {
         const int K = a.K, NT = ntri(K);
         const int j = 1 + (int)(q / a.n_rows);
         const int64_t n = q % a.n_rows;
-        double *Fm = sm + t, *v = Fm + NT * rb, *dg = v + K * rb, *of = dg + K * rb;
+        double *Fm = sm + t;
         const int64_t r1 = a.sub_base[0] + n, rj = a.sub_base[j] + n;
         for (int e = 0; e < NT; ++e) RS(Fm, e) = a.L[(int64_t)e * a.R + rj] - a.L[(int64_t)e * a.R + r1];
-        double corr = 0.0;
-        if (!row_pd_test(Fm, K, rb)) {
-            double mean_diag = 0.0;
-            for (int i = 0; i < K; ++i) mean_diag += a.L[(int64_t)tri(i, i) * a.R + r1];
-            mean_diag /= (double)K;
-            const double eps = a.eps_rel * (mean_diag > 1.0 ? mean_diag : 1.0);
-            for (int e = 0; e < NT; ++e) RS(Fm, e) = a.L[(int64_t)e * a.R + rj] - a.L[(int64_t)e * a.R + r1];
-            corr = fabs(min_eig_tridiag(Fm, v, dg, of, K, rb)) + eps;
-            nc = 1;
-        }
-        a.corr[q] = corr;
+        if (row_pd_test(Fm, K, rb))
+            a.corr[q] = 0.0;
+        else
+            listed = true;
+    }
+    const unsigned am = __activemask();
+    const unsigned votes = __ballot_sync(am, listed);
+    const int lane = t & 31, leader = __ffs(am) - 1;
+    unsigned base = 0;
+    if (lane == leader && votes) base = atomicAdd(a.list_n, (unsigned)__popc(votes));
+    base = __shfl_sync(am, base, leader);
+    if (listed) a.list[base + __popc(votes & ((1u << lane) - 1u))] = (int32_t)q;
+}
+
+// Pass 1b, one thread per listed pair: corr = |lambda_min| + eps (Algorithm 2).
+__global__ void __launch_bounds__(kRowBlock) aggregate_eig_kernel(AggParams a)
+{
+    extern __shared__ double sm[];
+    const int t = threadIdx.x, rb = blockDim.x;
+    const int64_t k = (int64_t)blockIdx.x * rb + t;
+    if ((int64_t)blockIdx.x * rb >= (int64_t)*a.list_n) return;    // the whole block is past the list
+    unsigned long long nc = 0;
+    if (k < (int64_t)*a.list_n) {
+        const int K = a.K, NT = ntri(K);
+        const int64_t q = a.list[k];
+        const int j = 1 + (int)(q / a.n_rows);
+        const int64_t n = q % a.n_rows;
+        double *Fm = sm + t, *v = Fm + NT * rb, *dg = v + K * rb, *of = dg + K * rb;
+        const int64_t r1 = a.sub_base[0] + n, rj = a.sub_base[j] + n;
+        double mean_diag = 0.0;
+        for (int i = 0; i < K; ++i) mean_diag += a.L[(int64_t)tri(i, i) * a.R + r1];
+        mean_diag /= (double)K;
+        const double eps = a.eps_rel * (mean_diag > 1.0 ? mean_diag : 1.0);
+        for (int e = 0; e < NT; ++e) RS(Fm, e) = a.L[(int64_t)e * a.R + rj] - a.L[(int64_t)e * a.R + r1];
+        a.corr[q] = fabs(min_eig_tridiag(Fm, v, dg, of, K, rb)) + eps;
+        nc = 1;
     }
     // one atomic per warp (the block may end in a partial warp: only its existing lanes vote)
     const unsigned am = __activemask();
@@ -862,13 +892,23 @@ void launch_aggregate(const AggParams &a, cudaStream_t st)
     if (a.n_rows <= 0) return;
     const int64_t n_pairs = a.n_rows * (int64_t)(a.J - 1);
     if (n_pairs > 0) {
+        cudaMemsetAsync(a.list_n, 0, sizeof(unsigned), st);
+        {
+            const size_t per = agg_pd_slots(a.K);
+            const int rb = row_block_small(per);
+            const size_t smem = per * rb * sizeof(double);
+            if (smem > 48 * 1024)
+                cudaFuncSetAttribute(aggregate_pd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+            aggregate_pd_kernel<<<(int)((n_pairs + rb - 1) / rb), rb, smem, st>>>(a, n_pairs);
+        }
         const size_t per = agg_corr_slots(a.K);
         const int rb = row_block_small(per);
         const size_t smem = per * rb * sizeof(double);
         if (smem > 48 * 1024)
-            cudaFuncSetAttribute(aggregate_corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(aggregate_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
-        aggregate_corr_kernel<<<(int)((n_pairs + rb - 1) / rb), rb, smem, st>>>(a, n_pairs);
+        aggregate_eig_kernel<<<(int)((n_pairs + rb - 1) / rb), rb, smem, st>>>(a);
     }
     const size_t per = agg_slots(a.K);
     const int rb = row_block_small(per);
