@@ -1249,7 +1249,26 @@ bmf_status finalize_stage(bmf_ctx *c, int stage)
 {
     int sl0, sl1;
     if (!stage_slots(c, stage, sl0, sl1)) return BMF_OK;
-    for (int sl = sl0; sl < sl1; ++sl) {
+    // moment matching of a whole stage in one launch per factor when its subsets are alike (the
+    // stage's rows are contiguous in each arena; a launch per subset leaves most SMs idle on
+    // small subsets)
+    bool batch = c->summary == BMF_SUMMARY_MM && c->full_moments && sl1 - sl0 > 1;
+    const int64_t kept0 = c->ss[geom_of_slot(c, sl0).sid].kept;
+    for (int sl = sl0; sl < sl1 && batch; ++sl) {
+        const SubState &su = c->ss[geom_of_slot(c, sl).sid];
+        batch = !su.finalized && su.kept == kept0 && kept0 >= c->K + 1;
+    }
+    if (batch) {
+        const SubsetGeom &ga = geom_of_slot(c, sl0), &gb = geom_of_slot(c, sl1 - 1);
+        for (int f = 0; f < 2; ++f) {
+            Side &sd = f == 0 ? c->X : c->W;
+            MMParams mp{c->K, f == 0 ? ga.xoff : ga.woff, f == 0 ? gb.xoff + gb.n() : gb.woff + gb.d(),
+                        sd.R, sd.S1, sd.S2, (double)kept0, sd.mm_mu, sd.mm_L, sd.mm_b, c->err_d};
+            launch_mm(mp, c->st);
+        }
+        for (int sl = sl0; sl < sl1; ++sl) c->ss[geom_of_slot(c, sl).sid].finalized = true;
+    }
+    for (int sl = sl0; sl < sl1 && !batch; ++sl) {
         bmf_status s = finalize_subset(c, geom_of_slot(c, sl).sid);
         if (s) return s;
     }
