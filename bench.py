@@ -41,6 +41,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "pp4x4-100000x20000-20M-k16"
+# arithmetic of the path per --precision: gathers and Gram sums, then the FP64 conditional
+DTYPE = {"fp32": "f32+f64", "bf16": "bf16+f64", "tf32": "tf32+f64", "fp64": "f64"}
 PLAIN_WORKLOAD = "zipf-69878x10677-10M-k10"
 METRIC = "Gibbs sweeps/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -165,7 +167,7 @@ def make_draws(d, K, nu0, n_sweeps, seed, out=None):
 def algorithmic(d, K, prec):
     """Algorithmic work per launch of each kernel class (the cost terms of Section 4.3)."""
     M = len(d["row"])
-    b = {"fp64": 8, "fp32": 4, "bf16": 2}[prec]
+    b = {"fp64": 8, "fp32": 4, "tf32": 4, "bf16": 2}[prec]
     bval = 8 if prec == "fp64" else 4
     per_obs = 4 + bval + K * b              # index + value + gathered partner row
     nt = K * (K + 1) // 2
@@ -315,7 +317,7 @@ def run_ours(args, rank, world, local_rank):
     out = {
         "metric": METRIC, "value": sweeps_s, "unit": "sweeps/s", "n_gpus": world, "steps": S,
         "warmup": W, "ms_per_step": ms / S, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if args.precision != "fp64" else "f64",
+        "vs_baseline": None, "dtype": DTYPE[args.precision],
         "data": "synthetic (seeded Zipf(1.2) rating matrix standing in for a MovieLens-shaped "
                 "data set; no real data available)",
         "config": {"workload": args.workload,
@@ -367,7 +369,7 @@ def pp_algorithmic(geom, K, prec):
     """Algorithmic work per launch of each kernel class in each stage (one launch per class and
     sweep with one row chunk): Gram pass bytes = entries x (index + value + gathered partner
     row); conditional FLOPs = rows x 2 x (assembly + Cholesky + two solves) FMAs."""
-    b = {"fp64": 8, "fp32": 4, "bf16": 2}[prec]
+    b = {"fp64": 8, "fp32": 4, "tf32": 4, "bf16": 2}[prec]
     bval = 8 if prec == "fp64" else 4
     per_obs = 4 + bval + K * b
     fma_row = K * (K + 1) // 2 + K + (K ** 3 - K) // 6 + K * (K - 1)
@@ -595,7 +597,7 @@ def run_pp(args, rank, world, local_rank):
     out = {
         "metric": METRIC, "value": sweeps_s, "unit": "sweeps/s", "n_gpus": world, "steps": S,
         "warmup": Wu, "ms_per_step": ms / S, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if args.precision != "fp64" else "f64",
+        "vs_baseline": None, "dtype": DTYPE[args.precision],
         "data": "synthetic (seeded Zipf(1.2) pattern, Gaussian values of a rank-16 truth plus "
                 "N(0, 0.5^2) noise; no real data available)",
         "config": {"workload": args.workload, "N": d["N"], "D": d["D"], "train_obs": M,
@@ -1182,7 +1184,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "tf32", "fp64"])
     ap.add_argument("--burnin", type=int, default=2)
     ap.add_argument("--pp-sweeps", type=int, default=PP_SWEEPS,
                     help="sweeps per stage of a PP run (grid workloads)")

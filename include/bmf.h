@@ -124,8 +124,11 @@ typedef enum {
 } bmf_status;
 
 /* Precision of the gathered factor copies and of the Gram accumulation.  The conditional
- * assembly, Cholesky, solves, draws, hyperparameter step and moments are FP64 in all modes. */
-enum { BMF_FP64 = 0, BMF_FP32 = 1, BMF_BF16 = 2 };
+ * assembly, Cholesky, solves, draws, hyperparameter step and moments are FP64 in all modes.
+ * FP32 gathers at K > 16 reach the tensor cores as split TF32 (three products per tile, close to
+ * FP32 products); BMF_TF32 keeps FP32 gathers but takes one TF32 product per tile (operands
+ * rounded to 10-bit mantissas) at K > 16, and is BMF_FP32 at K <= 16. */
+enum { BMF_FP64 = 0, BMF_FP32 = 1, BMF_BF16 = 2, BMF_TF32 = 3 };
 enum { BMF_ORDER_NONE = 0, BMF_ORDER_DECREASING = 1 };
 enum { BMF_FACTOR_X = 0, BMF_FACTOR_W = 1 };
 
@@ -133,7 +136,7 @@ enum { BMF_FACTOR_X = 0, BMF_FACTOR_W = 1 };
 
 typedef struct {
     int32_t K;         /* latent dimension, 1..BMF_MAX_K */
-    int32_t precision; /* BMF_FP64 / BMF_FP32 / BMF_BF16 */
+    int32_t precision; /* BMF_FP64 / BMF_FP32 / BMF_BF16 / BMF_TF32 */
     double tau;        /* noise precision (Eq. 3), > 0 */
     double beta0;      /* Normal-Wishart beta0 > 0 */
     double nu0;        /* Normal-Wishart nu0 > K - 1 */

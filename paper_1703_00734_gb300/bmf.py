@@ -11,8 +11,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libbmf.so")
 
-BMF_FP64, BMF_FP32, BMF_BF16 = 0, 1, 2
-PRECISION = {"fp64": BMF_FP64, "fp32": BMF_FP32, "bf16": BMF_BF16}
+BMF_FP64, BMF_FP32, BMF_BF16, BMF_TF32 = 0, 1, 2, 3
+PRECISION = {"fp64": BMF_FP64, "fp32": BMF_FP32, "bf16": BMF_BF16, "tf32": BMF_TF32}
 ORDER = {"none": 0, "decreasing": 1}
 MOMENTS = {"auto": 0, "mean": 1, "full": 2}
 SUMMARY = {"mm": 0, "dm": 1, "gmm": 2}

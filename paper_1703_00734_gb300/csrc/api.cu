@@ -184,6 +184,7 @@ struct bmf_ctx {
     std::vector<SubState> ss;
     int stage_open = 0;
     bool failed = false;
+    bool tf32 = false;               // BMF_TF32: one TF32 product per wide Gram tile
     std::string err;
     int chunk_obs = 1024;
     bool full_moments = false;
@@ -962,7 +963,7 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
                     g.part = static_cast<char *>(c->part) + (ia - i0) * c->ld_part * pbytes;
                     if (g.n_items > 0)
                         traced(c, c->st, f == 0 ? K_GRAM_X : K_GRAM_W, 1,
-                               [&] { launch_gram_wide(K, c->prec, g, gram_grid, c->st); });
+                               [&] { launch_gram_wide(K, c->prec, g, gram_grid, c->st, c->tf32); });
                 } else {
                     g.tasks = me.tasks + me.blk_task[ba];
                     g.n_tasks = me.blk_task[bb] - me.blk_task[ba];
@@ -1510,7 +1511,7 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
         g_init_error = "K must be in 1..64";
         return BMF_E_ARG;
     }
-    if (cfg->precision < BMF_FP64 || cfg->precision > BMF_BF16) {
+    if (cfg->precision < BMF_FP64 || cfg->precision > BMF_TF32) {
         g_init_error = "unknown precision";
         return BMF_E_ARG;
     }
@@ -1525,7 +1526,9 @@ bmf_status bmf_init(bmf_ctx **out, const bmf_config *cfg, int64_t N, int64_t D, 
     }
     bmf_ctx *c = new bmf_ctx();
     c->K = K;
-    c->prec = cfg->precision;
+    // single-pass TF32 is the FP32 storage and kernels with one product per wide Gram tile
+    c->prec = cfg->precision == BMF_TF32 ? BMF_FP32 : cfg->precision;
+    c->tf32 = cfg->precision == BMF_TF32;
     c->tau = cfg->tau;
     c->beta0 = cfg->beta0;
     c->nu0 = nu0;

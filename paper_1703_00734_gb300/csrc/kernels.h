@@ -270,7 +270,8 @@ void launch_mix_choose(const MixChooseParams &p, cudaStream_t st);
 // conditional draw with one warp per row.  Partials: packed lower of the exact K, then K rhs.
 int wide_kt(int K);
 int wide_part_ld(int K);
-void launch_gram_wide(int K, int prec, const GramParams &a, int grid, cudaStream_t st);
+void launch_gram_wide(int K, int prec, const GramParams &a, int grid, cudaStream_t st,
+                      bool tf32_single = false);
 // Conditional draw with a team of `team` lanes (4, 8, 16 or 32) per row (wide.cu).
 void launch_cond_team(int prec, const CondParams &a, int n_blocks, int team, cudaStream_t st);
 int cond_team_size(int K);

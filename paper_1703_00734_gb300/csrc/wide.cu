@@ -252,9 +252,10 @@ __global__ void __launch_bounds__(128) gram_wide_bf16(GramParams a)
 }
 
 // ------------------------------------------------------------------------------------------
-// FP32 Gram by split TF32: rows [obs][KT + 4] floats in shared memory (column KT holds y)
+// FP32 Gram by split TF32 (SPLIT: hi.hi + hi.lo + lo.hi per tile) or single-pass TF32 (hi.hi):
+// rows [obs][KT + 4] floats in shared memory (column KT holds y)
 // ------------------------------------------------------------------------------------------
-template <int KT>
+template <int KT, bool SPLIT>
 __global__ void __launch_bounds__(128) gram_wide_tf32(GramParams a)
 {
     constexpr int LDS = KT + 8;           // conflict-free fragment loads; column KT holds y
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(128) gram_wide_tf32(GramParams a)
 #pragma unroll
                     for (int h = 0; h < 4; ++h) {
                         ah[mi][h] = tf32_of(v[h]);
-                        al[mi][h] = tf32_of(v[h] - __uint_as_float(ah[mi][h]));
+                        if constexpr (SPLIT) al[mi][h] = tf32_of(v[h] - __uint_as_float(ah[mi][h]));
                     }
                 }
 #pragma unroll
@@ -312,10 +313,12 @@ __global__ void __launch_bounds__(128) gram_wide_tf32(GramParams a)
                     const int col = nj >= 0 ? 8 * nj : KT;
                     const float bv0 = S[(kb + tig) * LDS + col + g], bv1 = S[(kb + tig + 4) * LDS + col + g];
                     const uint32_t bh0 = tf32_of(bv0), bh1 = tf32_of(bv1);
-                    const uint32_t bl0 = tf32_of(bv0 - __uint_as_float(bh0));
-                    const uint32_t bl1 = tf32_of(bv1 - __uint_as_float(bh1));
-                    mma_tf32(acc[t], al[mi], bh0, bh1);
-                    mma_tf32(acc[t], ah[mi], bl0, bl1);
+                    if constexpr (SPLIT) {
+                        const uint32_t bl0 = tf32_of(bv0 - __uint_as_float(bh0));
+                        const uint32_t bl1 = tf32_of(bv1 - __uint_as_float(bh1));
+                        mma_tf32(acc[t], al[mi], bh0, bh1);
+                        mma_tf32(acc[t], ah[mi], bl0, bl1);
+                    }
                     mma_tf32(acc[t], ah[mi], bh0, bh1);
                 }
             }
@@ -405,21 +408,30 @@ int wide_kt(int K) { return K <= 32 ? 32 : (K <= 48 ? 48 : 64); }
 // Partial entries per item for K > 16 (exact K layout, padded to a multiple of 4).
 int wide_part_ld(int K) { return (ntri(K) + K + 3) / 4 * 4; }
 
+template <int KT, bool SPLIT>
+static void launch_tf32_t(const GramParams &a, int grid, cudaStream_t st)
+{
+    const size_t smem = (size_t)4 * kWideObs * (KT + 8) * 4;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(gram_wide_tf32<KT, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    gram_wide_tf32<KT, SPLIT><<<grid, 128, smem, st>>>(a);
+}
+
 template <int KT>
-static void launch_wide_t(int prec, const GramParams &a, int grid, cudaStream_t st)
+static void launch_wide_t(int prec, const GramParams &a, int grid, cudaStream_t st, bool single)
 {
     if (prec == BMF_BF16) {
         const size_t smem = (size_t)4 * kWideObs * (KT + 8) * 2;
         gram_wide_bf16<KT><<<grid, 128, smem, st>>>(a);
+    } else if (single) {
+        launch_tf32_t<KT, false>(a, grid, st);
     } else {
-        const size_t smem = (size_t)4 * kWideObs * (KT + 8) * 4;
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(gram_wide_tf32<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        gram_wide_tf32<KT><<<grid, 128, smem, st>>>(a);
+        launch_tf32_t<KT, true>(a, grid, st);
     }
 }
 
-void launch_gram_wide(int K, int prec, const GramParams &a, int grid, cudaStream_t st)
+void launch_gram_wide(int K, int prec, const GramParams &a, int grid, cudaStream_t st, bool tf32_single)
 {
     if (a.n_items == 0) return;
     if (prec == BMF_FP64) {
@@ -441,9 +453,9 @@ void launch_gram_wide(int K, int prec, const GramParams &a, int grid, cudaStream
         return;
     }
     switch (wide_kt(K)) {
-    case 32: launch_wide_t<32>(prec, a, grid, st); break;
-    case 48: launch_wide_t<48>(prec, a, grid, st); break;
-    default: launch_wide_t<64>(prec, a, grid, st); break;
+    case 32: launch_wide_t<32>(prec, a, grid, st, tf32_single); break;
+    case 48: launch_wide_t<48>(prec, a, grid, st, tf32_single); break;
+    default: launch_wide_t<64>(prec, a, grid, st, tf32_single); break;
     }
 }
 

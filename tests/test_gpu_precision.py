@@ -111,6 +111,16 @@ def test_fp32_single_transition_within_bound(K, pattern):
     print(f"fp32 K={K}: worst err/bound X {qx:.3f} W {qw:.3f}")
 
 
+@pytest.mark.parametrize("K", [24, 40])
+def test_tf32_single_transition_within_bound(K):
+    """BMF_TF32 at K > 16: one TF32 tensor-core product per Gram tile, partner rows and values
+    rounded to 10-bit mantissas (2^-11)."""
+    d = synth.make_workload(None, N=500, D=320, M=40_000, pattern="zipf", K=K, sigma=0.8,
+                            tau=1.5625, seed=60 + K, s_row=1.2, s_col=1.2, ratings=True)
+    qx, qw = run_reduced(d, K, "tf32", 2.0 ** -11, u_y=2.0 ** -11)
+    print(f"tf32 K={K}: worst err/bound X {qx:.3f} W {qw:.3f}")
+
+
 @pytest.mark.parametrize("K", [10, 16])
 def test_bf16_single_transition_within_bound(K):
     d = synth.make_workload(None, N=500, D=320, M=40_000, pattern="zipf", K=K, sigma=0.8,
