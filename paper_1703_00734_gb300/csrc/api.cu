@@ -727,7 +727,7 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
         gsweep.push_back(0);
         int64_t step = 1;
         while (gsweep.back() < n_sweeps) {
-            const int left = kCopyGroups - (int)gsweep.size();
+            const int left = kCopyGroups - 1 - (int)gsweep.size();   // one group for the first hyper blocks
             int64_t next = gsweep.back() + step;
             if (left <= 1 || next > n_sweeps) next = n_sweeps;
             gsweep.push_back(next);
@@ -735,19 +735,26 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
             else step = std::max<int64_t>(step, (n_sweeps - next + left - 2) / std::max(1, left - 1));
         }
     }
-    std::vector<int64_t> goff(gsweep.size());
-    for (size_t q = 0; q < gsweep.size(); ++q) goff[q] = gsweep[q] * per;
+    // group boundaries in doubles: the first sweep's hyperparameter blocks alone (the call's
+    // first hyperparameter draws read only them), then the groups of sweeps
+    const int64_t first_hyper = 2 * (int64_t)(sl1 - sl0) * hyper_block_len(K);
+    std::vector<int64_t> goff;
+    if (copy_async) {
+        goff.push_back(0);
+        goff.push_back(first_hyper);
+        for (size_t q = 1; q < gsweep.size(); ++q) goff.push_back(gsweep[q] * per);
+    }
     bmf_status s = stage_draws(c, draws, per * n_sweeps, &dr, copy_async ? c->st5 : c->st,
                                copy_async ? &goff : nullptr, c->ev_copyq);
     if (s) return s;
-    // readers of sweep `it`'s draws on stream sx wait for its copy group (once per group and
-    // stream)
+    // a reader of the draws up to offset `need` (exclusive) on stream sx waits for the group
+    // holding it (once per group and stream)
     cudaStream_t wst[3] = {nullptr, nullptr, nullptr};
     int wgot[3] = {-1, -1, -1};
-    auto wait_draws = [&](cudaStream_t sx, int64_t it) -> bmf_status {
+    auto wait_upto = [&](cudaStream_t sx, int64_t need) -> bmf_status {
         if (!copy_async) return BMF_OK;
         int q = 0;
-        while (gsweep[q + 1] <= it) ++q;
+        while (goff[q + 1] < need) ++q;
         int k = 0;
         while (k < 3 && wst[k] && wst[k] != sx) ++k;
         if (k == 3) return fail(c, BMF_E_STATE, "internal: too many draw-reading streams");
@@ -758,6 +765,9 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
         }
         return BMF_OK;
     };
+    // sweep it's hyperparameter blocks, and the whole sweep (its z's and noise variates)
+    auto wait_hyper = [&](cudaStream_t sx, int64_t it) { return wait_upto(sx, it * per + first_hyper); };
+    auto wait_draws = [&](cudaStream_t sx, int64_t it) { return wait_upto(sx, (it + 1) * per); };
     // the caller's host buffer is read until the copy completes: never return before that
     struct CopyWait {
         cudaStream_t st;
@@ -863,7 +873,7 @@ bmf_status run_batch(bmf_ctx *c, int sl0, int sl1, int n_sweeps, const bmf_draws
     // W | X of sweep it and the Gram pass of sweep it+1 (and symmetrically for W).
     auto side_hyper = [&](int f, int it) -> bmf_status {
         const double *d = draws_of(it);
-        if (bmf_status sw = wait_draws(c->st2, it)) return sw;
+        if (bmf_status sw = wait_hyper(c->st2, it)) return sw;
         if (gen && it >= 2) CUDA_TRY(c, cudaStreamWaitEvent(c->st2, c->ev_gen[it & 1], 0));
         const int j0 = f == 0 ? 0 : nj[0];
         HyperParams hp{K, c->d_jobs2 + j0, nj[f], c->stats2, c->mu0_d, c->beta0, c->nu0,
