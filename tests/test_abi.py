@@ -51,3 +51,20 @@ def test_missing_library_fails_loudly(tmp_path):
             bmf.load(str(tmp_path / "nope.so"))
         finally:
             bmf._lib = None
+
+
+def header_enums():
+    """name -> value of every `BMF_NAME = value` enumerator in the public header."""
+    src = open(os.path.join(ROOT, "include", "bmf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return {k: int(v) for k, v in re.findall(r"\b(BMF_[A-Z0-9_]+)\s*=\s*(\d+)", src)}
+
+
+def test_binding_constants_match_the_header():
+    from paper_1703_00734_gb300 import bmf
+    enums = header_enums()
+    for name in ("BMF_FP64", "BMF_FP32", "BMF_BF16", "BMF_TF32"):
+        assert getattr(bmf, name) == enums[name], name
+    assert bmf.PRECISION == {"fp64": enums["BMF_FP64"], "fp32": enums["BMF_FP32"],
+                             "bf16": enums["BMF_BF16"], "tf32": enums["BMF_TF32"]}
+    assert (bmf.FACTOR_X, bmf.FACTOR_W) == (enums["BMF_FACTOR_X"], enums["BMF_FACTOR_W"])
